@@ -1,0 +1,392 @@
+"""Throughput of the fused D2Q5Q4Q4 step (MLUPS and fraction of the HBM roofline).
+
+Workload: the 2D unsteady circular dam-break on a 4096 x 4096 periodic grid (depth 2
+inside radius 0.2 of the centre of the unit square, 1 outside, at rest, plus a seeded
+uniform perturbation of +-1e-3), D2Q5Q4Q4 with lambda = 8, s = 1.8, a = 0.05, g = 1,
+FP32 populations.  One bench step is one time step of the scheme: one launch of the
+fused pull-stream + collide kernel over the whole grid (boundaries, moments,
+equilibria, relaxation).  The two 872 MB population buffers exceed the 129 MB L2,
+so every step streams from HBM.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line on rank 0.  Under torchrun each rank runs an independent
+replica on its own GPU (weak scaling); `value` is the sum over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "MLUPS and % of HBM roofline per step (FP32 vs FP64, batched vs plain) at stated L1 error"
+UNIT = "MLUPS"
+N = 4096
+LAM, S_RATE, A_REST = 8.0, 1.8, 0.05
+BYTES_PER_LUP = {"f32": 104.0, "f64": 208.0}  # 13 populations read + 13 written
+WORKLOAD = ("2D circular dam-break 4096x4096 periodic, D2Q5Q4Q4 (13 populations), "
+            "lambda=8 s=1.8 a=0.05 g=1, h=2 for r<0.2 else 1 plus U[-1e-3,1e-3]")
+JOB_STEPS = 1000  # steps of the workload as one job (the end-to-end unit)
+REF_SAMPLE = 512   # side of the periodic window the CPU oracle advances per reference step
+
+# DRAM traffic per launch of the timed kernel from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), valid only for the kernel source it was taken on.
+NCU_TRAFFIC = {"src_sha256": None, "bytes_per_launch": None, "case": None}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels_2d.cu", "scheme.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1401_0427_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 100 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.perf_counter(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0: float, t1: float):
+        rows = [s for (t, s) in self.samples if t0 - 0.15 <= t <= t1 + 0.15]
+        if not rows:
+            rows = [s for (_, s) in self.samples]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            parts = [p.strip() for p in r.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- CPU oracle
+def cpu_oracle_mlups(W0, target_seconds: float = 12.0, max_steps: int = 40):
+    """The FP64 oracle as it stands, on all host cores, over the full 4096^2 grid for
+    a bounded number of steps (about target_seconds of CPU work)."""
+    import oracle
+
+    cores = oracle.set_threads(0)
+    p = oracle.params(N, N, lam=LAM, s=S_RATE, a=A_REST)
+    F = oracle.equilibrium_2d(*W0, p)
+    t = time.perf_counter()
+    F = oracle.run_2d(F, 1, p)
+    t1 = time.perf_counter() - t
+    steps = int(max(1, min(max_steps, math.ceil(target_seconds / max(t1, 1e-3)) - 1)))
+    t = time.perf_counter()
+    oracle.run_2d(F, steps, p)
+    dt = time.perf_counter() - t
+    return {"value": N * N * steps / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, the full 4096x4096 grid of the workload for {steps} steps "
+                      f"({dt:.1f} s, OpenMP over rows)"}
+
+
+def run_reference(args, world, rank):
+    """The oracle on the host cores: each bench step advances a 512x512 periodic window
+    of the workload's initial field by one step (a bounded sample of the workload)."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1401_0427_gb300 import inputs
+
+    cores = oracle.set_threads(0)
+    h, hu, hv = inputs.circular_dam_break_2d(N, seed=inputs.stream_seed(3))
+    c0 = N // 2 - REF_SAMPLE // 2
+    win = [np.ascontiguousarray(x[c0:c0 + REF_SAMPLE, c0:c0 + REF_SAMPLE]) for x in (h, hu, hv)]
+    p = oracle.params(REF_SAMPLE, REF_SAMPLE, lam=LAM, s=S_RATE, a=A_REST)
+    F = oracle.equilibrium_2d(*win, p)
+    for _ in range(args.warmup):
+        F = oracle.run_2d(F, 1, p)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        F = oracle.run_2d(F, 1, p)
+    dt = time.perf_counter() - t
+    value = REF_SAMPLE * REF_SAMPLE * args.steps / dt / 1e6
+    sample = (f"FP64 oracle on a {REF_SAMPLE}x{REF_SAMPLE} periodic window (centre) of the workload, "
+              f"one step per bench step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    global N
+    import torch
+
+    N = args.side
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1401_0427_gb300 import build as libbuild
+    from paper_1401_0427_gb300 import inputs, lbm_sw
+
+    libbuild.build()
+    stream = torch.cuda.current_stream()
+    W0 = inputs.circular_dam_break_2d(N, seed=inputs.stream_seed(3))
+    cells = N * N
+    prec = lbm_sw.FP64 if args.precision == "fp64" else lbm_sw.FP32
+    dt_name = "f64" if prec == lbm_sw.FP64 else "f32"
+
+    sim = lbm_sw.Simulation(N, N, precision=prec, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream)
+    sim.set_state(*W0)
+    launches0 = sim.info().kernel_launches
+    for _ in range(args.warmup):
+        sim.step(1)
+    sim.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    gpu_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].strip().isdigit() else local
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.3)
+
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    events[0].record(stream)
+    for i in range(args.steps):
+        sim.step(1)
+        events[i + 1].record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.perf_counter()
+    barrier(world)
+    time.sleep(0.2)
+    clocks.stop()
+
+    total_ms = events[0].elapsed_time(events[-1])
+    per_launch = [events[i].elapsed_time(events[i + 1]) for i in range(args.steps)]
+    launches = sim.info().kernel_launches - launches0 - args.warmup
+    total_ms = max_over_ranks(world, total_ms)
+    diag = sim.diagnostics()
+    mlups_rank = cells * args.steps / (total_ms * 1e-3) / 1e6
+    value = sum_over_ranks(world, cells * args.steps) / (total_ms * 1e-3) / 1e6
+
+    avg_launch_s = float(np.mean(per_launch)) * 1e-3
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_LUP[dt_name] * cells / avg_launch_s / 1e9
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["src_sha256"] == kernel_source_hash() else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": f"{peak_kind} (copy bandwidth)",
+                "frac_of_nominal_8tbs": achieved / 8000.0,
+                "kernel": "step2d_vec<float>" if dt_name == "f32" else "step2d_vec<double>",
+                "algorithmic_bytes_per_launch": BYTES_PER_LUP[dt_name] * cells,
+                "median_launch_ms": float(np.median(per_launch))}
+    sim.close()
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": dt_name, "data": "synthetic",
+              "config": {"workload": WORKLOAD if N == 4096 else WORKLOAD.replace("4096x4096", f"{N}x{N}"),
+                         "nx": N, "ny": N, "cells": cells, "precision": f"{args.precision.upper()} populations",
+                         "l2": "inputs larger than L2 (two 872 MB population buffers, 129 MB L2)",
+                         "parallelism": "replicas" if world > 1 else "single GPU"},
+              "roofline": roofline, "gpu_launches": int(launches),
+              "clocks": clocks.summary(t_wall0, t_wall1),
+              "conservation": {"sum_h": diag[0], "min_h": diag[3]}}
+
+    if not args.quick:
+        result["variants"] = variants(args, W0, stream, lbm_sw, torch)
+        result["l1_error"] = result["variants"].pop("_l1")
+        result["e2e"] = end_to_end(W0, stream, lbm_sw, torch)
+    if rank == 0 and not args.quick and not args.skip_cpu:
+        result["cpu_baseline"] = cpu_oracle_mlups(W0)
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def variants(args, W0, stream, lbm_sw, torch):
+    """FP64 throughput of the same workload, and the FP32 error against the FP64 run
+    (the FP64 path matches the FP64 oracle to 1e-12 in the parity tests)."""
+    out = {}
+    steps64 = min(args.steps, 200)
+    hs = {}
+    for name, prec in (("fp32", lbm_sw.FP32), ("fp64", lbm_sw.FP64)):
+        sim = lbm_sw.Simulation(N, N, precision=prec, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream)
+        sim.set_state(*W0)
+        sim.step(3)
+        sim.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps64
+        sim.step(JOB_STEPS - 3 - steps64)
+        hs[name] = sim.moments()[0]
+        sim.close()
+        bpl = BYTES_PER_LUP["f32" if name == "fp32" else "f64"]
+        out[name] = {"MLUPS": N * N / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                     "GB_per_s": bpl * N * N / (ms * 1e-3) / 1e9}
+    out["_l1"] = {"relative_l1_h": float(np.abs(hs["fp32"] - hs["fp64"]).sum() / np.abs(hs["fp64"]).sum()),
+                  "steps": JOB_STEPS, "against": "FP64 run of the same workload (equal to the FP64 oracle "
+                                                 "within 1e-12 in the parity tests)"}
+    return out
+
+
+def end_to_end(W0, stream, lbm_sw, torch, jobs: int = 3):
+    """Whole jobs through the public API with pinned host buffers: upload W0
+    (lbm_sw_set_state from host), 1000 steps, download (h, hu, hv) (lbm_sw_get_moments
+    to host).  One e2e step = one job."""
+    pinned = [torch.empty((N, N), dtype=torch.float64, pin_memory=True) for _ in range(6)]
+    src = [p.numpy() for p in pinned[:3]]
+    dst = [p.numpy() for p in pinned[3:]]
+    for s, w in zip(src, W0):
+        s[...] = w
+    sim = lbm_sw.Simulation(N, N, precision=lbm_sw.FP32, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream)
+    sim.set_state(*src)
+    sim.step(10)
+    sim.moments_into(*dst)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(jobs):
+        sim.set_state(*src)
+        sim.step(JOB_STEPS)
+        sim.moments_into(*dst)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    sim.close()
+    nbytes = 3 * N * N * 8
+    return {"value": N * N * JOB_STEPS * jobs / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "step": f"one job: upload W0, {JOB_STEPS} steps, download W",
+            "lb_steps_per_step": JOB_STEPS, "jobs": jobs, "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--quick", action="store_true", help="timed loop only (no variants, e2e, CPU baseline)")
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
+    ap.add_argument("--side", type=int, default=4096, help="grid side (profiling of smaller cases only)")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
+                    help="population precision of the timed loop (fp32 is the workload)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * lbm_sw.h — C ABI of the GB300 (sm_103a) library for the vectorial lattice
+ * Boltzmann schemes of F. Dubois, "Simulation of strong nonlinear waves with
+ * vectorial lattice Boltzmann schemes" (DSFD 2013), applied to the shallow-water
+ * equations:
+ *
+ *   1D: the D1Q3Q2 scheme of section 2 — populations f on D1Q3 (velocities
+ *       0, +lambda, -lambda) carry the depth h, populations g on D1Q2
+ *       (+lambda, -lambda) carry the discharge h u.
+ *   2D: the D2Q5Q4Q4 scheme of section 3 — f on D2Q5 (Eq. 3-stencil-d2q5),
+ *       gx and gy on D2Q4 (no rest population), carrying h, h u and h v.
+ *
+ * Equilibria are the derivatives of the potentials h_j^* of the kinetic
+ * decomposition of the dual entropy (section 1; Eqs. 2-potentiels-st-venant-1d,
+ * 2-potentiels-st-venant-1d-suite, 3-st-venant-contraintes-2, 3-st-venant-enplus),
+ * with p = g h^2 / 2 (the gamma = 2 system), and the collision is the BGK form of
+ * Eq. 2-relaxation (every rate equal to s).  Streaming moves each population one
+ * cell per step (lambda = dx/dt).
+ *
+ * Every compute step runs in hand-written CUDA kernels on the caller's stream;
+ * there is no CPU fallback.  No function throws; every function that can fail
+ * returns a status code (LBM_SW_OK = 0 or a negative LBM_SW_E_*), and the handle
+ * keeps a message for the last failure (lbm_sw_last_error).  Many handles may
+ * coexist; the library keeps no global state.
+ *
+ * Layouts at this boundary
+ *   - Moment fields (h, hu, hv) are FP64 arrays of nx*ny values, row-major
+ *     [ny][nx], x fastest, in either precision mode (conversion happens on the
+ *     device).  In 1D, ny = 1 and hv is ignored (may be NULL).
+ *   - Raw populations are dense planes [q][ny][nx] of the handle's precision
+ *     (float or double), q = 5 in 1D (f0, f+, f-, g+, g-) and 13 in 2D
+ *     (f0 f1 f2 f3 f4 gx1 gx2 gx3 gx4 gy1 gy2 gy3 gy4, v1 = (lambda,0),
+ *     v2 = (0,lambda), v3 = (-lambda,0), v4 = (0,-lambda)).
+ *   - "on_device" = 1: the pointer is device memory of the current CUDA device
+ *     (e.g. a torch tensor's data_ptr), 0: host memory (pageable or pinned).
+ *     Caller-owned in both cases; the library never frees caller memory.
+ *
+ * State convention: the library stores post-collision populations, the values
+ * that stream out of each cell at the next step.  A collision conserves h, h u
+ * and h v, so the moments of the stored state are those of the current time
+ * level.
+ */
+#ifndef LBM_SW_H
+#define LBM_SW_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_SW_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define LBM_SW_API __attribute__((visibility("default")))
+#else
+#define LBM_SW_API
+#endif
+
+/* Opaque handle: one simulation (parameters, two device population buffers, the
+ * caller's stream, scratch for reductions).  Owned by the library; create with
+ * lbm_sw_create, release with lbm_sw_destroy. */
+typedef struct lbm_sw lbm_sw;
+
+/* ---- status codes ---- */
+#define LBM_SW_OK 0
+#define LBM_SW_E_ARG (-1)      /* invalid argument (NULL, size, parameter out of range) */
+#define LBM_SW_E_CUDA (-2)     /* a CUDA call failed; see lbm_sw_last_error */
+#define LBM_SW_E_UNSTABLE (-3) /* a diagnostic found NaN/Inf or a depth h <= 0 */
+#define LBM_SW_E_TIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define LBM_SW_E_STATE (-5)    /* call not valid in the handle's state (e.g. no state set) */
+#define LBM_SW_E_NOMEM (-6)    /* device allocation failed */
+
+/* ---- boundary kinds (section 3, last paragraph: bounce-back and anti-bounce-back) ----
+ * The ghost cell beyond a side holds
+ *   PERIODIC: the cell on the opposite side (the opposite side must be PERIODIC too);
+ *   WALL:     the mirror image of the boundary cell: the incoming population takes
+ *             the post-collision value of its reflected partner at the same cell,
+ *             with the momentum family normal to the wall negated (slip wall, zero
+ *             normal flux, exact mass conservation);
+ *   OUTFLOW:  a copy of the boundary cell (zero-gradient open boundary);
+ *   INFLOW:   the equilibrium of the prescribed state inflow[side] = (h, hu, hv). */
+#define LBM_SW_BC_PERIODIC 0
+#define LBM_SW_BC_WALL 1
+#define LBM_SW_BC_OUTFLOW 2
+#define LBM_SW_BC_INFLOW 3
+
+/* sides, in the order of lbm_sw_params.bc */
+#define LBM_SW_SIDE_XM 0
+#define LBM_SW_SIDE_XP 1
+#define LBM_SW_SIDE_YM 2
+#define LBM_SW_SIDE_YP 3
+
+/* storage and arithmetic precision of the populations */
+#define LBM_SW_FP32 0
+#define LBM_SW_FP64 1
+
+/* form of populations handed to lbm_sw_set_populations */
+#define LBM_SW_POST_COLLISION 0 /* stored as given */
+#define LBM_SW_PRE_COLLISION 1  /* collided on the device first (moments, equilibria, relaxation) */
+
+/* 2D step kernel variants */
+#define LBM_SW_KERNEL_AUTO 0   /* library choice (currently VEC) */
+#define LBM_SW_KERNEL_SIMPLE 1 /* one thread per cell, scalar loads */
+#define LBM_SW_KERNEL_VEC 2    /* 16-byte vectors along x (4 FP32 or 2 FP64 cells per thread),
+                                  x-neighbours exchanged with warp shuffles */
+
+typedef struct lbm_sw_params {
+  int dim;             /* 1 (D1Q3Q2) or 2 (D2Q5Q4Q4) */
+  int nx, ny;          /* cells; ny must be 1 when dim == 1; nx, ny >= 1 */
+  int precision;       /* LBM_SW_FP32 or LBM_SW_FP64 */
+  double g;            /* gravity, > 0 (p = g h^2 / 2) */
+  double lambda;       /* lattice velocity dx/dt, > 0 */
+  double s;            /* BGK relaxation rate, 0 <= s < 2 */
+  double a;            /* weight of the rest potential h_0^* = (a/2) K theta^2, >= 0 */
+  int bc[4];           /* LBM_SW_BC_* for sides x-, x+, y-, y+ (y sides unused in 1D) */
+  double inflow[4][3]; /* (h, hu, hv) imposed on INFLOW sides */
+  void* stream;        /* cudaStream_t borrowed from the caller (NULL = legacy default) */
+  int kernel;          /* LBM_SW_KERNEL_* (2D only) */
+  int graph_chunk;     /* steps per captured CUDA graph in lbm_sw_step; 0 = default, < 0 = off */
+  int reserved[6];     /* must be zero */
+} lbm_sw_params;
+
+typedef struct lbm_sw_info {
+  int q;                     /* populations per cell: 5 (1D) or 13 (2D) */
+  int kernel;                /* step kernel variant in use */
+  size_t pitch;              /* elements per stored row (multiple of 32) */
+  size_t population_bytes;   /* bytes of one dense population set, q * nx * ny * sizeof(T) */
+  double bytes_per_update;   /* algorithmic DRAM bytes per lattice-cell update: 2 q sizeof(T) */
+  long long steps_done;      /* steps taken since the last set_state / set_populations */
+  long long kernel_launches; /* kernels this handle has launched */
+} lbm_sw_info;
+
+/* Fill *p with defaults: dim 2, FP32, g = 1, lambda = 8, s = 1.8, a = 0.05,
+ * periodic sides, NULL stream, automatic kernel choice, nx = ny = 0 (must be set).
+ * Returns LBM_SW_E_ARG if p is NULL. */
+LBM_SW_API int lbm_sw_params_init(lbm_sw_params* p);
+
+/* Validate *p, allocate two pitched population buffers (double buffering, 256-byte
+ * aligned planes) on the current device, and return a handle in *out.  The
+ * populations start undefined: call lbm_sw_set_state or lbm_sw_set_populations.
+ * Errors: LBM_SW_E_ARG (NULL, sizes, parameter ranges, mismatched periodic sides,
+ * nonzero reserved fields), LBM_SW_E_NOMEM, LBM_SW_E_CUDA; *out is then NULL. */
+LBM_SW_API int lbm_sw_create(const lbm_sw_params* p, lbm_sw** out);
+
+/* Release the handle and its device memory (synchronises its stream). NULL-safe. */
+LBM_SW_API void lbm_sw_destroy(lbm_sw* h);
+
+/* Set the populations to the equilibrium of W = (h, hu, hv) (paper: the state at
+ * t = 0 is taken at equilibrium, f = f^eq(W)).  Arrays: FP64 [ny][nx]; hv ignored in
+ * 1D.  Host arrays are copied before return; device arrays must stay valid until the
+ * stream reaches this work.  Errors: LBM_SW_E_ARG, LBM_SW_E_CUDA. */
+LBM_SW_API int lbm_sw_set_state(lbm_sw* h, const double* depth, const double* hu, const double* hv, int on_device);
+
+/* Advance n >= 0 time steps, each one fused pull-stream + collide kernel (streaming
+ * with the boundary rules, moments, equilibria, relaxation), asynchronously on the
+ * handle's stream; long runs replay a captured CUDA graph of graph_chunk steps.
+ * Errors: LBM_SW_E_ARG (n < 0), LBM_SW_E_STATE (no state set), LBM_SW_E_CUDA
+ * (launch failure; kernel faults surface at the next synchronising call). */
+LBM_SW_API int lbm_sw_step(lbm_sw* h, int n);
+
+/* Write the conserved moments (h = sum f, hu = sum gx, hv = sum gy; Eq.
+ * 1-hyp-N-vconserv) of the current state as FP64 [ny][nx] arrays.  With host
+ * arrays the call synchronises; with device arrays it is asynchronous on the stream.
+ * hv may be NULL (and is ignored in 1D). */
+LBM_SW_API int lbm_sw_get_moments(lbm_sw* h, double* depth, double* hu, double* hv, int on_device);
+
+/* Reduce the current state on the device (FP64 accumulation, warp shuffles, then a
+ * fixed-order second pass) and synchronise: out[0] = sum h, out[1] = sum hu,
+ * out[2] = sum hv (0 in 1D), out[3] = min h.  Returns LBM_SW_E_UNSTABLE when any
+ * cell holds NaN/Inf or h <= 0 (out is still written). */
+LBM_SW_API int lbm_sw_diagnostics(lbm_sw* h, double out[4]);
+
+/* Copy the stored (post-collision) populations out as dense planes [q][ny][nx] of
+ * the handle's precision; lbm_sw_get_info gives the byte count.  Synchronises for
+ * host memory. */
+LBM_SW_API int lbm_sw_get_populations(lbm_sw* h, void* dst, int on_device);
+
+/* Load dense planes [q][ny][nx] of the handle's precision.  form =
+ * LBM_SW_POST_COLLISION stores them as they are (a checkpoint written by
+ * lbm_sw_get_populations); LBM_SW_PRE_COLLISION collides them on the device first,
+ * so that the next step streams their post-collision values. */
+LBM_SW_API int lbm_sw_set_populations(lbm_sw* h, const void* src, int on_device, int form);
+
+/* Wait for all work queued by the handle; returns LBM_SW_E_CUDA on a kernel fault. */
+LBM_SW_API int lbm_sw_synchronize(lbm_sw* h);
+
+/* Sizes and counters of the handle. */
+LBM_SW_API int lbm_sw_get_info(const lbm_sw* h, lbm_sw_info* out);
+
+/* Message of the last failure on this handle ("" if none); valid until the next call. */
+LBM_SW_API const char* lbm_sw_last_error(const lbm_sw* h);
+
+/* Message of the last failed lbm_sw_create on the calling thread ("" if it succeeded). */
+LBM_SW_API const char* lbm_sw_create_error(void);
+
+/* Static text for a status code. */
+LBM_SW_API const char* lbm_sw_status_string(int status);
+
+/* LBM_SW_ABI_VERSION of the loaded library. */
+LBM_SW_API int lbm_sw_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_SW_H */

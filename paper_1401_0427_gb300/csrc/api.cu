@@ -1,0 +1,423 @@
+// C ABI of the library (declarations and contracts in include/lbm_sw.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace {
+
+int fail(lbm_sw* h, int code, const char* fmt, ...) {
+  if (h) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    h->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(lbm_sw* h, cudaError_t e, const char* what) {
+  return fail(h, e == cudaErrorMemoryAllocation ? LBM_SW_E_NOMEM : LBM_SW_E_CUDA, "%s: %s (%s)", what,
+              cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define LBM_CUDA(h, call, what)                       \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+  } while (0)
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+size_t state_bytes(const lbm_sw* h) { return static_cast<size_t>(h->q) * h->plane * h->elem; }
+
+template <class T>
+lbm::StepArgs<T> args(const lbm_sw* h, int src_buf) {
+  lbm::StepArgs<T> a;
+  a.src = static_cast<const T*>(h->buf[src_buf]);
+  a.dst = static_cast<T*>(h->buf[1 - src_buf]);
+  a.inflow_feq = static_cast<const T*>(h->inflow_feq);
+  a.nx = h->p.nx;
+  a.ny = h->p.ny;
+  a.pitch = h->pitch;
+  a.plane = h->plane;
+  for (int s = 0; s < 4; ++s) a.bc[s] = h->p.bc[s];
+  return a;
+}
+
+lbm::ConstsD consts(const lbm_sw* h) { return lbm::ConstsD{h->p.g, h->p.lambda, h->p.s, h->p.a}; }
+
+// One step from buffer `from` into the other buffer, on stream st.
+cudaError_t launch_one_step(lbm_sw* h, int from, cudaStream_t st) {
+  if (h->p.precision == LBM_SW_FP64) {
+    auto a = args<double>(h, from);
+    return h->p.dim == 1 ? lbm::launch_step1d<double>(a, consts(h), st)
+                         : lbm::launch_step2d<double>(a, consts(h), h->kernel, st);
+  }
+  auto a = args<float>(h, from);
+  return h->p.dim == 1 ? lbm::launch_step1d<float>(a, consts(h), st)
+                       : lbm::launch_step2d<float>(a, consts(h), h->kernel, st);
+}
+
+// Capture graph_chunk steps starting from buffer `from` (graph_chunk is even, so the
+// chunk ends in the buffer it started from).
+int build_graph(lbm_sw* h, int from) {
+  if (!h->capture_stream)
+    LBM_CUDA(h, cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  LBM_CUDA(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  cudaError_t le = cudaSuccess;
+  int b = from;
+  for (int i = 0; i < h->graph_chunk && le == cudaSuccess; ++i, b ^= 1) le = launch_one_step(h, b, h->capture_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(h->capture_stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(h, le, "step launch during graph capture");
+  }
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaStreamEndCapture");
+  cudaError_t ie = cudaGraphInstantiate(&h->graph[from], g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return cuda_fail(h, ie, "cudaGraphInstantiate");
+  return LBM_SW_OK;
+}
+
+int validate(const lbm_sw_params* p, lbm_sw* h) {
+  if (p->dim != 1 && p->dim != 2) return fail(h, LBM_SW_E_ARG, "dim must be 1 or 2 (got %d)", p->dim);
+  if (p->nx < 1 || p->ny < 1) return fail(h, LBM_SW_E_ARG, "nx and ny must be >= 1 (got %d, %d)", p->nx, p->ny);
+  if (p->dim == 1 && p->ny != 1) return fail(h, LBM_SW_E_ARG, "ny must be 1 when dim == 1");
+  if (p->nx > (1 << 30) || p->ny > (1 << 30)) return fail(h, LBM_SW_E_ARG, "nx, ny must be <= 2^30");
+  if (p->precision != LBM_SW_FP32 && p->precision != LBM_SW_FP64)
+    return fail(h, LBM_SW_E_ARG, "precision must be LBM_SW_FP32 or LBM_SW_FP64");
+  if (!(p->g > 0) || !std::isfinite(p->g)) return fail(h, LBM_SW_E_ARG, "g must be finite and > 0");
+  if (!(p->lambda > 0) || !std::isfinite(p->lambda)) return fail(h, LBM_SW_E_ARG, "lambda must be finite and > 0");
+  if (!(p->s >= 0 && p->s < 2)) return fail(h, LBM_SW_E_ARG, "s must be in [0, 2)");
+  if (!(p->a >= 0) || !std::isfinite(p->a)) return fail(h, LBM_SW_E_ARG, "a must be finite and >= 0");
+  const int nsides = p->dim == 1 ? 2 : 4;
+  for (int s = 0; s < nsides; ++s) {
+    if (p->bc[s] < LBM_SW_BC_PERIODIC || p->bc[s] > LBM_SW_BC_INFLOW)
+      return fail(h, LBM_SW_E_ARG, "bc[%d] = %d is not a LBM_SW_BC_* value", s, p->bc[s]);
+    if (p->bc[s] == LBM_SW_BC_INFLOW) {
+      if (!(p->inflow[s][0] > 0) || !std::isfinite(p->inflow[s][0]) || !std::isfinite(p->inflow[s][1]) ||
+          !std::isfinite(p->inflow[s][2]))
+        return fail(h, LBM_SW_E_ARG, "inflow[%d] must be finite with depth > 0", s);
+    }
+  }
+  for (int pair = 0; pair < nsides; pair += 2)
+    if ((p->bc[pair] == LBM_SW_BC_PERIODIC) != (p->bc[pair + 1] == LBM_SW_BC_PERIODIC))
+      return fail(h, LBM_SW_E_ARG, "periodic sides come in pairs (bc[%d], bc[%d])", pair, pair + 1);
+  if (p->kernel < LBM_SW_KERNEL_AUTO || p->kernel > LBM_SW_KERNEL_VEC)
+    return fail(h, LBM_SW_E_ARG, "kernel must be a LBM_SW_KERNEL_* value");
+  for (int r = 0; r < 6; ++r)
+    if (p->reserved[r] != 0) return fail(h, LBM_SW_E_ARG, "reserved fields must be zero");
+  return LBM_SW_OK;
+}
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+extern "C" {
+
+int lbm_sw_abi_version(void) { return LBM_SW_ABI_VERSION; }
+
+const char* lbm_sw_status_string(int status) {
+  switch (status) {
+    case LBM_SW_OK: return "ok";
+    case LBM_SW_E_ARG: return "invalid argument";
+    case LBM_SW_E_CUDA: return "CUDA error";
+    case LBM_SW_E_UNSTABLE: return "unstable state (NaN/Inf or depth <= 0)";
+    case LBM_SW_E_TIMEOUT: return "bounded device wait timed out";
+    case LBM_SW_E_STATE: return "call not valid in the current state";
+    case LBM_SW_E_NOMEM: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+int lbm_sw_params_init(lbm_sw_params* p) {
+  if (!p) return LBM_SW_E_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->dim = 2;
+  p->precision = LBM_SW_FP32;
+  p->g = 1.0;
+  p->lambda = 8.0;
+  p->s = 1.8;
+  p->a = 0.05;
+  for (int s = 0; s < 4; ++s) {
+    p->bc[s] = LBM_SW_BC_PERIODIC;
+    p->inflow[s][0] = 1.0;
+  }
+  p->kernel = LBM_SW_KERNEL_AUTO;
+  return LBM_SW_OK;
+}
+
+const char* lbm_sw_last_error(const lbm_sw* h) { return h ? h->err.c_str() : "null handle"; }
+
+const char* lbm_sw_create_error(void) { return g_create_error.c_str(); }
+
+void lbm_sw_destroy(lbm_sw* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (int i = 0; i < 2; ++i) {
+    if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+    if (h->buf[i]) cudaFree(h->buf[i]);
+  }
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  if (h->inflow_feq) cudaFree(h->inflow_feq);
+  if (h->moments_staging) cudaFree(h->moments_staging);
+  if (h->pop_staging) cudaFree(h->pop_staging);
+  if (h->diag_partials) cudaFree(h->diag_partials);
+  if (h->diag_out) cudaFree(h->diag_out);
+  if (h->diag_host) cudaFreeHost(h->diag_host);
+  delete h;
+}
+
+int lbm_sw_create(const lbm_sw_params* p, lbm_sw** out) {
+  if (!out) return LBM_SW_E_ARG;
+  *out = nullptr;
+  if (!p) return LBM_SW_E_ARG;
+  lbm_sw* h = new (std::nothrow) lbm_sw;
+  if (!h) return LBM_SW_E_NOMEM;
+  g_create_error.clear();
+  int rc = validate(p, h);
+  if (rc != LBM_SW_OK) {
+    g_create_error = h->err;  // the handle is not returned: keep the message per thread
+    delete h;
+    return rc;
+  }
+  h->p = *p;
+  h->stream = static_cast<cudaStream_t>(p->stream);
+  h->q = p->dim == 1 ? 5 : 13;
+  h->elem = p->precision == LBM_SW_FP64 ? 8 : 4;
+  h->pitch = round_up(p->nx, 32);
+  h->plane = round_up(h->pitch * p->ny, 64);  // 256-byte aligned planes in FP32 and FP64
+  h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? LBM_SW_KERNEL_VEC : p->kernel;
+  h->graph_chunk = p->graph_chunk == 0 ? 64 : (p->graph_chunk < 0 ? 0 : p->graph_chunk + (p->graph_chunk & 1));
+
+  auto bail = [&](int code) {
+    g_create_error = std::string("create: ") + lbm_sw_status_string(code) + ": " +
+                     cudaGetErrorString(cudaGetLastError());
+    lbm_sw_destroy(h);
+    return code;
+  };
+  if (cudaGetDevice(&h->device) != cudaSuccess) return bail(LBM_SW_E_CUDA);
+  const size_t bytes = state_bytes(h);
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMalloc(&h->buf[i], bytes) != cudaSuccess) return bail(LBM_SW_E_NOMEM);
+    if (cudaMemsetAsync(h->buf[i], 0, bytes, h->stream) != cudaSuccess) return bail(LBM_SW_E_CUDA);
+  }
+  if (cudaMalloc(&h->inflow_feq, 4 * h->q * h->elem) != cudaSuccess) return bail(LBM_SW_E_NOMEM);
+  if (cudaMalloc(&h->diag_partials, 5 * sizeof(double) * lbm::diag_max_blocks()) != cudaSuccess)
+    return bail(LBM_SW_E_NOMEM);
+  if (cudaMalloc(&h->diag_out, 8 * sizeof(double)) != cudaSuccess) return bail(LBM_SW_E_NOMEM);
+  if (cudaMallocHost(&h->diag_host, 8 * sizeof(double)) != cudaSuccess) return bail(LBM_SW_E_NOMEM);
+  cudaError_t e;
+  if (p->precision == LBM_SW_FP64)
+    e = p->dim == 1 ? lbm::launch_inflow_feq1d<double>(static_cast<double*>(h->inflow_feq), p->bc, p->inflow, consts(h), h->stream)
+                    : lbm::launch_inflow_feq2d<double>(static_cast<double*>(h->inflow_feq), p->bc, p->inflow, consts(h), h->stream);
+  else
+    e = p->dim == 1 ? lbm::launch_inflow_feq1d<float>(static_cast<float*>(h->inflow_feq), p->bc, p->inflow, consts(h), h->stream)
+                    : lbm::launch_inflow_feq2d<float>(static_cast<float*>(h->inflow_feq), p->bc, p->inflow, consts(h), h->stream);
+  if (e != cudaSuccess) return bail(LBM_SW_E_CUDA);
+  h->launches += 1;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(LBM_SW_E_CUDA);
+  *out = h;
+  return LBM_SW_OK;
+}
+
+int lbm_sw_set_state(lbm_sw* h, const double* depth, const double* hu, const double* hv, int on_device) {
+  if (!h) return LBM_SW_E_ARG;
+  if (!depth || !hu || (h->p.dim == 2 && !hv && on_device))
+    return fail(h, LBM_SW_E_ARG, "set_state: depth and hu are required (and hv for device input in 2D)");
+  const size_t n = static_cast<size_t>(h->p.nx) * h->p.ny;
+  const double *d = depth, *u = hu, *v = (h->p.dim == 2) ? hv : nullptr;
+  if (!on_device) {
+    if (!h->moments_staging)
+      LBM_CUDA(h, cudaMalloc(&h->moments_staging, 3 * n * sizeof(double)), "cudaMalloc(moments staging)");
+    double* s = h->moments_staging;
+    LBM_CUDA(h, cudaMemcpyAsync(s, depth, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy h");
+    LBM_CUDA(h, cudaMemcpyAsync(s + n, hu, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy hu");
+    if (h->p.dim == 2) {
+      if (hv)
+        LBM_CUDA(h, cudaMemcpyAsync(s + 2 * n, hv, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy hv");
+      else
+        LBM_CUDA(h, cudaMemsetAsync(s + 2 * n, 0, n * sizeof(double), h->stream), "zero hv");
+    }
+    d = s;
+    u = s + n;
+    v = h->p.dim == 2 ? s + 2 * n : nullptr;
+  }
+  cudaError_t e;
+  // the equilibrium is written into the current buffer (as the destination of "args")
+  const int from = 1 - h->cur;
+  if (h->p.precision == LBM_SW_FP64)
+    e = h->p.dim == 1 ? lbm::launch_init1d<double>(args<double>(h, from), consts(h), d, u, h->stream)
+                      : lbm::launch_init2d<double>(args<double>(h, from), consts(h), d, u, v, h->stream);
+  else
+    e = h->p.dim == 1 ? lbm::launch_init1d<float>(args<float>(h, from), consts(h), d, u, h->stream)
+                      : lbm::launch_init2d<float>(args<float>(h, from), consts(h), d, u, v, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state kernel launch");
+  h->launches += 1;
+  if (!on_device) LBM_CUDA(h, cudaStreamSynchronize(h->stream), "set_state synchronize");
+  h->has_state = true;
+  h->steps_done = 0;
+  return LBM_SW_OK;
+}
+
+int lbm_sw_step(lbm_sw* h, int n) {
+  if (!h) return LBM_SW_E_ARG;
+  if (n < 0) return fail(h, LBM_SW_E_ARG, "step: n must be >= 0 (got %d)", n);
+  if (!h->has_state) return fail(h, LBM_SW_E_STATE, "step: no state set (call set_state or set_populations)");
+  while (n > 0) {
+    if (h->graph_chunk > 0 && n >= h->graph_chunk) {
+      if (!h->graph[h->cur]) {
+        int rc = build_graph(h, h->cur);
+        if (rc != LBM_SW_OK) return rc;
+      }
+      LBM_CUDA(h, cudaGraphLaunch(h->graph[h->cur], h->stream), "cudaGraphLaunch");
+      n -= h->graph_chunk;
+      h->steps_done += h->graph_chunk;
+      h->launches += h->graph_chunk;
+    } else {
+      cudaError_t e = launch_one_step(h, h->cur, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
+      h->cur ^= 1;
+      n -= 1;
+      h->steps_done += 1;
+      h->launches += 1;
+    }
+  }
+  return LBM_SW_OK;
+}
+
+int lbm_sw_get_moments(lbm_sw* h, double* depth, double* hu, double* hv, int on_device) {
+  if (!h) return LBM_SW_E_ARG;
+  if (!depth || !hu) return fail(h, LBM_SW_E_ARG, "get_moments: depth and hu are required");
+  if (!h->has_state) return fail(h, LBM_SW_E_STATE, "get_moments: no state set");
+  const size_t n = static_cast<size_t>(h->p.nx) * h->p.ny;
+  double *d = depth, *u = hu, *v = (h->p.dim == 2) ? hv : nullptr;
+  if (!on_device) {
+    if (!h->moments_staging)
+      LBM_CUDA(h, cudaMalloc(&h->moments_staging, 3 * n * sizeof(double)), "cudaMalloc(moments staging)");
+    d = h->moments_staging;
+    u = d + n;
+    v = (h->p.dim == 2 && hv) ? d + 2 * n : nullptr;
+  }
+  cudaError_t e;
+  const int from = h->cur;
+  if (h->p.precision == LBM_SW_FP64)
+    e = h->p.dim == 1 ? lbm::launch_moments1d<double>(args<double>(h, from), d, u, h->stream)
+                      : lbm::launch_moments2d<double>(args<double>(h, from), d, u, v, h->stream);
+  else
+    e = h->p.dim == 1 ? lbm::launch_moments1d<float>(args<float>(h, from), d, u, h->stream)
+                      : lbm::launch_moments2d<float>(args<float>(h, from), d, u, v, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel launch");
+  h->launches += 1;
+  if (!on_device) {
+    LBM_CUDA(h, cudaMemcpyAsync(depth, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy h");
+    LBM_CUDA(h, cudaMemcpyAsync(hu, u, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy hu");
+    if (v) LBM_CUDA(h, cudaMemcpyAsync(hv, v, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy hv");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "get_moments synchronize");
+  }
+  return LBM_SW_OK;
+}
+
+int lbm_sw_diagnostics(lbm_sw* h, double out[4]) {
+  if (!h || !out) return h ? fail(h, LBM_SW_E_ARG, "diagnostics: out is NULL") : LBM_SW_E_ARG;
+  if (!h->has_state) return fail(h, LBM_SW_E_STATE, "diagnostics: no state set");
+  cudaError_t e = h->p.precision == LBM_SW_FP64
+                      ? lbm::launch_diagnostics<double>(args<double>(h, h->cur), h->q, h->diag_partials, h->diag_out, h->stream)
+                      : lbm::launch_diagnostics<float>(args<float>(h, h->cur), h->q, h->diag_partials, h->diag_out, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics kernel launch");
+  h->launches += 2;
+  LBM_CUDA(h, cudaMemcpyAsync(h->diag_host, h->diag_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+           "copy diagnostics");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "diagnostics synchronize");
+  for (int k = 0; k < 4; ++k) out[k] = h->diag_host[k];
+  if (h->diag_host[4] > 0)
+    return fail(h, LBM_SW_E_UNSTABLE, "diagnostics: %.0f cells with NaN/Inf or depth <= 0", h->diag_host[4]);
+  return LBM_SW_OK;
+}
+
+int lbm_sw_get_populations(lbm_sw* h, void* dst, int on_device) {
+  if (!h) return LBM_SW_E_ARG;
+  if (!dst) return fail(h, LBM_SW_E_ARG, "get_populations: dst is NULL");
+  if (!h->has_state) return fail(h, LBM_SW_E_STATE, "get_populations: no state set");
+  const size_t row = static_cast<size_t>(h->p.nx) * h->elem;
+  const size_t dplane = row * h->p.ny;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const char* src = static_cast<const char*>(h->buf[h->cur]);
+  for (int p = 0; p < h->q; ++p)
+    LBM_CUDA(h, cudaMemcpy2DAsync(static_cast<char*>(dst) + p * dplane, row, src + p * h->plane * h->elem,
+                                  h->pitch * h->elem, row, h->p.ny, kind, h->stream),
+             "copy populations out");
+  if (!on_device) LBM_CUDA(h, cudaStreamSynchronize(h->stream), "get_populations synchronize");
+  return LBM_SW_OK;
+}
+
+int lbm_sw_set_populations(lbm_sw* h, const void* src, int on_device, int form) {
+  if (!h) return LBM_SW_E_ARG;
+  if (!src) return fail(h, LBM_SW_E_ARG, "set_populations: src is NULL");
+  if (form != LBM_SW_POST_COLLISION && form != LBM_SW_PRE_COLLISION)
+    return fail(h, LBM_SW_E_ARG, "set_populations: form must be LBM_SW_POST_COLLISION or LBM_SW_PRE_COLLISION");
+  const size_t row = static_cast<size_t>(h->p.nx) * h->elem;
+  const size_t dplane = row * h->p.ny;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (form == LBM_SW_POST_COLLISION) {
+    char* dst = static_cast<char*>(h->buf[h->cur]);
+    for (int p = 0; p < h->q; ++p)
+      LBM_CUDA(h, cudaMemcpy2DAsync(dst + p * h->plane * h->elem, h->pitch * h->elem,
+                                    static_cast<const char*>(src) + p * dplane, row, row, h->p.ny, kind, h->stream),
+               "copy populations in");
+  } else {
+    const void* dense = src;
+    if (!on_device) {
+      if (!h->pop_staging)
+        LBM_CUDA(h, cudaMalloc(&h->pop_staging, h->q * dplane), "cudaMalloc(population staging)");
+      LBM_CUDA(h, cudaMemcpyAsync(h->pop_staging, src, h->q * dplane, cudaMemcpyHostToDevice, h->stream),
+               "copy populations in");
+      dense = h->pop_staging;
+    }
+    const int from = 1 - h->cur;  // write into the current buffer
+    cudaError_t e;
+    if (h->p.precision == LBM_SW_FP64)
+      e = h->p.dim == 1 ? lbm::launch_collide1d_dense<double>(args<double>(h, from), consts(h), static_cast<const double*>(dense), h->stream)
+                        : lbm::launch_collide2d_dense<double>(args<double>(h, from), consts(h), static_cast<const double*>(dense), h->stream);
+    else
+      e = h->p.dim == 1 ? lbm::launch_collide1d_dense<float>(args<float>(h, from), consts(h), static_cast<const float*>(dense), h->stream)
+                        : lbm::launch_collide2d_dense<float>(args<float>(h, from), consts(h), static_cast<const float*>(dense), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "collide kernel launch");
+    h->launches += 1;
+  }
+  if (!on_device) LBM_CUDA(h, cudaStreamSynchronize(h->stream), "set_populations synchronize");
+  h->has_state = true;
+  h->steps_done = 0;
+  return LBM_SW_OK;
+}
+
+int lbm_sw_synchronize(lbm_sw* h) {
+  if (!h) return LBM_SW_E_ARG;
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+  return LBM_SW_OK;
+}
+
+int lbm_sw_get_info(const lbm_sw* h, lbm_sw_info* out) {
+  if (!h || !out) return LBM_SW_E_ARG;
+  out->q = h->q;
+  out->kernel = h->p.dim == 1 ? LBM_SW_KERNEL_SIMPLE : h->kernel;
+  out->pitch = static_cast<size_t>(h->pitch);
+  out->population_bytes = static_cast<size_t>(h->q) * h->p.nx * h->p.ny * h->elem;
+  out->bytes_per_update = 2.0 * h->q * static_cast<double>(h->elem);
+  out->steps_done = h->steps_done;
+  out->kernel_launches = h->launches;
+  return LBM_SW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// Internal declarations shared by the library's translation units (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/lbm_sw.h"
+
+namespace lbm {
+
+// Direction of each 2D population: 0 rest, 1 +x, 2 +y, 3 -x, 4 -y (Eq. 3-stencil-d2q5).
+// Plane p of family k (f: 0..4, gx: 5..8, gy: 9..12) with direction d has index
+// p = d for f and p = 4 + d (gx), 8 + d (gy).
+
+// Kernel arguments of one fused step (and of the helpers that read/write states).
+template <class T>
+struct StepArgs {
+  const T* __restrict__ src;  // post-collision populations at time n (pitched planes)
+  T* __restrict__ dst;        // post-collision populations at time n + 1
+  const T* inflow_feq;        // [4][q] equilibrium of each INFLOW side (device)
+  int nx, ny;
+  long long pitch;            // elements per row
+  long long plane;            // elements per plane (pitch * ny)
+  int bc[4];
+};
+
+struct ConstsD {  // scheme constants before conversion to T
+  double g, lambda, s, a;
+};
+
+// ---- 2D launchers (kernels_2d.cu) ----
+template <class T>
+cudaError_t launch_step2d(const StepArgs<T>& a, const ConstsD& k, int variant, cudaStream_t st);
+template <class T>
+cudaError_t launch_init2d(const StepArgs<T>& a, const ConstsD& k, const double* h, const double* hu,
+                          const double* hv, cudaStream_t st);
+template <class T>
+cudaError_t launch_collide2d_dense(const StepArgs<T>& a, const ConstsD& k, const T* dense, cudaStream_t st);
+template <class T>
+cudaError_t launch_moments2d(const StepArgs<T>& a, double* h, double* hu, double* hv, cudaStream_t st);
+template <class T>
+cudaError_t launch_inflow_feq2d(T* out, const int bc[4], const double inflow[4][3], const ConstsD& k,
+                                cudaStream_t st);
+
+// ---- 1D launchers (kernels_1d.cu) ----
+template <class T>
+cudaError_t launch_step1d(const StepArgs<T>& a, const ConstsD& k, cudaStream_t st);
+template <class T>
+cudaError_t launch_init1d(const StepArgs<T>& a, const ConstsD& k, const double* h, const double* hu,
+                          cudaStream_t st);
+template <class T>
+cudaError_t launch_collide1d_dense(const StepArgs<T>& a, const ConstsD& k, const T* dense, cudaStream_t st);
+template <class T>
+cudaError_t launch_moments1d(const StepArgs<T>& a, double* h, double* hu, cudaStream_t st);
+template <class T>
+cudaError_t launch_inflow_feq1d(T* out, const int bc[4], const double inflow[4][3], const ConstsD& k,
+                                cudaStream_t st);
+
+// ---- reductions (reduce.cu) ----
+// Block partials (5 doubles each: sum h, sum hu, sum hv, min h, bad-cell count) then a
+// fixed-order final pass into out[5].  partials must hold diag_max_blocks() * 5 doubles.
+int diag_max_blocks();
+template <class T>
+cudaError_t launch_diagnostics(const StepArgs<T>& a, int q, double* partials, double* out, cudaStream_t st);
+
+}  // namespace lbm
+
+struct lbm_sw {
+  lbm_sw_params p{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int q = 13;
+  size_t elem = 4;          // sizeof(T)
+  long long pitch = 0;      // elements per row
+  long long plane = 0;      // elements per plane
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;              // buffer holding the current state
+  void* inflow_feq = nullptr;
+  double* moments_staging = nullptr;  // 3 * nx * ny doubles, for host transfers
+  void* pop_staging = nullptr;        // dense populations, for host transfers / collide
+  double* diag_partials = nullptr;
+  double* diag_out = nullptr;         // device, 8 doubles
+  double* diag_host = nullptr;        // pinned host, 8 doubles
+  int kernel = LBM_SW_KERNEL_VEC;
+  int graph_chunk = 64;
+  bool has_state = false;
+  long long steps_done = 0;
+  long long launches = 0;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // CUDA graph of graph_chunk steps from buffer 0 / 1
+  std::string err;
+};

@@ -1,0 +1,296 @@
+"""ctypes binding of the C ABI in ``include/lbm_sw.h`` (argument marshalling only).
+
+The functions keep the C names (``lbm_sw_create``, ``lbm_sw_set_state``,
+``lbm_sw_step``, ``lbm_sw_get_moments``, ``lbm_sw_destroy`` ...) and raise
+``LbmSwError`` on a negative status.  Every compute step runs in the CUDA library;
+loading fails loudly if ``liblbm_sw.so`` has not been built: there is no fallback.
+
+``Simulation`` is a convenience owner of one handle that moves numpy arrays or
+torch CUDA tensors across the boundary.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PERIODIC, WALL, OUTFLOW, INFLOW = 0, 1, 2, 3
+XM, XP, YM, YP = 0, 1, 2, 3
+FP32, FP64 = 0, 1
+POST_COLLISION, PRE_COLLISION = 0, 1
+KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_VEC = 0, 1, 2
+
+OK, E_ARG, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE, E_NOMEM = 0, -1, -2, -3, -4, -5, -6
+
+
+class LbmSwError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class lbm_sw_params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("nx", ctypes.c_int),
+        ("ny", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("g", ctypes.c_double),
+        ("lambda_", ctypes.c_double),
+        ("s", ctypes.c_double),
+        ("a", ctypes.c_double),
+        ("bc", ctypes.c_int * 4),
+        ("inflow", (ctypes.c_double * 3) * 4),
+        ("stream", ctypes.c_void_p),
+        ("kernel", ctypes.c_int),
+        ("graph_chunk", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
+    ]
+
+
+class lbm_sw_info(ctypes.Structure):
+    _fields_ = [
+        ("q", ctypes.c_int),
+        ("kernel", ctypes.c_int),
+        ("pitch", ctypes.c_size_t),
+        ("population_bytes", ctypes.c_size_t),
+        ("bytes_per_update", ctypes.c_double),
+        ("steps_done", ctypes.c_longlong),
+        ("kernel_launches", ctypes.c_longlong),
+    ]
+
+
+_lib = None
+
+# name -> (restype, argtypes); the complete list of entry points of include/lbm_sw.h
+_H = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "lbm_sw_params_init": (ctypes.c_int, [ctypes.POINTER(lbm_sw_params)]),
+    "lbm_sw_create": (ctypes.c_int, [ctypes.POINTER(lbm_sw_params), ctypes.POINTER(ctypes.c_void_p)]),
+    "lbm_sw_destroy": (None, [_H]),
+    "lbm_sw_set_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "lbm_sw_step": (ctypes.c_int, [_H, ctypes.c_int]),
+    "lbm_sw_get_moments": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "lbm_sw_diagnostics": (ctypes.c_int, [_H, _DP]),
+    "lbm_sw_get_populations": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
+    "lbm_sw_set_populations": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "lbm_sw_synchronize": (ctypes.c_int, [_H]),
+    "lbm_sw_get_info": (ctypes.c_int, [_H, ctypes.POINTER(lbm_sw_info)]),
+    "lbm_sw_last_error": (ctypes.c_char_p, [_H]),
+    "lbm_sw_create_error": (ctypes.c_char_p, []),
+    "lbm_sw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "lbm_sw_abi_version": (ctypes.c_int, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load liblbm_sw.so (built by ``__graft_entry__.build()`` / ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} is missing (run __graft_entry__.build()); "
+                          "the lattice Boltzmann path has no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, handle=None, what: str = "") -> int:
+    if status < 0:
+        lib = load()
+        msg = lib.lbm_sw_last_error(handle).decode() if handle else ""
+        if not msg:
+            msg = lib.lbm_sw_status_string(status).decode()
+        raise LbmSwError(status, f"{what}: {msg}" if what else msg)
+    return status
+
+
+# ---------------------------------------------------------------- C entry points
+def lbm_sw_params_init() -> lbm_sw_params:
+    p = lbm_sw_params()
+    _check(load().lbm_sw_params_init(ctypes.byref(p)))
+    return p
+
+
+def lbm_sw_create(p: lbm_sw_params) -> int:
+    lib = load()
+    h = ctypes.c_void_p()
+    st = lib.lbm_sw_create(ctypes.byref(p), ctypes.byref(h))
+    if st < 0:
+        raise LbmSwError(st, "lbm_sw_create: " + (lib.lbm_sw_create_error().decode() or lib.lbm_sw_status_string(st).decode()))
+    return h.value
+
+
+def lbm_sw_destroy(h: int) -> None:
+    load().lbm_sw_destroy(h)
+
+
+def lbm_sw_set_state(h: int, depth: int, hu: int, hv: int | None, on_device: bool) -> None:
+    _check(load().lbm_sw_set_state(h, depth, hu, hv, int(on_device)), h, "lbm_sw_set_state")
+
+
+def lbm_sw_step(h: int, n: int) -> None:
+    _check(load().lbm_sw_step(h, int(n)), h, "lbm_sw_step")
+
+
+def lbm_sw_get_moments(h: int, depth: int, hu: int, hv: int | None, on_device: bool) -> None:
+    _check(load().lbm_sw_get_moments(h, depth, hu, hv, int(on_device)), h, "lbm_sw_get_moments")
+
+
+def lbm_sw_diagnostics(h: int, raise_unstable: bool = True):
+    """Returns (sum h, sum hu, sum hv, min h, status)."""
+    out = (ctypes.c_double * 4)()
+    st = load().lbm_sw_diagnostics(h, out)
+    if st != E_UNSTABLE or raise_unstable:
+        _check(st, h, "lbm_sw_diagnostics")
+    return out[0], out[1], out[2], out[3], st
+
+
+def lbm_sw_get_populations(h: int, dst: int, on_device: bool) -> None:
+    _check(load().lbm_sw_get_populations(h, dst, int(on_device)), h, "lbm_sw_get_populations")
+
+
+def lbm_sw_set_populations(h: int, src: int, on_device: bool, form: int) -> None:
+    _check(load().lbm_sw_set_populations(h, src, int(on_device), int(form)), h, "lbm_sw_set_populations")
+
+
+def lbm_sw_synchronize(h: int) -> None:
+    _check(load().lbm_sw_synchronize(h), h, "lbm_sw_synchronize")
+
+
+def lbm_sw_get_info(h: int) -> lbm_sw_info:
+    info = lbm_sw_info()
+    _check(load().lbm_sw_get_info(h, ctypes.byref(info)), h, "lbm_sw_get_info")
+    return info
+
+
+def lbm_sw_abi_version() -> int:
+    return load().lbm_sw_abi_version()
+
+
+# ---------------------------------------------------------------- convenience
+def make_params(nx: int, ny: int = 1, *, dim: int | None = None, precision: int = FP32, g: float = 1.0,
+                lam: float = 8.0, s: float = 1.8, a: float | None = None, bc=(PERIODIC,) * 4, inflow=None,
+                stream: int | None = None, kernel: int = KERNEL_AUTO, graph_chunk: int = 0) -> lbm_sw_params:
+    dim = 2 if dim is None else int(dim)
+    p = lbm_sw_params_init()
+    p.dim, p.nx, p.ny, p.precision = dim, int(nx), int(ny), int(precision)
+    p.g, p.lambda_, p.s = float(g), float(lam), float(s)
+    p.a = float(a if a is not None else (0.15 if dim == 1 else 0.05))
+    bc = list(bc) + [PERIODIC] * (4 - len(bc))
+    for k in range(4):
+        p.bc[k] = int(bc[k])
+    if inflow is not None:
+        for k in range(min(4, len(inflow))):
+            if inflow[k] is not None:
+                for c, v in enumerate(inflow[k]):
+                    p.inflow[k][c] = float(v)
+    p.stream = stream
+    p.kernel = int(kernel)
+    p.graph_chunk = int(graph_chunk)
+    return p
+
+
+def _ptr(x, on_device: bool):
+    """Address of a contiguous numpy array or torch tensor (and whether it is on the GPU)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    assert isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]
+    return x.ctypes.data
+
+
+class Simulation:
+    """Owner of one lbm_sw handle.  Moment arrays are FP64 [ny][nx]; populations
+    [q][ny][nx] in the handle's precision.  numpy arrays cross as host memory,
+    torch CUDA tensors as device memory."""
+
+    def __init__(self, nx: int, ny: int = 1, **kw):
+        self.params = make_params(nx, ny, **kw)
+        self.handle = lbm_sw_create(self.params)
+        self.nx, self.ny, self.dim = self.params.nx, self.params.ny, self.params.dim
+        self.q = 5 if self.dim == 1 else 13
+        self.dtype = np.float64 if self.params.precision == FP64 else np.float32
+
+    def close(self):
+        if self.handle:
+            lbm_sw_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _on_device(x) -> bool:
+        return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+    def set_state(self, h, hu, hv=None):
+        dev = self._on_device(h)
+        if not dev:
+            h, hu = (np.ascontiguousarray(x, dtype=np.float64) for x in (h, hu))
+            hv = None if hv is None else np.ascontiguousarray(hv, dtype=np.float64)
+        lbm_sw_set_state(self.handle, _ptr(h, dev), _ptr(hu, dev), _ptr(hv, dev), dev)
+
+    def step(self, n: int = 1):
+        lbm_sw_step(self.handle, n)
+
+    def moments(self):
+        h = np.empty((self.ny, self.nx))
+        hu = np.empty_like(h)
+        hv = np.empty_like(h) if self.dim == 2 else None
+        lbm_sw_get_moments(self.handle, _ptr(h, False), _ptr(hu, False), _ptr(hv, False), False)
+        return (h, hu, hv) if self.dim == 2 else (h[0], hu[0])
+
+    def moments_into(self, h, hu, hv=None):
+        dev = self._on_device(h)
+        lbm_sw_get_moments(self.handle, _ptr(h, dev), _ptr(hu, dev), _ptr(hv, dev), dev)
+
+    def populations(self) -> np.ndarray:
+        out = np.empty((self.q, self.ny, self.nx), dtype=self.dtype)
+        lbm_sw_get_populations(self.handle, _ptr(out, False), False)
+        return out
+
+    def populations_into(self, out):
+        dev = self._on_device(out)
+        lbm_sw_get_populations(self.handle, _ptr(out, dev), dev)
+
+    def set_populations(self, F, form: int = POST_COLLISION):
+        dev = self._on_device(F)
+        if not dev:
+            F = np.ascontiguousarray(F, dtype=self.dtype).reshape(self.q, self.ny, self.nx)
+        lbm_sw_set_populations(self.handle, _ptr(F, dev), dev, form)
+
+    def diagnostics(self, raise_unstable: bool = True):
+        return lbm_sw_diagnostics(self.handle, raise_unstable)
+
+    def synchronize(self):
+        lbm_sw_synchronize(self.handle)
+
+    def info(self) -> lbm_sw_info:
+        return lbm_sw_get_info(self.handle)

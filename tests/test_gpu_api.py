@@ -1,0 +1,130 @@
+"""Behaviour of the C ABI on the GPU: state round trips, device-pointer transfers,
+diagnostics (totals in FP64, NaN / dry-cell detection), error codes, lake at rest."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_0427_gb300 import inputs, lbm_sw
+
+from gpu_helpers import FP64_TOL, torch_stream
+
+pytestmark = pytest.mark.gpu
+
+P, W, O, I = lbm_sw.PERIODIC, lbm_sw.WALL, lbm_sw.OUTFLOW, lbm_sw.INFLOW
+
+
+@pytest.mark.parametrize("precision", [lbm_sw.FP64, lbm_sw.FP32])
+@pytest.mark.parametrize("bc", [(P, P, P, P), (W, W, W, W), (O, O, O, O), (W, O, P, P)], ids=str)
+@pytest.mark.parametrize("h0", [1.0, 2.0, 0.5])
+def test_lake_at_rest_stays_exactly_at_rest(precision, bc, h0):
+    nx, ny = 133, 70
+    with lbm_sw.Simulation(nx, ny, precision=precision, bc=bc, stream=torch_stream()) as sim:
+        sim.set_state(np.full((ny, nx), h0), np.zeros((ny, nx)), np.zeros((ny, nx)))
+        F0 = sim.populations()
+        sim.step(200)
+        assert np.array_equal(sim.populations(), F0)
+        h, hu, hv = sim.moments()
+    assert np.all(h == h0) and np.all(hu == 0) and np.all(hv == 0)
+
+
+@pytest.mark.parametrize("precision", [lbm_sw.FP64, lbm_sw.FP32])
+def test_set_state_is_the_oracle_equilibrium(precision):
+    nx, ny = 97, 31
+    h, hu, hv = inputs.random_states(nx * ny, seed=77)
+    W0 = [x.reshape(ny, nx) for x in (h, hu, hv)]
+    with lbm_sw.Simulation(nx, ny, precision=precision, stream=torch_stream()) as sim:
+        sim.set_state(*W0)
+        F = sim.populations().astype(np.float64)
+        m = sim.moments()
+    want = oracle.equilibrium_2d(*W0, oracle.params(nx, ny, a=0.05))
+    tol = FP64_TOL if precision == lbm_sw.FP64 else 1e-6
+    assert np.abs(F - want).max() <= tol * np.abs(want).max()
+    for got, w in zip(m, W0):
+        assert np.abs(got - w).max() <= tol * np.abs(W0[0]).max()
+
+
+def test_device_pointers_match_host_path():
+    import torch
+
+    nx, ny = 200, 90
+    h = np.ascontiguousarray(inputs.circular_dam_break_2d(200, seed=inputs.stream_seed(3))[0][:ny])
+    hu = 0.1 * inputs.uniform(5, nx * ny, -1, 1).reshape(ny, nx)
+    hv = 0.1 * inputs.uniform(6, nx * ny, -1, 1).reshape(ny, nx)
+    with lbm_sw.Simulation(nx, ny, precision=lbm_sw.FP64, bc=(W, W, O, I), inflow=[None, None, None, (1.1, 0, 0.1)],
+                           stream=torch_stream()) as a, \
+         lbm_sw.Simulation(nx, ny, precision=lbm_sw.FP64, bc=(W, W, O, I), inflow=[None, None, None, (1.1, 0, 0.1)],
+                           stream=torch_stream()) as b:
+        a.set_state(h, hu, hv)
+        b.set_state(*[torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (h, hu, hv)])
+        a.step(33)
+        b.step(33)
+        host = a.moments()
+        dev = [torch.empty((ny, nx), dtype=torch.float64, device="cuda") for _ in range(3)]
+        b.moments_into(*dev)
+        torch.cuda.synchronize()
+        for x, y in zip(host, dev):
+            assert np.array_equal(x, y.cpu().numpy())
+        Fa = a.populations()
+        Fb = torch.empty(Fa.shape, dtype=torch.float64, device="cuda")
+        b.populations_into(Fb)
+        torch.cuda.synchronize()
+        assert np.array_equal(Fa, Fb.cpu().numpy())
+        # checkpoint round trip: post-collision populations in, same trajectory out
+        b.set_populations(Fb, form=lbm_sw.POST_COLLISION)
+        a.step(5)
+        b.step(5)
+        assert np.array_equal(a.populations(), b.populations())
+
+
+@pytest.mark.parametrize("precision", [lbm_sw.FP64, lbm_sw.FP32])
+def test_diagnostics_are_fp64_totals(precision):
+    nx, ny = 301, 211
+    h, hu, hv = (x.reshape(ny, nx) for x in inputs.random_states(nx * ny, seed=88))
+    with lbm_sw.Simulation(nx, ny, precision=precision, bc=(W, W, W, W), stream=torch_stream()) as sim:
+        sim.set_state(h, hu, hv)
+        sim.step(10)
+        m = sim.moments()
+        d = sim.diagnostics()
+    assert d[4] == lbm_sw.OK
+    scale = np.abs(m[0]).sum()
+    assert abs(d[0] - m[0].sum()) <= 1e-12 * scale
+    assert abs(d[1] - m[1].sum()) <= 1e-12 * scale and abs(d[2] - m[2].sum()) <= 1e-12 * scale
+    assert d[3] == m[0].min()
+
+
+def test_diagnostics_report_unstable_states():
+    nx, ny = 64, 48
+    with lbm_sw.Simulation(nx, ny, precision=lbm_sw.FP32, stream=torch_stream()) as sim:
+        h = np.ones((ny, nx))
+        h[10, 20] = -0.5  # a dry (negative-depth) cell
+        sim.set_state(h, np.zeros_like(h), np.zeros_like(h))
+        out = sim.diagnostics(raise_unstable=False)
+        assert out[4] == lbm_sw.E_UNSTABLE and abs(out[3] + 0.5) < 1e-6
+        F = sim.populations()
+        F[3, 5, 5] = np.nan
+        sim.set_populations(F)
+        with pytest.raises(lbm_sw.LbmSwError) as ei:
+            sim.diagnostics()
+        assert ei.value.status == lbm_sw.E_UNSTABLE and "cells" in str(ei.value)
+
+
+def test_state_errors_and_counters():
+    with lbm_sw.Simulation(40, 30, stream=torch_stream()) as sim:
+        with pytest.raises(lbm_sw.LbmSwError) as ei:
+            sim.step(1)
+        assert ei.value.status == lbm_sw.E_STATE
+        with pytest.raises(lbm_sw.LbmSwError) as ei:
+            lbm_sw.lbm_sw_step(sim.handle, -1)
+        assert ei.value.status == lbm_sw.E_ARG
+        sim.set_state(np.ones((30, 40)), np.zeros((30, 40)), np.zeros((30, 40)))
+        sim.step(7)
+        info = sim.info()
+        assert info.q == 13 and info.steps_done == 7 and info.pitch == 64
+        assert info.bytes_per_update == 104.0 and info.kernel == lbm_sw.KERNEL_VEC
+
+
+def test_1d_info():
+    with lbm_sw.Simulation(1000, 1, dim=1, precision=lbm_sw.FP64, bc=(W, W), stream=torch_stream()) as sim:
+        info = sim.info()
+        assert info.q == 5 and info.bytes_per_update == 80.0

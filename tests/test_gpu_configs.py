@@ -147,6 +147,6 @@ def test_dam_break_4096_d4_symmetry_and_conservation():
         h, hu, hv = sim.moments()
     assert np.array_equal(h, h[::-1, :]) and np.array_equal(h, h[:, ::-1]) and np.array_equal(h, h.T)
     assert np.array_equal(hu, -hu[:, ::-1]) and np.array_equal(hu, hu[::-1, :]) and np.array_equal(hu, hv.T)
-    assert h.max() < 2.0 and not np.array_equal(h, W0[0])
+    assert h.max() < 2.0 + 1e-5 and not np.array_equal(h, W0[0])  # FP32 rounding of the untouched column
     assert abs(d1[0] - d0[0]) <= 1e-6 * d0[0]  # FP32 state, FP64 totals
     assert abs(d1[1]) <= 1e-6 * d0[0] and abs(d1[2]) <= 1e-6 * d0[0]

@@ -182,6 +182,38 @@ LBM_SW_API int lbm_sw_get_populations(lbm_sw* h, void* dst, int on_device);
  * so that the next step streams their post-collision values. */
 LBM_SW_API int lbm_sw_set_populations(lbm_sw* h, const void* src, int on_device, int form);
 
+/* Allocation-free diagnostics (the paper has no counterpart: this is a service of the
+ * library, not a step of the scheme).  Some callers cannot allocate device memory at the
+ * moment they need a health check of a state: a caller whose memory manager owns the whole
+ * device and forbids allocations outside it, a caller with a fixed device-memory budget
+ * fixed at start-up, or a caller that has just hit an out-of-memory error and wants to know
+ * whether the state it still holds is sound.  This entry point computes the same numbers as
+ * lbm_sw_diagnostics without any allocation: no cudaMalloc, no cudaFree, no allocating
+ * library routine.
+ *
+ * Input: populations, a device pointer to q planes (q = 5 in 1D, 13 in 2D, the population
+ * order above) of the given precision, each ny rows of row_pitch elements (row_pitch >= nx),
+ * planes plane_pitch elements apart (plane_pitch >= row_pitch * ny); dense planes from
+ * lbm_sw_get_populations have row_pitch = nx and plane_pitch = nx * ny.  Output: out, a
+ * device pointer to 5 doubles, written asynchronously on `stream` (a cudaStream_t, NULL =
+ * legacy default): sum h, sum hu, sum hv (0 in 1D), min h, and the number of cells with
+ * NaN/Inf or h <= 0 (the call does not synchronise, so it reports that count in out[4]
+ * instead of returning LBM_SW_E_UNSTABLE).  Totals are accumulated in FP64.
+ *
+ * Limit: ny <= LBM_SW_NOALLOC_MAX_ROWS (one partial per row lives in a static device array
+ * of 8192 * 5 doubles = 327,680 bytes, which every GPU that loads this library holds until the
+ * process exits).  Larger ny, NULL pointers, bad sizes or pitches return LBM_SW_E_ARG without
+ * launching anything; a failed CUDA call returns LBM_SW_E_CUDA.
+ *
+ * The first call on a device (with that device current) looks up the device address of the
+ * static array; make that first call before any stream capture.  All calls share the array
+ * and each call fully rewrites the part it reads, so nothing needs clearing between calls;
+ * calls whose work overlaps on the GPU (different streams, or different threads) race on the
+ * array and must be serialised by the caller. */
+#define LBM_SW_NOALLOC_MAX_ROWS 8192
+LBM_SW_API int lbm_sw_diagnostics_noalloc(const void* populations, int dim, int precision, int nx, int ny,
+                                          size_t row_pitch, size_t plane_pitch, double* out, void* stream);
+
 /* Wait for all work queued by the handle; returns LBM_SW_E_CUDA on a kernel fault. */
 LBM_SW_API int lbm_sw_synchronize(lbm_sw* h);
 

@@ -63,6 +63,10 @@ cudaError_t launch_inflow_feq1d(T* out, const int bc[4], const double inflow[4][
 int diag_max_blocks();
 template <class T>
 cudaError_t launch_diagnostics(const StepArgs<T>& a, int q, double* partials, double* out, cudaStream_t st);
+// Same reduction with an explicit number of pass-1 blocks (partials must hold nblocks * 5).
+template <class T>
+cudaError_t launch_diagnostics_blocks(const StepArgs<T>& a, int q, int nblocks, double* partials, double* out,
+                                      cudaStream_t st);
 
 }  // namespace lbm
 

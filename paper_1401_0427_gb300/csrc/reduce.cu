@@ -129,7 +129,22 @@ cudaError_t launch_diagnostics(const StepArgs<T>& a, int q, double* partials, do
   return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t launch_diagnostics_blocks(const StepArgs<T>& a, int q, int nblocks, double* partials, double* out,
+                                      cudaStream_t st) {
+  if (q == 13)
+    diag_partials<T, 13><<<nblocks, kThreads, 0, st>>>(a, partials);
+  else
+    diag_partials<T, 5><<<nblocks, kThreads, 0, st>>>(a, partials);
+  diag_final<<<1, kThreads, 0, st>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_diagnostics<float>(const StepArgs<float>&, int, double*, double*, cudaStream_t);
 template cudaError_t launch_diagnostics<double>(const StepArgs<double>&, int, double*, double*, cudaStream_t);
+template cudaError_t launch_diagnostics_blocks<float>(const StepArgs<float>&, int, int, double*, double*,
+                                                      cudaStream_t);
+template cudaError_t launch_diagnostics_blocks<double>(const StepArgs<double>&, int, int, double*, double*,
+                                                       cudaStream_t);
 
 }  // namespace lbm

@@ -85,6 +85,9 @@ SIGNATURES = {
     "lbm_sw_create_error": (ctypes.c_char_p, []),
     "lbm_sw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lbm_sw_abi_version": (ctypes.c_int, []),
+    "lbm_sw_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_void_p,
+                                                  ctypes.c_void_p]),
 }
 
 
@@ -181,6 +184,22 @@ def lbm_sw_get_info(h: int) -> lbm_sw_info:
 
 def lbm_sw_abi_version() -> int:
     return load().lbm_sw_abi_version()
+
+
+NOALLOC_MAX_ROWS = 8192  # LBM_SW_NOALLOC_MAX_ROWS
+
+
+def lbm_sw_diagnostics_noalloc(populations: int, dim: int, precision: int, nx: int, ny: int, row_pitch: int,
+                               plane_pitch: int, out: int, stream: int | None) -> None:
+    """Allocation-free diagnostics for callers that may not allocate device memory when
+    they check a state (see include/lbm_sw.h).  ``populations`` and ``out`` (5 doubles)
+    are device addresses; the result is written asynchronously on ``stream``."""
+    st = load().lbm_sw_diagnostics_noalloc(populations, int(dim), int(precision), int(nx), int(ny),
+                                           int(row_pitch), int(plane_pitch), out, stream)
+    if st == E_ARG and ny > NOALLOC_MAX_ROWS:
+        raise LbmSwError(st, f"lbm_sw_diagnostics_noalloc: ny = {ny} rows exceeds the static scratch "
+                             f"capacity of {NOALLOC_MAX_ROWS} rows")
+    _check(st, None, "lbm_sw_diagnostics_noalloc")
 
 
 # ---------------------------------------------------------------- convenience

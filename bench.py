@@ -340,7 +340,90 @@ def variants(args, W0, stream, lbm_sw, torch):
     out["_l1"] = {"relative_l1_h": float(np.abs(hs["fp32"] - hs["fp64"]).sum() / np.abs(hs["fp64"]).sum()),
                   "steps": JOB_STEPS, "against": "FP64 run of the same workload (equal to the FP64 oracle "
                                                  "within 1e-12 in the parity tests)"}
+    out["batched_256"] = batched_variant(stream, lbm_sw, torch)
+    out["shock_reflection_512"] = shock_reflection_variant(stream, lbm_sw, torch)
+    out["shock_tube_1d_1000"] = shock_tube_variant(stream, lbm_sw, torch)
     return out
+
+
+def _timed(stream, torch, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def batched_variant(stream, lbm_sw, torch, steps: int = 500):
+    """256 dam-break instances (sides 64..1024, depth U[1.5, 4], radius U[0.1, 0.3]) for 500
+    steps in FP32: one batch (persistent tile-list launch per step, CUDA graph of 50 steps,
+    autotuned tiles) against a plain loop over 256 single handles (each replaying its own
+    graph of the same 500 steps)."""
+    from paper_1401_0427_gb300 import inputs
+
+    table = inputs.batched_instances(256)
+    sizes = [(n, n) for n, _, _ in table]
+    cells = sum(n * n for n, _ in sizes)
+    states = [inputs.circular_dam_break_2d(n, seed=None, h_in=hin, radius=r) for n, hin, r in table]
+    with lbm_sw.Batch(sizes, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream) as b:
+        for i, W0 in enumerate(states):
+            b.set_state(i, *W0)
+        tune = b.autotune(3)
+        b.step(4)
+        t_batch = _timed(stream, torch, lambda: b.step(steps))
+    sims = []
+    for (n, _), W0 in zip(sizes, states):
+        sim = lbm_sw.Simulation(n, n, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream)
+        sim.set_state(*W0)
+        sim.step(2)
+        sims.append(sim)
+    t_plain = _timed(stream, torch, lambda: [sim.step(steps) for sim in sims])
+    for sim in sims:
+        sim.close()
+    peak, _ = measured_peaks()
+    gbs = BYTES_PER_LUP["f32"] * cells * steps / t_batch / 1e9
+    return {"instances": 256, "cells": cells, "steps": steps,
+            "batched": {"MLUPS": cells * steps / t_batch / 1e6, "ms_per_step": t_batch / steps * 1e3,
+                        "GB_per_s": gbs, "frac_of_hbm_peak": gbs / peak, "tile_rows": tune.tile_rows,
+                        "ctas_per_sm": tune.ctas_per_sm, "autotune_candidates": tune.candidates},
+            "plain_loop": {"MLUPS": cells * steps / t_plain / 1e6, "ms_per_step": t_plain / steps * 1e3},
+            "speedup_batched_over_plain": t_plain / t_batch}
+
+
+def shock_reflection_variant(stream, lbm_sw, torch, steps: int = 2000):
+    """512 x 512 planar shock reflected by a wall, 2000 steps, FP32 and FP64 (the state fits
+    in L2: this measures L2-resident throughput)."""
+    from paper_1401_0427_gb300 import inputs
+
+    n = 512
+    uL = inputs.shock_speed_state(2.0, 1.0)
+    W0 = inputs.planar_shock_2d(n, n)
+    out = {}
+    for name, prec in (("fp32", lbm_sw.FP32), ("fp64", lbm_sw.FP64)):
+        with lbm_sw.Simulation(n, n, precision=prec, lam=LAM, s=S_RATE, a=A_REST,
+                               bc=(lbm_sw.INFLOW, lbm_sw.WALL, lbm_sw.PERIODIC, lbm_sw.PERIODIC),
+                               inflow=[(2.0, 2.0 * uL, 0.0)] * 4, stream=stream.cuda_stream) as sim:
+            sim.set_state(*W0)
+            sim.step(4)
+            t = _timed(stream, torch, lambda: sim.step(steps))
+        out[name] = {"MLUPS": n * n * steps / t / 1e6, "ms_per_step": t / steps * 1e3}
+    return out
+
+
+def shock_tube_variant(stream, lbm_sw, torch, steps: int = 500):
+    """1D dam-break shock tube, 1000 cells, 500 steps, FP64, walls (latency-bound)."""
+    from paper_1401_0427_gb300 import inputs
+
+    n = 1000
+    h, q = inputs.dam_break_1d(n)
+    with lbm_sw.Simulation(n, 1, dim=1, precision=lbm_sw.FP64, lam=LAM, s=S_RATE, a=0.15,
+                           bc=(lbm_sw.WALL, lbm_sw.WALL), stream=stream.cuda_stream) as sim:
+        sim.set_state(h, q)
+        sim.step(4)
+        t = _timed(stream, torch, lambda: sim.step(steps))
+    return {"MLUPS": n * steps / t / 1e6, "ms_per_run": t * 1e3, "steps": steps}
 
 
 def end_to_end(W0, stream, lbm_sw, torch, jobs: int = 3):

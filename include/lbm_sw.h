@@ -182,6 +182,84 @@ LBM_SW_API int lbm_sw_get_populations(lbm_sw* h, void* dst, int on_device);
  * so that the next step streams their post-collision values. */
 LBM_SW_API int lbm_sw_set_populations(lbm_sw* h, const void* src, int on_device, int form);
 
+/* ---- Batched instances ----
+ * Many independent D2Q5Q4Q4 grids of uneven sizes (e.g. an ensemble of dam-breaks), all with
+ * the same scheme parameters and boundary kinds, advanced together: one kernel launch per
+ * time step walks a list of tiles (rows x 32 vectors) covering every instance, either one CTA
+ * per tile or a persistent grid of a few CTAs per SM striding through the list,
+ * and long runs replay a CUDA graph of graph_chunk steps.  Each instance evolves exactly as
+ * it would in its own lbm_sw handle (same device arithmetic, bit for bit).  Tile shape and
+ * schedule come from lbm_sw_batch_autotune (or the params).  All instances share two device
+ * buffers (double buffering); instance i stores its planes like a single handle does
+ * (pitch = nx rounded up to 32 elements, 256-byte aligned planes). */
+typedef struct lbm_sw_batch lbm_sw_batch;
+
+typedef struct lbm_sw_batch_params {
+  int count;              /* instances, 1 .. 65536 */
+  const int* nx;          /* count widths (host array, copied by create), each >= 1 */
+  const int* ny;          /* count heights (host array, copied by create), each >= 1 */
+  int precision;          /* LBM_SW_FP32 or LBM_SW_FP64 */
+  double g, lambda, s, a; /* as in lbm_sw_params */
+  int bc[4];              /* boundary kinds shared by every instance */
+  double inflow[4][3];    /* (h, hu, hv) of INFLOW sides */
+  void* stream;           /* cudaStream_t borrowed from the caller */
+  int tile_rows;          /* rows per CTA tile: 1, 2, 4 or 8; 0 = default (4) */
+  int ctas_per_sm;        /* persistent CTAs per SM, 1 .. 32; 0 = one CTA per tile (default) */
+  int graph_chunk;        /* steps per captured CUDA graph; 0 = default (50), < 0 = off */
+  int reserved[5];        /* must be zero */
+} lbm_sw_batch_params;
+
+typedef struct lbm_sw_batch_tuning {
+  int tile_rows;          /* chosen rows per tile */
+  int ctas_per_sm;        /* chosen persistent CTAs per SM (0: one CTA per tile) */
+  int candidates;         /* configurations timed by the last autotune (0 if none) */
+  double ms_per_step;     /* time per step of the chosen configuration (0 if not timed) */
+  long long tiles;        /* tiles in the work list */
+  long long cells;        /* cells over all instances */
+} lbm_sw_batch_tuning;
+
+/* Defaults as for lbm_sw_params_init (count = 0, nx = ny = NULL must be set). */
+LBM_SW_API int lbm_sw_batch_params_init(lbm_sw_batch_params* p);
+
+/* Validate, allocate the two shared buffers and the tile list.  Errors as lbm_sw_create
+ * (message from lbm_sw_create_error). */
+LBM_SW_API int lbm_sw_batch_create(const lbm_sw_batch_params* p, lbm_sw_batch** out);
+
+/* Release the batch (synchronises its stream).  NULL-safe. */
+LBM_SW_API void lbm_sw_batch_destroy(lbm_sw_batch* b);
+
+/* Equilibrium state f = f^eq(W) of one instance (arrays FP64 [ny_i][nx_i]; hv may be NULL
+ * for host input: zero).  Every instance needs a state before lbm_sw_batch_step. */
+LBM_SW_API int lbm_sw_batch_set_state(lbm_sw_batch* b, int instance, const double* depth, const double* hu,
+                                      const double* hv, int on_device);
+
+/* Advance every instance n >= 0 steps: one tile-list kernel launch per step.  Errors:
+ * LBM_SW_E_ARG, LBM_SW_E_STATE (an instance has no state), LBM_SW_E_CUDA. */
+LBM_SW_API int lbm_sw_batch_step(lbm_sw_batch* b, int n);
+
+/* Moments of one instance (as lbm_sw_get_moments). */
+LBM_SW_API int lbm_sw_batch_get_moments(lbm_sw_batch* b, int instance, double* depth, double* hu, double* hv,
+                                        int on_device);
+
+/* Post-collision populations of one instance, dense [13][ny_i][nx_i] of the batch precision. */
+LBM_SW_API int lbm_sw_batch_get_populations(lbm_sw_batch* b, int instance, void* dst, int on_device);
+
+/* FP64 totals of one instance (as lbm_sw_diagnostics, including LBM_SW_E_UNSTABLE). */
+LBM_SW_API int lbm_sw_batch_diagnostics(lbm_sw_batch* b, int instance, double out[4]);
+
+/* Time trial_steps launches (>= 1) of every candidate tile shape (1, 2, 4, 8 rows) and
+ * schedule (one CTA per tile, or 2, 4, 8 persistent CTAs per SM), keep the fastest, and
+ * report it.  The
+ * trials read the current state and write the spare buffer, so the state does not change.
+ * Needs every instance's state.  Synchronises. */
+LBM_SW_API int lbm_sw_batch_autotune(lbm_sw_batch* b, int trial_steps, lbm_sw_batch_tuning* out);
+
+/* The tile shape and schedule in use. */
+LBM_SW_API int lbm_sw_batch_get_tuning(const lbm_sw_batch* b, lbm_sw_batch_tuning* out);
+
+/* Message of the last failure on this batch ("" if none). */
+LBM_SW_API const char* lbm_sw_batch_last_error(const lbm_sw_batch* b);
+
 /* Allocation-free diagnostics (the paper has no counterpart: this is a service of the
  * library, not a step of the scheme).  Some callers cannot allocate device memory at the
  * moment they need a health check of a state: a caller whose memory manager owns the whole

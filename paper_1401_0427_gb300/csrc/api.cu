@@ -124,6 +124,10 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+namespace lbm {
+void set_create_error(const char* msg) { g_create_error = msg ? msg : ""; }
+}  // namespace lbm
+
 extern "C" {
 
 int lbm_sw_abi_version(void) { return LBM_SW_ABI_VERSION; }

@@ -57,6 +57,9 @@ template <class T>
 cudaError_t launch_inflow_feq1d(T* out, const int bc[4], const double inflow[4][3], const ConstsD& k,
                                 cudaStream_t st);
 
+// Message returned by lbm_sw_create_error() on the calling thread (api.cu).
+void set_create_error(const char* msg);
+
 // ---- reductions (reduce.cu) ----
 // Block partials (5 doubles each: sum h, sum hu, sum hv, min h, bad-cell count) then a
 // fixed-order final pass into out[5].  partials must hold diag_max_blocks() * 5 doubles.

@@ -14,11 +14,10 @@
 
 #include "internal.h"
 #include "scheme.cuh"
+#include "step2d_vec.cuh"
 
 namespace lbm {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
 
 // Velocity components of each population and its partner across an x- / y-wall.
 __device__ __forceinline__ int ex_of(int p) {
@@ -87,7 +86,7 @@ __global__ void __launch_bounds__(256) step2d_simple(const StepArgs<T> A, const 
 }
 
 // --------------------------------------------------------------------------
-// VEC variant: each thread owns V consecutive cells of one row (one 16-byte
+// VEC variant (row body in step2d_vec.cuh): each thread owns V consecutive cells of one row (one 16-byte
 // vector per plane: 4 FP32 or 2 FP64 values), a warp owns 32 V cells of a row.
 // All 13 loads are aligned vectors: the y-moving families read whole vectors of
 // rows y -+ 1, and the x-moving families read their own row and shift it by one
@@ -96,199 +95,12 @@ __global__ void __launch_bounds__(256) step2d_simple(const StepArgs<T> A, const 
 // rows are warp-uniform, so only the first and last row and the warps holding
 // x = 0 or x = nx - 1 take a boundary branch.
 // --------------------------------------------------------------------------
-template <class T>
-struct V16;
-template <>
-struct V16<float> {
-  static constexpr int n = 4;
-  __device__ static void load(const float* p, float (&o)[4]) {
-    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
-    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
-  }
-  __device__ static void store(float* p, const float (&o)[4]) {
-    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
-  }
-};
-template <>
-struct V16<double> {
-  static constexpr int n = 2;
-  __device__ static void load(const double* p, double (&o)[2]) {
-    const double2 t = __ldg(reinterpret_cast<const double2*>(p));
-    o[0] = t.x; o[1] = t.y;
-  }
-  __device__ static void store(double* p, const double (&o)[2]) {
-    *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
-  }
-};
-
-template <class T, int V>
-__device__ __forceinline__ T pick(const T (&a)[V], int i) {
-  T r = a[0];
-#pragma unroll
-  for (int k = 1; k < V; ++k)
-    if (i == k) r = a[k];
-  return r;
-}
-
 template <class T, int BY>
 __global__ void __launch_bounds__(32 * BY) step2d_vec(const StepArgs<T> A, const Consts<T> K) {
-  using VV = V16<T>;
-  constexpr int V = VV::n;
-  const int lane = threadIdx.x;
-  const int nx = A.nx, ny = A.ny;
-  const long long P = A.plane;
-  const T* __restrict__ S = A.src;
-  const int x0 = (blockIdx.x * 32 + lane) * V;
-  const bool active = x0 < nx;
-
-  for (int y = blockIdx.y * BY + threadIdx.y; y < ny; y += gridDim.y * BY) {  // warp-uniform
-    const long long row = static_cast<long long>(y) * A.pitch;
-    T c0[V], xp[3][V], xm[3][V], yp[3][V], ym[3][V];
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-      c0[k] = T(0);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) xp[c][k] = xm[c][k] = yp[c][k] = ym[c][k] = T(0);
-    }
-    if (active) {
-      VV::load(S + row + x0, c0);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        VV::load(S + (1 + 4 * c) * P + row + x0, xp[c]);  // f1, gx1, gy1 (moving +x)
-        VV::load(S + (3 + 4 * c) * P + row + x0, xm[c]);  // f3, gx3, gy3 (moving -x)
-      }
-    }
-    // Populations moving +y (f2, gx2, gy2) arrive from row y - 1.
-    {
-      const int bcs = A.bc[LBM_SW_SIDE_YM];
-      if (y > 0 || bcs == LBM_SW_BC_PERIODIC) {
-        const long long r = static_cast<long long>(y > 0 ? y - 1 : ny - 1) * A.pitch;
-        if (active)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) VV::load(S + (2 + 4 * c) * P + r + x0, yp[c]);
-      } else if (bcs == LBM_SW_BC_WALL) {  // mirror of row 0: f4, gx4, -gy4
-        if (active)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) VV::load(S + (4 + 4 * c) * P + row + x0, yp[c]);
-#pragma unroll
-        for (int k = 0; k < V; ++k) yp[2][k] = -yp[2][k];
-      } else if (bcs == LBM_SW_BC_OUTFLOW) {
-        if (active)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) VV::load(S + (2 + 4 * c) * P + row + x0, yp[c]);
-      } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const T v = A.inflow_feq[LBM_SW_SIDE_YM * 13 + 2 + 4 * c];
-#pragma unroll
-          for (int k = 0; k < V; ++k) yp[c][k] = v;
-        }
-      }
-    }
-    // Populations moving -y (f4, gx4, gy4) arrive from row y + 1.
-    {
-      const int bcs = A.bc[LBM_SW_SIDE_YP];
-      if (y < ny - 1 || bcs == LBM_SW_BC_PERIODIC) {
-        const long long r = static_cast<long long>(y < ny - 1 ? y + 1 : 0) * A.pitch;
-        if (active)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) VV::load(S + (4 + 4 * c) * P + r + x0, ym[c]);
-      } else if (bcs == LBM_SW_BC_WALL) {  // mirror of row ny-1: f2, gx2, -gy2
-        if (active)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) VV::load(S + (2 + 4 * c) * P + row + x0, ym[c]);
-#pragma unroll
-        for (int k = 0; k < V; ++k) ym[2][k] = -ym[2][k];
-      } else if (bcs == LBM_SW_BC_OUTFLOW) {
-        if (active)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) VV::load(S + (4 + 4 * c) * P + row + x0, ym[c]);
-      } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const T v = A.inflow_feq[LBM_SW_SIDE_YP * 13 + 4 + 4 * c];
-#pragma unroll
-          for (int k = 0; k < V; ++k) ym[c][k] = v;
-        }
-      }
-    }
-    // x-moving families: L[c][k] = value at x0 + k - 1 (+x movers), R[c][k] = at x0 + k + 1.
-    T L[3][V], R[3][V];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      T up = __shfl_up_sync(kFull, xp[c][V - 1], 1);
-      T dn = __shfl_down_sync(kFull, xm[c][0], 1);
-      if (lane == 0) up = (active && x0 > 0) ? S[(1 + 4 * c) * P + row + x0 - 1] : T(0);
-      if (lane == 31) dn = (x0 + V < nx) ? S[(3 + 4 * c) * P + row + x0 + V] : T(0);
-      L[c][0] = up;
-#pragma unroll
-      for (int k = 1; k < V; ++k) L[c][k] = xp[c][k - 1];
-#pragma unroll
-      for (int k = 0; k < V - 1; ++k) R[c][k] = xm[c][k + 1];
-      R[c][V - 1] = dn;
-    }
-    if (x0 == 0) {  // cell x = 0: +x movers come from the x- ghost
-      switch (A.bc[LBM_SW_SIDE_XM]) {
-        case LBM_SW_BC_PERIODIC:
-#pragma unroll
-          for (int c = 0; c < 3; ++c) L[c][0] = S[(1 + 4 * c) * P + row + nx - 1];
-          break;
-        case LBM_SW_BC_WALL:
-          L[0][0] = xm[0][0];
-          L[1][0] = -xm[1][0];
-          L[2][0] = xm[2][0];
-          break;
-        case LBM_SW_BC_OUTFLOW:
-#pragma unroll
-          for (int c = 0; c < 3; ++c) L[c][0] = xp[c][0];
-          break;
-        default:
-#pragma unroll
-          for (int c = 0; c < 3; ++c) L[c][0] = A.inflow_feq[LBM_SW_SIDE_XM * 13 + 1 + 4 * c];
-      }
-    }
-    const int kk = nx - 1 - x0;  // cell x = nx - 1 is this thread's cell kk
-    if (kk >= 0 && kk < V) {
-      T rv[3];
-      switch (A.bc[LBM_SW_SIDE_XP]) {
-        case LBM_SW_BC_PERIODIC:
-#pragma unroll
-          for (int c = 0; c < 3; ++c) rv[c] = S[(3 + 4 * c) * P + row];
-          break;
-        case LBM_SW_BC_WALL:
-          rv[0] = pick(xp[0], kk);
-          rv[1] = -pick(xp[1], kk);
-          rv[2] = pick(xp[2], kk);
-          break;
-        case LBM_SW_BC_OUTFLOW:
-#pragma unroll
-          for (int c = 0; c < 3; ++c) rv[c] = pick(xm[c], kk);
-          break;
-        default:
-#pragma unroll
-          for (int c = 0; c < 3; ++c) rv[c] = A.inflow_feq[LBM_SW_SIDE_XP * 13 + 3 + 4 * c];
-      }
-#pragma unroll
-      for (int k = 0; k < V; ++k)
-        if (k == kk)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) R[c][k] = rv[c];
-    }
-
-    T out[13][V];
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-      T f[13] = {c0[k],    L[0][k], yp[0][k], R[0][k], ym[0][k], L[1][k], yp[1][k],
-                 R[1][k], ym[1][k], L[2][k], yp[2][k], R[2][k], ym[2][k]};
-      collide13(f, K);
-      const bool valid = x0 + k < nx;  // padding cells are stored as zero
-#pragma unroll
-      for (int p = 0; p < 13; ++p) out[p][k] = valid ? f[p] : T(0);
-    }
-    if (active)
-#pragma unroll
-      for (int p = 0; p < 13; ++p) VV::store(A.dst + p * P + row + x0, out[p]);
-  }
+  constexpr int V = V16<T>::n;
+  const int x0 = (blockIdx.x * 32 + threadIdx.x) * V;
+  for (int y = blockIdx.y * BY + threadIdx.y; y < A.ny; y += gridDim.y * BY)  // warp-uniform
+    vec_row<T, false>(A, K, y, x0, threadIdx.x, nullptr);
 }
 
 // --------------------------------------------------------------------------

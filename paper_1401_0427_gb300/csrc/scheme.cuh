@@ -96,15 +96,21 @@ __device__ __forceinline__ void equilibrium13(T h, T qx, T qy, const Consts<T>& 
   e[12] = sub(y4, pyy);
 }
 
-// Moments -> equilibria -> BGK relaxation, in place.
+// Moments -> equilibria -> BGK relaxation, in place; the moments (h, qx, qy) are
+// returned too (the collision conserves them).
 template <class T>
-__device__ __forceinline__ void collide13(T f[13], const Consts<T>& k) {
-  T h, qx, qy;
+__device__ __forceinline__ void collide13(T f[13], const Consts<T>& k, T& h, T& qx, T& qy) {
   moments13(f, h, qx, qy);
   T e[13];
   equilibrium13(h, qx, qy, k, e);
 #pragma unroll
   for (int j = 0; j < 13; ++j) f[j] = fmad(k.s, sub(e[j], f[j]), f[j]);
+}
+
+template <class T>
+__device__ __forceinline__ void collide13(T f[13], const Consts<T>& k) {
+  T h, qx, qy;
+  collide13(f, k, h, qx, qy);
 }
 
 // ---- 1D: populations f0, f+, f-, g+, g- ----

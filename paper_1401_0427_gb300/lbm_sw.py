@@ -64,6 +64,37 @@ class lbm_sw_info(ctypes.Structure):
     ]
 
 
+class lbm_sw_batch_params(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int),
+        ("nx", ctypes.POINTER(ctypes.c_int)),
+        ("ny", ctypes.POINTER(ctypes.c_int)),
+        ("precision", ctypes.c_int),
+        ("g", ctypes.c_double),
+        ("lambda_", ctypes.c_double),
+        ("s", ctypes.c_double),
+        ("a", ctypes.c_double),
+        ("bc", ctypes.c_int * 4),
+        ("inflow", (ctypes.c_double * 3) * 4),
+        ("stream", ctypes.c_void_p),
+        ("tile_rows", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int),
+        ("graph_chunk", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5),
+    ]
+
+
+class lbm_sw_batch_tuning(ctypes.Structure):
+    _fields_ = [
+        ("tile_rows", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int),
+        ("candidates", ctypes.c_int),
+        ("ms_per_step", ctypes.c_double),
+        ("tiles", ctypes.c_longlong),
+        ("cells", ctypes.c_longlong),
+    ]
+
+
 _lib = None
 
 # name -> (restype, argtypes); the complete list of entry points of include/lbm_sw.h
@@ -85,6 +116,19 @@ SIGNATURES = {
     "lbm_sw_create_error": (ctypes.c_char_p, []),
     "lbm_sw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lbm_sw_abi_version": (ctypes.c_int, []),
+    "lbm_sw_batch_params_init": (ctypes.c_int, [ctypes.POINTER(lbm_sw_batch_params)]),
+    "lbm_sw_batch_create": (ctypes.c_int, [ctypes.POINTER(lbm_sw_batch_params), ctypes.POINTER(ctypes.c_void_p)]),
+    "lbm_sw_batch_destroy": (None, [_H]),
+    "lbm_sw_batch_set_state": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_int]),
+    "lbm_sw_batch_step": (ctypes.c_int, [_H, ctypes.c_int]),
+    "lbm_sw_batch_get_moments": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_int]),
+    "lbm_sw_batch_get_populations": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+    "lbm_sw_batch_diagnostics": (ctypes.c_int, [_H, ctypes.c_int, _DP]),
+    "lbm_sw_batch_autotune": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(lbm_sw_batch_tuning)]),
+    "lbm_sw_batch_get_tuning": (ctypes.c_int, [_H, ctypes.POINTER(lbm_sw_batch_tuning)]),
+    "lbm_sw_batch_last_error": (ctypes.c_char_p, [_H]),
     "lbm_sw_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                   ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_void_p,
                                                   ctypes.c_void_p]),
@@ -202,6 +246,70 @@ def lbm_sw_diagnostics_noalloc(populations: int, dim: int, precision: int, nx: i
     _check(st, None, "lbm_sw_diagnostics_noalloc")
 
 
+def _bcheck(status: int, b, what: str) -> int:
+    if status < 0:
+        lib = load()
+        msg = lib.lbm_sw_batch_last_error(b).decode() if b else ""
+        raise LbmSwError(status, f"{what}: {msg or lib.lbm_sw_status_string(status).decode()}")
+    return status
+
+
+def lbm_sw_batch_params_init() -> lbm_sw_batch_params:
+    p = lbm_sw_batch_params()
+    _check(load().lbm_sw_batch_params_init(ctypes.byref(p)))
+    return p
+
+
+def lbm_sw_batch_create(p: lbm_sw_batch_params) -> int:
+    lib = load()
+    b = ctypes.c_void_p()
+    st = lib.lbm_sw_batch_create(ctypes.byref(p), ctypes.byref(b))
+    if st < 0:
+        raise LbmSwError(st, "lbm_sw_batch_create: " + (lib.lbm_sw_create_error().decode() or
+                                                        lib.lbm_sw_status_string(st).decode()))
+    return b.value
+
+
+def lbm_sw_batch_destroy(b: int) -> None:
+    load().lbm_sw_batch_destroy(b)
+
+
+def lbm_sw_batch_set_state(b: int, i: int, depth: int, hu: int, hv: int | None, on_device: bool) -> None:
+    _bcheck(load().lbm_sw_batch_set_state(b, int(i), depth, hu, hv, int(on_device)), b, "lbm_sw_batch_set_state")
+
+
+def lbm_sw_batch_step(b: int, n: int) -> None:
+    _bcheck(load().lbm_sw_batch_step(b, int(n)), b, "lbm_sw_batch_step")
+
+
+def lbm_sw_batch_get_moments(b: int, i: int, depth: int, hu: int, hv: int | None, on_device: bool) -> None:
+    _bcheck(load().lbm_sw_batch_get_moments(b, int(i), depth, hu, hv, int(on_device)), b, "lbm_sw_batch_get_moments")
+
+
+def lbm_sw_batch_get_populations(b: int, i: int, dst: int, on_device: bool) -> None:
+    _bcheck(load().lbm_sw_batch_get_populations(b, int(i), dst, int(on_device)), b, "lbm_sw_batch_get_populations")
+
+
+def lbm_sw_batch_diagnostics(b: int, i: int, raise_unstable: bool = True):
+    out = (ctypes.c_double * 4)()
+    st = load().lbm_sw_batch_diagnostics(b, int(i), out)
+    if st != E_UNSTABLE or raise_unstable:
+        _bcheck(st, b, "lbm_sw_batch_diagnostics")
+    return out[0], out[1], out[2], out[3], st
+
+
+def lbm_sw_batch_autotune(b: int, trial_steps: int) -> lbm_sw_batch_tuning:
+    t = lbm_sw_batch_tuning()
+    _bcheck(load().lbm_sw_batch_autotune(b, int(trial_steps), ctypes.byref(t)), b, "lbm_sw_batch_autotune")
+    return t
+
+
+def lbm_sw_batch_get_tuning(b: int) -> lbm_sw_batch_tuning:
+    t = lbm_sw_batch_tuning()
+    _bcheck(load().lbm_sw_batch_get_tuning(b, ctypes.byref(t)), b, "lbm_sw_batch_get_tuning")
+    return t
+
+
 # ---------------------------------------------------------------- convenience
 def make_params(nx: int, ny: int = 1, *, dim: int | None = None, precision: int = FP32, g: float = 1.0,
                 lam: float = 8.0, s: float = 1.8, a: float | None = None, bc=(PERIODIC,) * 4, inflow=None,
@@ -313,3 +421,77 @@ class Simulation:
 
     def info(self) -> lbm_sw_info:
         return lbm_sw_get_info(self.handle)
+
+
+class Batch:
+    """Owner of one lbm_sw_batch: many independent 2D grids advanced by one launch per step."""
+
+    def __init__(self, sizes, *, precision: int = FP32, g: float = 1.0, lam: float = 8.0, s: float = 1.8,
+                 a: float = 0.05, bc=(PERIODIC,) * 4, inflow=None, stream: int | None = None, tile_rows: int = 0,
+                 ctas_per_sm: int = 0, graph_chunk: int = 0):
+        self.sizes = [(int(nx), int(ny)) for nx, ny in sizes]
+        self._nx = (ctypes.c_int * len(self.sizes))(*[nx for nx, _ in self.sizes])
+        self._ny = (ctypes.c_int * len(self.sizes))(*[ny for _, ny in self.sizes])
+        p = lbm_sw_batch_params_init()
+        p.count, p.nx, p.ny, p.precision = len(self.sizes), self._nx, self._ny, int(precision)
+        p.g, p.lambda_, p.s, p.a = float(g), float(lam), float(s), float(a)
+        for k in range(4):
+            p.bc[k] = int(bc[k])
+        if inflow is not None:
+            for k in range(4):
+                if inflow[k] is not None:
+                    for c, v in enumerate(inflow[k]):
+                        p.inflow[k][c] = float(v)
+        p.stream = stream
+        p.tile_rows, p.ctas_per_sm, p.graph_chunk = int(tile_rows), int(ctas_per_sm), int(graph_chunk)
+        self.params = p
+        self.handle = lbm_sw_batch_create(p)
+        self.dtype = np.float64 if precision == FP64 else np.float32
+
+    def close(self):
+        if self.handle:
+            lbm_sw_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, i: int, h, hu, hv=None):
+        dev = Simulation._on_device(h)
+        if not dev:
+            h, hu = (np.ascontiguousarray(x, dtype=np.float64) for x in (h, hu))
+            hv = None if hv is None else np.ascontiguousarray(hv, dtype=np.float64)
+        lbm_sw_batch_set_state(self.handle, i, _ptr(h, dev), _ptr(hu, dev), _ptr(hv, dev), dev)
+
+    def step(self, n: int = 1):
+        lbm_sw_batch_step(self.handle, n)
+
+    def moments(self, i: int):
+        nx, ny = self.sizes[i]
+        out = [np.empty((ny, nx)) for _ in range(3)]
+        lbm_sw_batch_get_moments(self.handle, i, *[_ptr(o, False) for o in out], False)
+        return tuple(out)
+
+    def populations(self, i: int) -> np.ndarray:
+        nx, ny = self.sizes[i]
+        out = np.empty((13, ny, nx), dtype=self.dtype)
+        lbm_sw_batch_get_populations(self.handle, i, _ptr(out, False), False)
+        return out
+
+    def diagnostics(self, i: int, raise_unstable: bool = True):
+        return lbm_sw_batch_diagnostics(self.handle, i, raise_unstable)
+
+    def autotune(self, trial_steps: int = 5) -> lbm_sw_batch_tuning:
+        return lbm_sw_batch_autotune(self.handle, trial_steps)
+
+    def tuning(self) -> lbm_sw_batch_tuning:
+        return lbm_sw_batch_get_tuning(self.handle)

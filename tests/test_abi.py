@@ -134,3 +134,36 @@ def test_null_arguments(lib):
     lib.lbm_sw_destroy(None)  # NULL-safe
     for code in (0, -1, -2, -3, -4, -5, -6, -99):
         assert lib.lbm_sw_status_string(code)
+
+
+def _batch_params(**changes):
+    nx = (ctypes.c_int * 2)(8, 16)
+    ny = (ctypes.c_int * 2)(8, 4)
+    p = lbm_sw.lbm_sw_batch_params_init()
+    p.count, p.nx, p.ny = 2, nx, ny
+    for k, v in changes.items():
+        setattr(p, k, v)
+    return p, (nx, ny)
+
+
+@pytest.mark.parametrize("changes,needle", [
+    (dict(count=0), "count"),
+    (dict(nx=None), "arrays"),
+    (dict(tile_rows=3), "tile_rows"),
+    (dict(ctas_per_sm=40), "ctas_per_sm"),
+    (dict(s=-0.1), "s must"),
+    (dict(precision=5), "precision"),
+])
+def test_batch_create_rejects_bad_parameters(lib, changes, needle):
+    p, keep = _batch_params(**changes)
+    with pytest.raises(lbm_sw.LbmSwError) as ei:
+        lbm_sw.lbm_sw_batch_create(p)
+    assert ei.value.status == lbm_sw.E_ARG and needle in str(ei.value)
+
+
+def test_batch_rejects_a_zero_width_instance(lib):
+    p, keep = _batch_params()
+    keep[0][1] = 0
+    with pytest.raises(lbm_sw.LbmSwError) as ei:
+        lbm_sw.lbm_sw_batch_create(p)
+    assert "instance 1" in str(ei.value)

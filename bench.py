@@ -343,6 +343,7 @@ def variants(args, W0, stream, lbm_sw, torch):
     out["batched_256"] = batched_variant(stream, lbm_sw, torch)
     out["shock_reflection_512"] = shock_reflection_variant(stream, lbm_sw, torch)
     out["shock_tube_1d_1000"] = shock_tube_variant(stream, lbm_sw, torch)
+    out["adjoint_1024"] = adjoint_variant(stream, lbm_sw, torch)
     return out
 
 
@@ -410,6 +411,39 @@ def shock_reflection_variant(stream, lbm_sw, torch, steps: int = 2000):
             t = _timed(stream, torch, lambda: sim.step(steps))
         out[name] = {"MLUPS": n * n * steps / t / 1e6, "ms_per_step": t / steps * 1e3}
     return out
+
+
+def adjoint_variant(stream, lbm_sw, torch, steps: int = 200):
+    """Inverse-problem workload: 1024 x 1024 periodic, 8 Gaussian bumps on depth 1, T = 200,
+    FP32 states with FP64 checkpoints every ceil(sqrt(T)) steps.  One gradient = recorded
+    forward run + adjoint (segment replays + adjoint steps), against 2T plain steps."""
+    from paper_1401_0427_gb300 import inputs
+
+    n = 1024
+    h0 = inputs.gaussian_bumps_2d(n, seed=inputs.stream_seed(5, 5))[0]
+    z = np.zeros((n, n))
+    with lbm_sw.Simulation(n, n, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream) as sim:
+        sim.set_state(h0, z, z)
+        sim.step(4)
+        t_plain = _timed(stream, torch, lambda: sim.step(2 * steps))
+        g = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        g += 1e-3
+        times = []
+        for _ in range(2):
+            sim.set_state(h0, z, z)
+            tape = lbm_sw.Tape(sim, steps)
+
+            def gradient():
+                tape.record()
+                tape.adjoint(g)
+
+            times.append(_timed(stream, torch, gradient))
+            info = tape.info()
+            tape.close()
+    t_grad = min(times)
+    return {"cells": n * n, "steps": steps, "interval": info.interval, "checkpoints": info.checkpoints,
+            "checkpoint_bytes": info.checkpoint_bytes, "ms_per_gradient": t_grad * 1e3,
+            "ms_2T_plain_steps": t_plain * 1e3, "gradient_over_2T_plain": t_grad / t_plain}
 
 
 def shock_tube_variant(stream, lbm_sw, torch, steps: int = 500):

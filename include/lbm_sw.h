@@ -260,6 +260,54 @@ LBM_SW_API int lbm_sw_batch_get_tuning(const lbm_sw_batch* b, lbm_sw_batch_tunin
 /* Message of the last failure on this batch ("" if none). */
 LBM_SW_API const char* lbm_sw_batch_last_error(const lbm_sw_batch* b);
 
+/* ---- Discrete adjoint (gradients through time, 2D) ----
+ * For a loss L(W^T) of the moments after T steps, the adjoint of the fused step gives
+ * dL/dW^0 of the discrete scheme exactly (up to rounding):
+ *   Phi^T = M^T dL/dW^T,  Phi^{n-1} = J_C(W^{n-1})^T S^T Phi^n,  dL/dW^0 = D(W^0)^T Phi^0,
+ * where S is the streaming with the boundary rules (its transpose pulls in the reverse
+ * direction), M sums each family, D = df^eq/dW (the equilibria of section 3) and
+ * J_C = (1 - s) I + s D M is the Jacobian of the BGK collision (Eq. 2-relaxation).  A tape
+ * stores the state every `interval` steps (about sqrt(T) by default) in FP64; the backward
+ * pass replays each segment from its checkpoint (bit for bit: widening FP32 to FP64 is
+ * exact), keeping only the moments W^n (3 planes per step), then runs the adjoint steps.
+ * Phi and the replay use the handle's precision.  The tape owns all of its memory; the
+ * handle's own state is not touched by lbm_sw_adjoint. */
+typedef struct lbm_sw_tape lbm_sw_tape;
+
+typedef struct lbm_sw_tape_info {
+  int steps;               /* T */
+  int interval;            /* steps between checkpoints */
+  int checkpoints;         /* ceil(T / interval) */
+  int recorded;            /* 1 after lbm_sw_forward_record */
+  size_t checkpoint_bytes; /* FP64 checkpoint storage */
+  size_t replay_bytes;     /* moments of one segment, two adjoint and two replay buffers */
+} lbm_sw_tape_info;
+
+/* Tape for `steps` >= 1 steps of 2D handle h, checkpoints every `interval` steps
+ * (0 = ceil(sqrt(steps))).  Errors: LBM_SW_E_ARG (1D handle, bad counts), LBM_SW_E_NOMEM. */
+LBM_SW_API int lbm_sw_tape_create(lbm_sw* h, int steps, int interval, lbm_sw_tape** out);
+
+/* Release a tape (synchronises the owner's stream).  NULL-safe. */
+LBM_SW_API void lbm_sw_tape_destroy(lbm_sw_tape* t);
+
+/* Advance h by the tape's steps from its current state (its W^0 is the state at this
+ * call), storing the checkpoints.  Errors: LBM_SW_E_ARG (tape of another handle),
+ * LBM_SW_E_STATE (no state), LBM_SW_E_CUDA. */
+LBM_SW_API int lbm_sw_forward_record(lbm_sw* h, lbm_sw_tape* t);
+
+/* Given dL/dW^T (g_h required, g_hu and g_hv may be NULL = 0; FP64 [ny][nx]), write
+ * dL/dW^0 (d_h required, d_hu and d_hv may be NULL).  on_device selects device or host
+ * pointers for all six arrays; host calls synchronise.  Errors: LBM_SW_E_STATE (not
+ * recorded), LBM_SW_E_ARG, LBM_SW_E_CUDA. */
+LBM_SW_API int lbm_sw_adjoint(lbm_sw* h, lbm_sw_tape* t, const double* g_h, const double* g_hu, const double* g_hv,
+                              double* d_h, double* d_hu, double* d_hv, int on_device);
+
+/* Sizes of a tape. */
+LBM_SW_API int lbm_sw_tape_get_info(const lbm_sw_tape* t, lbm_sw_tape_info* out);
+
+/* Message of the last failure on this tape ("" if none). */
+LBM_SW_API const char* lbm_sw_tape_last_error(const lbm_sw_tape* t);
+
 /* Allocation-free diagnostics (the paper has no counterpart: this is a service of the
  * library, not a step of the scheme).  Some callers cannot allocate device memory at the
  * moment they need a health check of a state: a caller whose memory manager owns the whole

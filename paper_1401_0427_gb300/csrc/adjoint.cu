@@ -1,0 +1,390 @@
+// Discrete adjoint of the fused D2Q5Q4Q4 step, with sqrt(T) checkpointing.
+//
+// Forward (post-collision storage): F*^0 = E(W^0); for n = 1..T, F^n = S(F*^{n-1}),
+// W^n = M F^n (sums of the families), F*^n = C(F^n) = F^n + s (E(W^n) - F^n), where
+// S is the pull streaming with the boundary rules, E the equilibria of section 3
+// and C the BGK relaxation of Eq. 2-relaxation.  For a loss L(W^T), with
+// Phi^n = dL/dF^n (the adjoint of the pre-collision state):
+//
+//   Phi^T     = M^T dL/dW^T                       (M J_C = M: the collision conserves W)
+//   Phi^{n-1} = J_C(W^{n-1})^T S^T Phi^n,  n = T .. 1
+//   dL/dW^0   = D(W^0)^T Phi^0                    (D^T J_C^T = D^T because J_C D = D)
+//
+// with J_C(W) = (1 - s) I + s D M and D = dE/dW (13 x 3).  Per cell,
+// J_C^T psi = (1 - s) psi + s M^T (D^T psi): the adjoint step pulls psi = S^T Phi^n in
+// the reverse direction (the transposed boundary rules below), then applies this local
+// product; it needs the moments W^{n-1} only, so the replay of a segment keeps three
+// planes per step.  Checkpoints of F* every `interval` steps are stored in FP64 (exact
+// for FP32 states, so the replay repeats the forward run bit for bit).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+#include <string>
+
+#include "internal.h"
+#include "scheme.cuh"
+
+namespace lbm {
+namespace {
+
+template <class T>
+struct AdjArgs {
+  const T* __restrict__ phi_in;  // Phi^n (13 planes)
+  T* __restrict__ phi_out;       // Phi^{n-1}
+  const T* __restrict__ w;       // W^{n-1}: h, hu, hv planes
+  int nx, ny;
+  long long pitch, plane;
+  int bc[4];
+};
+
+__device__ __forceinline__ int dir_of(int p) { return p == 0 ? 0 : (p - 1) % 4 + 1; }
+__device__ __forceinline__ int ex_dir(int d) { return d == 1 ? 1 : (d == 3 ? -1 : 0); }
+__device__ __forceinline__ int ey_dir(int d) { return d == 2 ? 1 : (d == 4 ? -1 : 0); }
+__device__ __forceinline__ int mirror_pop(int p, bool xwall) {
+  const int d = dir_of(p), base = p - d;
+  if (xwall) return base + (d == 1 ? 3 : (d == 3 ? 1 : d));
+  return base + (d == 2 ? 4 : (d == 4 ? 2 : d));
+}
+__device__ __forceinline__ int side_of(int dx, int dy) {
+  return dx < 0 ? LBM_SW_SIDE_XM : dx > 0 ? LBM_SW_SIDE_XP : dy < 0 ? LBM_SW_SIDE_YM : LBM_SW_SIDE_YP;
+}
+
+// psi_q(x) = (S^T Phi)_q(x): the value of every forward pull that read F*_q(x).
+//   - the cell x + v_q pulled it (interior); beyond the front side: PERIODIC wraps,
+//     WALL hands it to the mirror partner at x (sign of the normal family), OUTFLOW and
+//     INFLOW let it leave;
+//   - an OUTFLOW ghost on the back side copied it into x itself.
+template <class T>
+__device__ __forceinline__ T reverse_pull(const AdjArgs<T>& A, int q, int x, int y) {
+  const long long P = A.plane;
+  if (q == 0) return A.phi_in[y * A.pitch + x];
+  const int d = dir_of(q), ex = ex_dir(d), ey = ey_dir(d);
+  int xf = x + ex, yf = y + ey;
+  T v = T(0);
+  if (xf >= 0 && xf < A.nx && yf >= 0 && yf < A.ny) {
+    v = A.phi_in[q * P + yf * A.pitch + xf];
+  } else {
+    const int side = side_of(ex, ey);
+    const int bc = A.bc[side];
+    if (bc == LBM_SW_BC_PERIODIC) {
+      xf = (xf + A.nx) % A.nx;
+      yf = (yf + A.ny) % A.ny;
+      v = A.phi_in[q * P + yf * A.pitch + xf];
+    } else if (bc == LBM_SW_BC_WALL) {
+      const bool xwall = side < 2;
+      const int m = mirror_pop(q, xwall);
+      const bool normal = xwall ? (q >= 5 && q <= 8) : (q >= 9);
+      const T w = A.phi_in[m * P + y * A.pitch + x];
+      v = normal ? -w : w;
+    }
+  }
+  const int xb = x - ex, yb = y - ey;
+  if (!(xb >= 0 && xb < A.nx && yb >= 0 && yb < A.ny) && A.bc[side_of(-ex, -ey)] == LBM_SW_BC_OUTFLOW)
+    v += A.phi_in[q * P + y * A.pitch + x];
+  return v;
+}
+
+// z = D(W)^T psi: vector-Jacobian product of the equilibria (closed forms of section 3
+// in W = (h, qx, qy); kappa = h/2 - (qx^2 + qy^2)/(4 g h^2), c = 1/(2 lambda)).
+template <class T>
+__device__ __forceinline__ void equilibrium_vjp(T h, T qx, T qy, const T psi[13], const Consts<T>& K, T& zh,
+                                                T& zx, T& zy) {
+  const T rh = T(1) / h;
+  const T u = qx * rh, v = qy * rh;
+  const T gh = T(2) * K.half_g * h;
+  const T inv2gh = T(2) * K.inv4g * rh;
+  const T kh = T(0.5) + (u * u + v * v) * inv2gh;  // dkappa/dh
+  const T kx = -u * inv2gh;                        // dkappa/dqx
+  const T ky = -v * inv2gh;                        // dkappa/dqy
+  const T Sf = (psi[1] + psi[3]) + (psi[2] + psi[4]);
+  const T Af = psi[0] - T(0.25) * Sf;
+  const T Df13 = psi[1] - psi[3], Df24 = psi[2] - psi[4];
+  const T Sx = (psi[5] + psi[7]) + (psi[6] + psi[8]);
+  const T Dx13 = psi[5] - psi[7], Dx24 = psi[6] - psi[8];
+  const T Sy = (psi[9] + psi[11]) + (psi[10] + psi[12]);
+  const T Dy13 = psi[9] - psi[11], Dy24 = psi[10] - psi[12];
+  const T X = Dx24 + Dy13;
+  const T c = K.c;
+  zh = K.a * kh * Af + T(0.25) * Sf + c * (Dx13 * (gh - u * u) - X * u * v + Dy24 * (gh - v * v));
+  zx = K.a * kx * Af + c * Df13 + T(0.25) * Sx + c * (T(2) * Dx13 * u + X * v);
+  zy = K.a * ky * Af + c * Df24 + T(0.25) * Sy + c * (X * u + T(2) * Dy24 * v);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) adjoint_step(const AdjArgs<T> A, const Consts<T> K) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < A.ny; y += gridDim.y * blockDim.y) {
+    if (x >= A.nx) continue;
+    T psi[13];
+#pragma unroll
+    for (int q = 0; q < 13; ++q) psi[q] = reverse_pull(A, q, x, y);
+    const long long c = static_cast<long long>(y) * A.pitch + x;
+    T zh, zx, zy;
+    equilibrium_vjp(A.w[c], A.w[A.plane + c], A.w[2 * A.plane + c], psi, K, zh, zx, zy);
+    const T oms = T(1) - K.s;
+#pragma unroll
+    for (int q = 0; q < 13; ++q) {
+      const T z = q < 5 ? zh : (q < 9 ? zx : zy);
+      A.phi_out[q * A.plane + c] = oms * psi[q] + K.s * z;
+    }
+  }
+}
+
+// Phi^T = M^T (dL/dh, dL/dhu, dL/dhv): every population of a family receives its field.
+template <class T>
+__global__ void adjoint_terminal(T* __restrict__ phi, const double* __restrict__ gh, const double* __restrict__ gu,
+                                 const double* __restrict__ gv, int nx, int ny, long long pitch, long long plane) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < ny; y += gridDim.y * blockDim.y) {
+    if (x >= nx) continue;
+    const long long i = static_cast<long long>(y) * nx + x, c = static_cast<long long>(y) * pitch + x;
+    const T a = static_cast<T>(gh[i]), b = static_cast<T>(gu ? gu[i] : 0.0), d = static_cast<T>(gv ? gv[i] : 0.0);
+#pragma unroll
+    for (int q = 0; q < 13; ++q) phi[q * plane + c] = q < 5 ? a : (q < 9 ? b : d);
+  }
+}
+
+// dL/dW^0 = D(W^0)^T Phi^0.
+template <class T>
+__global__ void adjoint_gradient(const T* __restrict__ phi, const T* __restrict__ w, const Consts<T> K, int nx,
+                                 int ny, long long pitch, long long plane, double* __restrict__ dh,
+                                 double* __restrict__ du, double* __restrict__ dv) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < ny; y += gridDim.y * blockDim.y) {
+    if (x >= nx) continue;
+    const long long i = static_cast<long long>(y) * nx + x, c = static_cast<long long>(y) * pitch + x;
+    T psi[13];
+#pragma unroll
+    for (int q = 0; q < 13; ++q) psi[q] = phi[q * plane + c];
+    T zh, zx, zy;
+    equilibrium_vjp(w[c], w[plane + c], w[2 * plane + c], psi, K, zh, zx, zy);
+    dh[i] = static_cast<double>(zh);
+    if (du) du[i] = static_cast<double>(zx);
+    if (dv) dv[i] = static_cast<double>(zy);
+  }
+}
+
+dim3 grid_for(int nx, int ny, dim3 block) {
+  const unsigned gx = (nx + block.x - 1) / block.x;
+  const long long gy = (ny + block.y - 1) / block.y;
+  return dim3(gx, static_cast<unsigned>(gy < 65535 ? gy : 65535));
+}
+
+}  // namespace
+}  // namespace lbm
+
+struct lbm_sw_tape {
+  const lbm_sw* owner = nullptr;
+  int steps = 0, interval = 0, checkpoints = 0;
+  bool recorded = false;
+  size_t state_elems = 0;  // 13 * plane
+  double* ckpt = nullptr;  // checkpoints * 13 * plane doubles
+  void* wstore = nullptr;  // interval * 3 * plane of T
+  void* phi[2] = {nullptr, nullptr};
+  void* rep[2] = {nullptr, nullptr};
+  double* grad_staging = nullptr;  // 3 * nx * ny doubles (host transfers)
+  std::string err;
+};
+
+namespace {
+
+int tfail(lbm_sw_tape* t, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (t) t->err = buf;
+  return code;
+}
+
+#define TAPE_CUDA(t, call, what)                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return tfail(t, e_ == cudaErrorMemoryAllocation ? LBM_SW_E_NOMEM : LBM_SW_E_CUDA, "%s: %s", what, \
+                   cudaGetErrorString(e_));                                                   \
+  } while (0)
+
+template <class T>
+lbm::StepArgs<T> replay_args(const lbm_sw* h, const lbm_sw_tape* t, int from) {
+  lbm::StepArgs<T> a = lbm::handle_args<T>(h, 0);
+  a.src = static_cast<const T*>(t->rep[from]);
+  a.dst = static_cast<T*>(t->rep[1 - from]);
+  return a;
+}
+
+template <class T>
+int run_adjoint(lbm_sw* h, lbm_sw_tape* t, const double* gh, const double* gu, const double* gv, double* dh,
+                double* du, double* dv) {
+  cudaStream_t st = h->stream;
+  const lbm::Consts<T> K = lbm::make_consts<T>(h->p.g, h->p.lambda, h->p.s, h->p.a);
+  const lbm::ConstsD kd = lbm::handle_consts(h);
+  const int nx = h->p.nx, ny = h->p.ny;
+  const long long P = h->plane, pitch = h->pitch;
+  const dim3 block(128, 2), grid = lbm::grid_for(nx, ny, block);
+  T* W = static_cast<T*>(t->wstore);
+  int cur = 0;
+  lbm::adjoint_terminal<T><<<grid, block, 0, st>>>(static_cast<T*>(t->phi[cur]), gh, gu, gv, nx, ny, pitch, P);
+  TAPE_CUDA(t, cudaGetLastError(), "adjoint terminal launch");
+  for (int seg = t->checkpoints - 1; seg >= 0; --seg) {
+    const int k0 = seg * t->interval;
+    const int k1 = (k0 + t->interval < t->steps) ? k0 + t->interval : t->steps;
+    // replay the segment from its checkpoint, keeping W^{k0} .. W^{k1-1}
+    TAPE_CUDA(t, (lbm::launch_convert<double, T>(t->ckpt + static_cast<size_t>(seg) * t->state_elems,
+                                                 static_cast<T*>(t->rep[0]), static_cast<long long>(t->state_elems), st)),
+              "checkpoint restore");
+    TAPE_CUDA(t, lbm::launch_moments2d_planes<T>(replay_args<T>(h, t, 0), W, st), "replay moments");
+    for (int j = 1; j < k1 - k0; ++j)
+      TAPE_CUDA(t, lbm::launch_step2d_store_w<T>(replay_args<T>(h, t, (j - 1) & 1), kd, W + 3 * P * j, st),
+                "replay step");
+    // adjoint steps n = k1 .. k0 + 1
+    for (int n = k1; n > k0; --n) {
+      lbm::AdjArgs<T> A;
+      A.phi_in = static_cast<const T*>(t->phi[cur]);
+      A.phi_out = static_cast<T*>(t->phi[1 - cur]);
+      A.w = W + 3 * P * (n - 1 - k0);
+      A.nx = nx;
+      A.ny = ny;
+      A.pitch = pitch;
+      A.plane = P;
+      for (int s = 0; s < 4; ++s) A.bc[s] = h->p.bc[s];
+      lbm::adjoint_step<T><<<grid, block, 0, st>>>(A, K);
+      TAPE_CUDA(t, cudaGetLastError(), "adjoint step launch");
+      cur ^= 1;
+    }
+  }
+  lbm::adjoint_gradient<T><<<grid, block, 0, st>>>(static_cast<const T*>(t->phi[cur]), W, K, nx, ny, pitch, P, dh, du,
+                                                    dv);
+  TAPE_CUDA(t, cudaGetLastError(), "adjoint gradient launch");
+  return LBM_SW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_sw_tape_destroy(lbm_sw_tape* t) {
+  if (!t) return;
+  if (t->owner) cudaStreamSynchronize(t->owner->stream);
+  if (t->ckpt) cudaFree(t->ckpt);
+  if (t->wstore) cudaFree(t->wstore);
+  for (int i = 0; i < 2; ++i) {
+    if (t->phi[i]) cudaFree(t->phi[i]);
+    if (t->rep[i]) cudaFree(t->rep[i]);
+  }
+  if (t->grad_staging) cudaFree(t->grad_staging);
+  delete t;
+}
+
+int lbm_sw_tape_create(lbm_sw* h, int steps, int interval, lbm_sw_tape** out) {
+  if (!out) return LBM_SW_E_ARG;
+  *out = nullptr;
+  if (!h) return LBM_SW_E_ARG;
+  if (h->p.dim != 2) {
+    h->err = "tape_create: the adjoint is available for 2D handles";
+    return LBM_SW_E_ARG;
+  }
+  if (steps < 1 || interval < 0 || interval > steps) {
+    h->err = "tape_create: need steps >= 1 and 0 <= interval <= steps";
+    return LBM_SW_E_ARG;
+  }
+  lbm_sw_tape* t = new (std::nothrow) lbm_sw_tape;
+  if (!t) return LBM_SW_E_NOMEM;
+  t->owner = h;
+  t->steps = steps;
+  t->interval = interval ? interval : static_cast<int>(std::ceil(std::sqrt(static_cast<double>(steps))));
+  t->checkpoints = (steps + t->interval - 1) / t->interval;
+  t->state_elems = static_cast<size_t>(13) * h->plane;
+  const size_t n = static_cast<size_t>(h->p.nx) * h->p.ny;
+  bool ok = cudaMalloc(&t->ckpt, sizeof(double) * t->state_elems * t->checkpoints) == cudaSuccess &&
+            cudaMalloc(&t->wstore, h->elem * 3 * h->plane * t->interval) == cudaSuccess &&
+            cudaMalloc(&t->grad_staging, sizeof(double) * 3 * n) == cudaSuccess;
+  for (int i = 0; i < 2 && ok; ++i)
+    ok = cudaMalloc(&t->phi[i], h->elem * t->state_elems) == cudaSuccess &&
+         cudaMemsetAsync(t->phi[i], 0, h->elem * t->state_elems, h->stream) == cudaSuccess &&
+         cudaMalloc(&t->rep[i], h->elem * t->state_elems) == cudaSuccess &&
+         cudaMemsetAsync(t->rep[i], 0, h->elem * t->state_elems, h->stream) == cudaSuccess;
+  if (ok) ok = cudaMemsetAsync(t->wstore, 0, h->elem * 3 * h->plane * t->interval, h->stream) == cudaSuccess;
+  if (!ok) {
+    h->err = std::string("tape_create: device allocation failed: ") + cudaGetErrorString(cudaGetLastError());
+    lbm_sw_tape_destroy(t);
+    return LBM_SW_E_NOMEM;
+  }
+  *out = t;
+  return LBM_SW_OK;
+}
+
+int lbm_sw_forward_record(lbm_sw* h, lbm_sw_tape* t) {
+  if (!h || !t) return LBM_SW_E_ARG;
+  if (t->owner != h) return tfail(t, LBM_SW_E_ARG, "forward_record: tape belongs to another handle");
+  if (!h->has_state) return tfail(t, LBM_SW_E_STATE, "forward_record: the handle has no state");
+  for (int k = 0; k < t->steps; ++k) {
+    if (k % t->interval == 0) {
+      double* dst = t->ckpt + static_cast<size_t>(k / t->interval) * t->state_elems;
+      cudaError_t e = h->p.precision == LBM_SW_FP64
+                          ? lbm::launch_convert<double, double>(static_cast<const double*>(h->buf[h->cur]), dst,
+                                                                static_cast<long long>(t->state_elems), h->stream)
+                          : lbm::launch_convert<float, double>(static_cast<const float*>(h->buf[h->cur]), dst,
+                                                               static_cast<long long>(t->state_elems), h->stream);
+      TAPE_CUDA(t, e, "checkpoint store");
+    }
+    const int rc = lbm_sw_step(h, 1);
+    if (rc != LBM_SW_OK) return tfail(t, rc, "forward_record: %s", h->err.c_str());
+  }
+  t->recorded = true;
+  return LBM_SW_OK;
+}
+
+int lbm_sw_adjoint(lbm_sw* h, lbm_sw_tape* t, const double* g_h, const double* g_hu, const double* g_hv,
+                   double* d_h, double* d_hu, double* d_hv, int on_device) {
+  if (!h || !t) return LBM_SW_E_ARG;
+  if (t->owner != h) return tfail(t, LBM_SW_E_ARG, "adjoint: tape belongs to another handle");
+  if (!t->recorded) return tfail(t, LBM_SW_E_STATE, "adjoint: call lbm_sw_forward_record first");
+  if (!g_h || !d_h) return tfail(t, LBM_SW_E_ARG, "adjoint: g_h and d_h are required");
+  const size_t n = static_cast<size_t>(h->p.nx) * h->p.ny;
+  const double *gh = g_h, *gu = g_hu, *gv = g_hv;
+  double *dh = d_h, *du = d_hu, *dv = d_hv;
+  double* s = t->grad_staging;
+  if (!on_device) {
+    TAPE_CUDA(t, cudaMemcpyAsync(s, g_h, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy g_h");
+    if (g_hu) TAPE_CUDA(t, cudaMemcpyAsync(s + n, g_hu, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy g_hu");
+    if (g_hv)
+      TAPE_CUDA(t, cudaMemcpyAsync(s + 2 * n, g_hv, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy g_hv");
+    gh = s;
+    gu = g_hu ? s + n : nullptr;
+    gv = g_hv ? s + 2 * n : nullptr;
+    // the gradient overwrites the staging only after the terminal kernel has read it
+    dh = s;
+    du = d_hu ? s + n : nullptr;
+    dv = d_hv ? s + 2 * n : nullptr;
+  }
+  const int rc = h->p.precision == LBM_SW_FP64 ? run_adjoint<double>(h, t, gh, gu, gv, dh, du, dv)
+                                               : run_adjoint<float>(h, t, gh, gu, gv, dh, du, dv);
+  if (rc != LBM_SW_OK) return rc;
+  if (!on_device) {
+    TAPE_CUDA(t, cudaMemcpyAsync(d_h, dh, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy d_h");
+    if (d_hu) TAPE_CUDA(t, cudaMemcpyAsync(d_hu, du, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy d_hu");
+    if (d_hv) TAPE_CUDA(t, cudaMemcpyAsync(d_hv, dv, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy d_hv");
+    TAPE_CUDA(t, cudaStreamSynchronize(h->stream), "adjoint synchronize");
+  }
+  return LBM_SW_OK;
+}
+
+int lbm_sw_tape_get_info(const lbm_sw_tape* t, lbm_sw_tape_info* out) {
+  if (!t || !out) return LBM_SW_E_ARG;
+  out->steps = t->steps;
+  out->interval = t->interval;
+  out->checkpoints = t->checkpoints;
+  out->recorded = t->recorded ? 1 : 0;
+  out->checkpoint_bytes = sizeof(double) * t->state_elems * t->checkpoints;
+  out->replay_bytes = t->owner->elem * (3 * t->owner->plane * t->interval + 4 * t->state_elems);
+  return LBM_SW_OK;
+}
+
+const char* lbm_sw_tape_last_error(const lbm_sw_tape* t) { return t ? t->err.c_str() : "null tape"; }
+
+}  // extern "C"

@@ -41,19 +41,10 @@ size_t state_bytes(const lbm_sw* h) { return static_cast<size_t>(h->q) * h->plan
 
 template <class T>
 lbm::StepArgs<T> args(const lbm_sw* h, int src_buf) {
-  lbm::StepArgs<T> a;
-  a.src = static_cast<const T*>(h->buf[src_buf]);
-  a.dst = static_cast<T*>(h->buf[1 - src_buf]);
-  a.inflow_feq = static_cast<const T*>(h->inflow_feq);
-  a.nx = h->p.nx;
-  a.ny = h->p.ny;
-  a.pitch = h->pitch;
-  a.plane = h->plane;
-  for (int s = 0; s < 4; ++s) a.bc[s] = h->p.bc[s];
-  return a;
+  return lbm::handle_args<T>(h, src_buf);
 }
 
-lbm::ConstsD consts(const lbm_sw* h) { return lbm::ConstsD{h->p.g, h->p.lambda, h->p.s, h->p.a}; }
+lbm::ConstsD consts(const lbm_sw* h) { return lbm::handle_consts(h); }
 
 // One step from buffer `from` into the other buffer, on stream st.
 cudaError_t launch_one_step(lbm_sw* h, int from, cudaStream_t st) {

@@ -43,6 +43,15 @@ template <class T>
 cudaError_t launch_inflow_feq2d(T* out, const int bc[4], const double inflow[4][3], const ConstsD& k,
                                 cudaStream_t st);
 
+// Fused step that also writes the moments of the new state into w_out (3 planes of the
+// population pitch), moments of a state into such planes, and element-wise conversion.
+template <class T>
+cudaError_t launch_step2d_store_w(const StepArgs<T>& a, const ConstsD& k, T* w_out, cudaStream_t st);
+template <class T>
+cudaError_t launch_moments2d_planes(const StepArgs<T>& a, T* w_out, cudaStream_t st);
+template <class Tin, class Tout>
+cudaError_t launch_convert(const Tin* in, Tout* out, long long n, cudaStream_t st);
+
 // ---- 1D launchers (kernels_1d.cu) ----
 template <class T>
 cudaError_t launch_step1d(const StepArgs<T>& a, const ConstsD& k, cudaStream_t st);
@@ -98,3 +107,24 @@ struct lbm_sw {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // CUDA graph of graph_chunk steps from buffer 0 / 1
   std::string err;
 };
+
+namespace lbm {
+
+// Kernel arguments of a step of handle h reading buffer src_buf (writing the other).
+template <class T>
+inline StepArgs<T> handle_args(const lbm_sw* h, int src_buf) {
+  StepArgs<T> a;
+  a.src = static_cast<const T*>(h->buf[src_buf]);
+  a.dst = static_cast<T*>(h->buf[1 - src_buf]);
+  a.inflow_feq = static_cast<const T*>(h->inflow_feq);
+  a.nx = h->p.nx;
+  a.ny = h->p.ny;
+  a.pitch = h->pitch;
+  a.plane = h->plane;
+  for (int s = 0; s < 4; ++s) a.bc[s] = h->p.bc[s];
+  return a;
+}
+
+inline ConstsD handle_consts(const lbm_sw* h) { return ConstsD{h->p.g, h->p.lambda, h->p.s, h->p.a}; }
+
+}  // namespace lbm

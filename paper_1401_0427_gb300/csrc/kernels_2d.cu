@@ -103,6 +103,16 @@ __global__ void __launch_bounds__(32 * BY) step2d_vec(const StepArgs<T> A, const
     vec_row<T, false>(A, K, y, x0, threadIdx.x, nullptr);
 }
 
+// The same step, also writing the moments (h, hu, hv) of the new state to three planes
+// (used by the replay of the discrete adjoint).
+template <class T, int BY>
+__global__ void __launch_bounds__(32 * BY) step2d_vec_w(const StepArgs<T> A, const Consts<T> K, T* w_out) {
+  constexpr int V = V16<T>::n;
+  const int x0 = (blockIdx.x * 32 + threadIdx.x) * V;
+  for (int y = blockIdx.y * BY + threadIdx.y; y < A.ny; y += gridDim.y * BY)
+    vec_row<T, true>(A, K, y, x0, threadIdx.x, w_out);
+}
+
 // --------------------------------------------------------------------------
 // Helpers: equilibrium initialisation, collision of dense populations, moments,
 // inflow equilibria.
@@ -155,6 +165,31 @@ __global__ void moments2d(const StepArgs<T> A, double* __restrict__ h, double* _
   }
 }
 
+// Moments of the state in A.src into three planes of the population pitch.
+template <class T>
+__global__ void moments2d_planes(const StepArgs<T> A, T* __restrict__ w) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < A.ny; y += gridDim.y * blockDim.y) {
+    if (x >= A.nx) continue;
+    T f[13];
+#pragma unroll
+    for (int p = 0; p < 13; ++p) f[p] = A.src[p * A.plane + y * A.pitch + x];
+    T d, qx, qy;
+    moments13(f, d, qx, qy);
+    const long long c = static_cast<long long>(y) * A.pitch + x;
+    w[c] = d;
+    w[A.plane + c] = qx;
+    w[2 * A.plane + c] = qy;
+  }
+}
+
+template <class Tin, class Tout>
+__global__ void convert_kernel(const Tin* __restrict__ in, Tout* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    out[i] = static_cast<Tout>(in[i]);
+}
+
 struct InflowStates {
   int bc[4];
   double w[4][3];
@@ -202,6 +237,36 @@ cudaError_t launch_step2d(const StepArgs<T>& a, const ConstsD& kd, int variant, 
 }
 
 template <class T>
+cudaError_t launch_step2d_store_w(const StepArgs<T>& a, const ConstsD& kd, T* w_out, cudaStream_t st) {
+  const Consts<T> K = make_consts<T>(kd.g, kd.lambda, kd.s, kd.a);
+  constexpr int BY = 4;
+  constexpr int V = V16<T>::n;
+  const dim3 block(32, BY);
+  const dim3 grid((a.nx + 32 * V - 1) / (32 * V),
+                  static_cast<unsigned>(std::min<long long>((a.ny + BY - 1) / BY, 65535)));
+  step2d_vec_w<T, BY><<<grid, block, 0, st>>>(a, K, w_out);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_moments2d_planes(const StepArgs<T>& a, T* w_out, cudaStream_t st) {
+  const dim3 block(128, 2);
+  moments2d_planes<T><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, w_out);
+  return cudaGetLastError();
+}
+
+template <class Tin, class Tout>
+cudaError_t launch_convert(const Tin* in, Tout* out, long long n, cudaStream_t st) {
+  const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+  convert_kernel<Tin, Tout><<<static_cast<unsigned>(blocks > 0 ? blocks : 1), 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
+template cudaError_t launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+template cudaError_t launch_convert<double, double>(const double*, double*, long long, cudaStream_t);
+
+template <class T>
 cudaError_t launch_init2d(const StepArgs<T>& a, const ConstsD& kd, const double* h, const double* hu,
                           const double* hv, cudaStream_t st) {
   const dim3 block(128, 2);
@@ -243,7 +308,9 @@ cudaError_t launch_inflow_feq2d(T* out, const int bc[4], const double inflow[4][
                                         const double*, cudaStream_t);                                      \
   template cudaError_t launch_collide2d_dense<T>(const StepArgs<T>&, const ConstsD&, const T*, cudaStream_t); \
   template cudaError_t launch_moments2d<T>(const StepArgs<T>&, double*, double*, double*, cudaStream_t);   \
-  template cudaError_t launch_inflow_feq2d<T>(T*, const int[4], const double[4][3], const ConstsD&, cudaStream_t);
+  template cudaError_t launch_inflow_feq2d<T>(T*, const int[4], const double[4][3], const ConstsD&, cudaStream_t); \
+  template cudaError_t launch_step2d_store_w<T>(const StepArgs<T>&, const ConstsD&, T*, cudaStream_t);       \
+  template cudaError_t launch_moments2d_planes<T>(const StepArgs<T>&, T*, cudaStream_t);
 
 LBM_INSTANTIATE_2D(float)
 LBM_INSTANTIATE_2D(double)

@@ -95,6 +95,17 @@ class lbm_sw_batch_tuning(ctypes.Structure):
     ]
 
 
+class lbm_sw_tape_info(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_int),
+        ("interval", ctypes.c_int),
+        ("checkpoints", ctypes.c_int),
+        ("recorded", ctypes.c_int),
+        ("checkpoint_bytes", ctypes.c_size_t),
+        ("replay_bytes", ctypes.c_size_t),
+    ]
+
+
 _lib = None
 
 # name -> (restype, argtypes); the complete list of entry points of include/lbm_sw.h
@@ -129,6 +140,12 @@ SIGNATURES = {
     "lbm_sw_batch_autotune": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(lbm_sw_batch_tuning)]),
     "lbm_sw_batch_get_tuning": (ctypes.c_int, [_H, ctypes.POINTER(lbm_sw_batch_tuning)]),
     "lbm_sw_batch_last_error": (ctypes.c_char_p, [_H]),
+    "lbm_sw_tape_create": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "lbm_sw_tape_destroy": (None, [_H]),
+    "lbm_sw_forward_record": (ctypes.c_int, [_H, _H]),
+    "lbm_sw_adjoint": (ctypes.c_int, [_H, _H] + [ctypes.c_void_p] * 6 + [ctypes.c_int]),
+    "lbm_sw_tape_get_info": (ctypes.c_int, [_H, ctypes.POINTER(lbm_sw_tape_info)]),
+    "lbm_sw_tape_last_error": (ctypes.c_char_p, [_H]),
     "lbm_sw_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                   ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_void_p,
                                                   ctypes.c_void_p]),
@@ -308,6 +325,39 @@ def lbm_sw_batch_get_tuning(b: int) -> lbm_sw_batch_tuning:
     t = lbm_sw_batch_tuning()
     _bcheck(load().lbm_sw_batch_get_tuning(b, ctypes.byref(t)), b, "lbm_sw_batch_get_tuning")
     return t
+
+
+def _tcheck(status: int, t, h, what: str) -> int:
+    if status < 0:
+        lib = load()
+        msg = (lib.lbm_sw_tape_last_error(t).decode() if t else "") or (lib.lbm_sw_last_error(h).decode() if h else "")
+        raise LbmSwError(status, f"{what}: {msg or lib.lbm_sw_status_string(status).decode()}")
+    return status
+
+
+def lbm_sw_tape_create(h: int, steps: int, interval: int = 0) -> int:
+    t = ctypes.c_void_p()
+    _tcheck(load().lbm_sw_tape_create(h, int(steps), int(interval), ctypes.byref(t)), None, h, "lbm_sw_tape_create")
+    return t.value
+
+
+def lbm_sw_tape_destroy(t: int) -> None:
+    load().lbm_sw_tape_destroy(t)
+
+
+def lbm_sw_forward_record(h: int, t: int) -> None:
+    _tcheck(load().lbm_sw_forward_record(h, t), t, h, "lbm_sw_forward_record")
+
+
+def lbm_sw_adjoint(h: int, t: int, g_h: int, g_hu: int | None, g_hv: int | None, d_h: int, d_hu: int | None,
+                   d_hv: int | None, on_device: bool) -> None:
+    _tcheck(load().lbm_sw_adjoint(h, t, g_h, g_hu, g_hv, d_h, d_hu, d_hv, int(on_device)), t, h, "lbm_sw_adjoint")
+
+
+def lbm_sw_tape_get_info(t: int) -> lbm_sw_tape_info:
+    info = lbm_sw_tape_info()
+    _tcheck(load().lbm_sw_tape_get_info(t, ctypes.byref(info)), t, None, "lbm_sw_tape_get_info")
+    return info
 
 
 # ---------------------------------------------------------------- convenience
@@ -495,3 +545,53 @@ class Batch:
 
     def tuning(self) -> lbm_sw_batch_tuning:
         return lbm_sw_batch_get_tuning(self.handle)
+
+
+class Tape:
+    """Checkpoint tape of a forward run of a 2D Simulation, for the discrete adjoint."""
+
+    def __init__(self, sim: Simulation, steps: int, interval: int = 0):
+        self.sim = sim
+        self.handle = lbm_sw_tape_create(sim.handle, steps, interval)
+
+    def close(self):
+        if self.handle:
+            lbm_sw_tape_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def record(self):
+        lbm_sw_forward_record(self.sim.handle, self.handle)
+
+    def adjoint(self, g_h, g_hu=None, g_hv=None, want_momentum: bool = False):
+        """dL/dW^0 from dL/dW^T.  numpy in, numpy out (host), or torch CUDA in, torch out."""
+        dev = Simulation._on_device(g_h)
+        ny, nx = self.sim.ny, self.sim.nx
+        if dev:
+            import torch
+
+            outs = [torch.empty((ny, nx), dtype=torch.float64, device=g_h.device)
+                    for _ in range(3 if want_momentum else 1)]
+        else:
+            g_h = np.ascontiguousarray(g_h, dtype=np.float64)
+            g_hu = None if g_hu is None else np.ascontiguousarray(g_hu, dtype=np.float64)
+            g_hv = None if g_hv is None else np.ascontiguousarray(g_hv, dtype=np.float64)
+            outs = [np.empty((ny, nx)) for _ in range(3 if want_momentum else 1)]
+        d = [outs[0], outs[1] if want_momentum else None, outs[2] if want_momentum else None]
+        lbm_sw_adjoint(self.sim.handle, self.handle, _ptr(g_h, dev), _ptr(g_hu, dev), _ptr(g_hv, dev),
+                       _ptr(d[0], dev), _ptr(d[1], dev), _ptr(d[2], dev), dev)
+        return tuple(outs) if want_momentum else outs[0]
+
+    def info(self) -> lbm_sw_tape_info:
+        return lbm_sw_tape_get_info(self.handle)

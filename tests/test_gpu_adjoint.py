@@ -1,0 +1,174 @@
+"""Discrete adjoint (lbm_sw_tape_* / lbm_sw_adjoint) against complex-step derivatives of
+the FP64 oracle.
+
+For L = 1/2 sum (h_T - h_obs)^2 after T steps from f = f^eq(W0), the directional
+derivative dL/dW0 . delta from the GPU adjoint must equal Im L(W0 + i eps delta) / eps
+computed by the oracle in complex arithmetic (the scheme is analytic in W0; eps = 1e-30),
+on random directions and single cells, for periodic and mixed (wall / outflow / inflow)
+boundaries, in the h and hu components.  FP64 to 1e-9; FP32 (FP32 states and adjoint,
+FP64 checkpoints) to 2e-3 relative (the adjoint accumulates FP32 rounding over T steps).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_0427_gb300 import inputs, lbm_sw
+
+from gpu_helpers import torch_stream
+
+pytestmark = pytest.mark.gpu
+
+P, W, O, I = lbm_sw.PERIODIC, lbm_sw.WALL, lbm_sw.OUTFLOW, lbm_sw.INFLOW
+INFLOW = [(1.1, 0.1, 0.0), (1.0, 0.0, 0.0), (1.05, 0.0, 0.08), (1.0, 0.0, 0.0)]
+
+
+def _workload(n, seed_true=5, seed_guess=6):
+    h_true = inputs.gaussian_bumps_2d(n, seed=inputs.stream_seed(5, seed_true))[0]
+    h_guess = 1.0 + 0.5 * (h_true - 1.0)
+    return h_true, h_guess
+
+
+def _oracle_hT(W0, steps, p):
+    F = oracle.run_2d(oracle.equilibrium_2d(*W0, p), steps, p)
+    return oracle.moments_2d(F, p)[0]
+
+
+def _oracle_directional(W0, dW, steps, p, h_obs):
+    """Im L(W0 + i eps dW) / eps with the oracle in complex arithmetic."""
+    eps = 1e-30
+    Wc = [W0[k] + 1j * eps * dW[k] for k in range(3)]
+    F = oracle.run_2d_cplx(oracle.equilibrium_2d_cplx(*Wc, p), steps, p)
+    hT = F[0] + ((F[1] + F[3]) + (F[2] + F[4]))
+    L = 0.5 * ((hT - h_obs) ** 2).sum()
+    return L.imag / eps
+
+
+def _gpu_gradient(W0, steps, h_obs, *, precision, bc=(P,) * 4, interval=0):
+    ny, nx = W0[0].shape
+    with lbm_sw.Simulation(nx, ny, precision=precision, bc=bc, inflow=INFLOW, stream=torch_stream()) as sim:
+        sim.set_state(*W0)
+        with lbm_sw.Tape(sim, steps, interval) as tape:
+            tape.record()
+            hT = sim.moments()[0]
+            grads = tape.adjoint(hT - h_obs, want_momentum=True)
+            info = tape.info()
+    return grads, hT, info
+
+
+def _directions(n, count, seed):
+    out = [inputs.uniform(seed + k, n * n, -1, 1).reshape(n, n) for k in range(count)]
+    rng = np.random.default_rng(seed)
+    for _ in range(count):
+        e = np.zeros((n, n))
+        e[rng.integers(n), rng.integers(n)] = 1.0
+        out.append(e)
+    return out
+
+
+def test_fp64_gradient_matches_complex_step_periodic_64():
+    n, steps = 64, 200
+    h_true, h_guess = _workload(n)
+    z = np.zeros((n, n))
+    p = oracle.params(n, n, a=0.05)
+    h_obs = _oracle_hT((h_true, z, z), steps, p)
+    (gh, gu, gv), hT, info = _gpu_gradient((h_guess, z, z), steps, h_obs, precision=lbm_sw.FP64)
+    assert info.interval == 15 and info.checkpoints == 14
+    for d in _directions(n, 6, 300):
+        want = _oracle_directional((h_guess, z, z), (d, z, z), steps, p, h_obs)
+        got = float((gh * d).sum())
+        assert abs(got - want) <= 1e-9 * max(abs(want), 1e-3), (got, want)
+
+
+@pytest.mark.parametrize("bc", [(W, O, I, W), (I, W, P, P), (O, O, W, W)], ids=["WOIW", "IWPP", "OOWW"])
+def test_fp64_gradient_matches_complex_step_mixed_boundaries(bc):
+    nx, ny, steps = 24, 16, 30
+    W0 = [x.reshape(ny, nx) for x in inputs.random_states(nx * ny, seed=410, h=(0.8, 1.4), speed=0.25)]
+    W1 = [x.reshape(ny, nx) for x in inputs.random_states(nx * ny, seed=411, h=(0.8, 1.4), speed=0.25)]
+    p = oracle.params(nx, ny, a=0.05, bc=bc, inflow=INFLOW)
+    h_obs = _oracle_hT(W1, steps, p)
+    grads, _, _ = _gpu_gradient(W0, steps, h_obs, precision=lbm_sw.FP64, bc=bc)
+    rng = np.random.default_rng(412)
+    for comp in range(3):
+        for k in range(3):
+            d = rng.uniform(-1, 1, (ny, nx))
+            dW = [np.zeros((ny, nx)) for _ in range(3)]
+            dW[comp] = d
+            want = _oracle_directional(W0, dW, steps, p, h_obs)
+            got = float((grads[comp] * d).sum())
+            assert abs(got - want) <= 1e-9 * max(abs(want), 1e-3), (comp, got, want)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    """The segment logic must not change the result: only rounding may differ (at a
+    checkpoint the moments are summed from the stored post-collision state, inside a
+    replayed step from the pre-collision one; the collision conserves them exactly in
+    exact arithmetic only)."""
+    nx, ny, steps = 40, 24, 37
+    W0 = [x.reshape(ny, nx) for x in inputs.random_states(nx * ny, seed=420, h=(0.8, 1.4), speed=0.25)]
+    h_obs = np.ones((ny, nx))
+    ref = None
+    for interval in (1, 4, 7, 0, 37):
+        for prec in (lbm_sw.FP64,):
+            g, _, info = _gpu_gradient(W0, steps, h_obs, precision=prec, bc=(W, O, P, P), interval=interval)
+            if ref is None:
+                ref = g
+            else:
+                for a, b in zip(g, ref):
+                    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), interval
+
+
+def test_fp32_gradient_matches_complex_step_64():
+    n, steps = 64, 200
+    h_true, h_guess = _workload(n)
+    z = np.zeros((n, n))
+    p = oracle.params(n, n, a=0.05)
+    h_obs = _oracle_hT((h_true, z, z), steps, p)
+    (gh, _, _), _, _ = _gpu_gradient((h_guess, z, z), steps, h_obs, precision=lbm_sw.FP32)
+    for d in _directions(n, 4, 500)[:6]:
+        want = _oracle_directional((h_guess, z, z), (d, z, z), steps, p, h_obs)
+        got = float((gh * d).sum())
+        assert abs(got - want) <= 2e-3 * max(abs(want), 1e-3), (got, want)
+
+
+def test_inverse_problem_workload_1024():
+    """1024 x 1024 periodic, 8 Gaussian bumps, T = 200, FP32 with FP64 checkpoints: the FP32
+    gradient against the FP64 one (relative L2) and one direction against the oracle."""
+    n, steps = 1024, 200
+    h_true, h_guess = _workload(n)
+    z = np.zeros((n, n))
+    p = oracle.params(n, n, a=0.05)
+    h_obs = _oracle_hT((h_true, z, z), steps, p)
+    (g64, _, _), _, _ = _gpu_gradient((h_guess, z, z), steps, h_obs, precision=lbm_sw.FP64)
+    (g32, _, _), _, info = _gpu_gradient((h_guess, z, z), steps, h_obs, precision=lbm_sw.FP32)
+    assert info.checkpoints == 14 and info.checkpoint_bytes == 14 * 13 * 1024 * 1024 * 8
+    assert np.linalg.norm(g32 - g64) <= 2e-3 * np.linalg.norm(g64)
+    d = inputs.uniform(77, n * n, -1, 1).reshape(n, n)
+    want = _oracle_directional((h_guess, z, z), (d, z, z), steps, p, h_obs)
+    assert abs(float((g64 * d).sum()) - want) <= 1e-9 * abs(want)
+
+
+def test_autograd_function_and_recovery():
+    import torch
+
+    from paper_1401_0427_gb300 import adjoint
+
+    n, steps = 128, 100
+    h_true, h_guess = _workload(n)
+    dev = torch.device("cuda")
+    with lbm_sw.Simulation(n, n, precision=lbm_sw.FP64, stream=torch_stream()) as sim:
+        ht = torch.tensor(h_true, device=dev)
+        h_obs = adjoint.run(ht, sim, steps).detach()
+        h0 = torch.tensor(h_guess, device=dev, requires_grad=True)
+        loss = 0.5 * ((adjoint.run(h0, sim, steps) - h_obs) ** 2).sum()
+        loss.backward()
+        g_auto = h0.grad.cpu().numpy()
+        (g_tape, _, _), _, _ = _gpu_gradient((h_guess, np.zeros((n, n)), np.zeros((n, n))), steps,
+                                             h_obs.cpu().numpy(), precision=lbm_sw.FP64)
+        assert np.allclose(g_auto, g_tape, rtol=0, atol=1e-12 * np.abs(g_tape).max())
+        h_fit, losses = adjoint.recover_initial_depth(h_obs, sim, steps, torch.tensor(h_guess, device=dev),
+                                                      iterations=15)
+    assert losses[-1] < 0.05 * losses[0]
+    err0 = np.abs(h_guess - h_true).mean()
+    err1 = np.abs(h_fit.cpu().numpy() - h_true).mean()
+    assert err1 < 0.5 * err0

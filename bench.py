@@ -488,6 +488,60 @@ def end_to_end(W0, stream, lbm_sw, torch, jobs: int = 3):
             "lb_steps_per_step": JOB_STEPS, "jobs": jobs, "seconds": dt}
 
 
+def profile_case(args, local):
+    """Run one kernel family for --warmup + --steps iterations so that a profiler can
+    capture it (prints a short JSON summary, not the benchmark line)."""
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1401_0427_gb300 import build as libbuild
+    from paper_1401_0427_gb300 import inputs, lbm_sw
+
+    libbuild.build()
+    stream = torch.cuda.current_stream()
+    n = args.side
+    out = {"case": args.case, "side": n, "steps": args.steps, "warmup": args.warmup}
+    if args.case == "batched":
+        table = inputs.batched_instances(256)[:args.count]
+        sizes = [(k, k) for k, _, _ in table]
+        with lbm_sw.Batch(sizes, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream, tile_rows=1,
+                          ctas_per_sm=0, graph_chunk=-1) as b:
+            for i, (k, hin, r) in enumerate(table):
+                b.set_state(i, *inputs.circular_dam_break_2d(k, seed=None, h_in=hin, radius=r))
+            b.step(args.warmup)
+            t = _timed(stream, torch, lambda: b.step(args.steps))
+            out["cells"] = sum(k * k for k, _ in sizes)
+    elif args.case == "adjoint":
+        h0 = inputs.gaussian_bumps_2d(n, seed=inputs.stream_seed(5, 5))[0]
+        z = np.zeros((n, n))
+        prec = lbm_sw.FP64 if args.precision == "fp64" else lbm_sw.FP32
+        with lbm_sw.Simulation(n, n, precision=prec, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream) as sim:
+            sim.set_state(h0, z, z)
+            with lbm_sw.Tape(sim, args.steps) as tape:
+                tape.record()
+                g = torch.full((n, n), 1e-3, dtype=torch.float64, device="cuda")
+                t = _timed(stream, torch, lambda: tape.adjoint(g))
+        out["cells"] = n * n
+    elif args.case == "shock_tube":
+        h, q = inputs.dam_break_1d(1000)
+        with lbm_sw.Simulation(1000, 1, dim=1, precision=lbm_sw.FP64, lam=LAM, s=S_RATE, a=0.15,
+                               bc=(lbm_sw.WALL, lbm_sw.WALL), stream=stream.cuda_stream, graph_chunk=-1) as sim:
+            sim.set_state(h, q)
+            sim.step(args.warmup)
+            t = _timed(stream, torch, lambda: sim.step(args.steps))
+        out["cells"] = 1000
+    else:  # diag
+        W0 = inputs.circular_dam_break_2d(n, seed=inputs.stream_seed(3))
+        with lbm_sw.Simulation(n, n, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream) as sim:
+            sim.set_state(*W0)
+            for _ in range(args.warmup):
+                sim.diagnostics()
+            t = _timed(stream, torch, lambda: [sim.diagnostics() for _ in range(args.steps)])
+        out["cells"] = n * n
+    out["seconds"] = t
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -497,14 +551,19 @@ def main():
     ap.add_argument("--quick", action="store_true", help="timed loop only (no variants, e2e, CPU baseline)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--side", type=int, default=4096, help="grid side (profiling of smaller cases only)")
+    ap.add_argument("--count", type=int, default=256, help="instances of the batched profiling case")
+    ap.add_argument("--case", choices=["step", "batched", "adjoint", "shock_tube", "diag"], default="step",
+                    help="kernel to run for profiling (only 'step' prints the benchmark line)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
                     help="population precision of the timed loop (fp32 is the workload)")
     args = ap.parse_args()
-    if args.warmup < 3:
+    if args.warmup < 3 and args.case == "step":
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.case != "step":
+        profile_case(args, local)
     else:
         run_ours(args, world, rank, local)
 

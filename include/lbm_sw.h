@@ -99,11 +99,14 @@ typedef struct lbm_sw lbm_sw;
 #define LBM_SW_POST_COLLISION 0 /* stored as given */
 #define LBM_SW_PRE_COLLISION 1  /* collided on the device first (moments, equilibria, relaxation) */
 
-/* 2D step kernel variants */
-#define LBM_SW_KERNEL_AUTO 0   /* library choice (currently VEC) */
-#define LBM_SW_KERNEL_SIMPLE 1 /* one thread per cell, scalar loads */
-#define LBM_SW_KERNEL_VEC 2    /* 16-byte vectors along x (4 FP32 or 2 FP64 cells per thread),
-                                  x-neighbours exchanged with warp shuffles */
+/* step kernel variants */
+#define LBM_SW_KERNEL_AUTO 0    /* library choice: VEC in 2D, CLUSTER in 1D when the line fits */
+#define LBM_SW_KERNEL_SIMPLE 1  /* one launch per step, one thread per cell, scalar loads */
+#define LBM_SW_KERNEL_VEC 2     /* 2D: 16-byte vectors along x (4 FP32 or 2 FP64 cells per thread),
+                                   x-neighbours exchanged with warp shuffles */
+#define LBM_SW_KERNEL_CLUSTER 3 /* 1D: all n steps of lbm_sw_step in one thread-block-cluster
+                                   launch, the line held in shared memory (up to 16384 cells on a
+                                   GB300; longer lines use SIMPLE) */
 
 typedef struct lbm_sw_params {
   int dim;             /* 1 (D1Q3Q2) or 2 (D2Q5Q4Q4) */
@@ -116,7 +119,7 @@ typedef struct lbm_sw_params {
   int bc[4];           /* LBM_SW_BC_* for sides x-, x+, y-, y+ (y sides unused in 1D) */
   double inflow[4][3]; /* (h, hu, hv) imposed on INFLOW sides */
   void* stream;        /* cudaStream_t borrowed from the caller (NULL = legacy default) */
-  int kernel;          /* LBM_SW_KERNEL_* (2D only) */
+  int kernel;          /* LBM_SW_KERNEL_*: AUTO, SIMPLE, VEC (2D) or CLUSTER (1D) */
   int graph_chunk;     /* steps per captured CUDA graph in lbm_sw_step; 0 = default, < 0 = off */
   int reserved[6];     /* must be zero */
 } lbm_sw_params;

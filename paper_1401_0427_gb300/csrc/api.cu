@@ -104,8 +104,10 @@ int validate(const lbm_sw_params* p, lbm_sw* h) {
   for (int pair = 0; pair < nsides; pair += 2)
     if ((p->bc[pair] == LBM_SW_BC_PERIODIC) != (p->bc[pair + 1] == LBM_SW_BC_PERIODIC))
       return fail(h, LBM_SW_E_ARG, "periodic sides come in pairs (bc[%d], bc[%d])", pair, pair + 1);
-  if (p->kernel < LBM_SW_KERNEL_AUTO || p->kernel > LBM_SW_KERNEL_VEC)
+  if (p->kernel < LBM_SW_KERNEL_AUTO || p->kernel > LBM_SW_KERNEL_CLUSTER)
     return fail(h, LBM_SW_E_ARG, "kernel must be a LBM_SW_KERNEL_* value");
+  if ((p->dim == 2 && p->kernel == LBM_SW_KERNEL_CLUSTER) || (p->dim == 1 && p->kernel == LBM_SW_KERNEL_VEC))
+    return fail(h, LBM_SW_E_ARG, "kernel: CLUSTER is for 1D handles, VEC for 2D handles");
   for (int r = 0; r < 6; ++r)
     if (p->reserved[r] != 0) return fail(h, LBM_SW_E_ARG, "reserved fields must be zero");
   return LBM_SW_OK;
@@ -193,7 +195,10 @@ int lbm_sw_create(const lbm_sw_params* p, lbm_sw** out) {
   h->elem = p->precision == LBM_SW_FP64 ? 8 : 4;
   h->pitch = round_up(p->nx, 32);
   h->plane = round_up(h->pitch * p->ny, 64);  // 256-byte aligned planes in FP32 and FP64
-  h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? LBM_SW_KERNEL_VEC : p->kernel;
+  if (p->dim == 2)
+    h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? LBM_SW_KERNEL_VEC : p->kernel;
+  else
+    h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? LBM_SW_KERNEL_CLUSTER : p->kernel;
   h->graph_chunk = p->graph_chunk == 0 ? 64 : (p->graph_chunk < 0 ? 0 : p->graph_chunk + (p->graph_chunk & 1));
 
   auto bail = [&](int code) {
@@ -270,6 +275,19 @@ int lbm_sw_step(lbm_sw* h, int n) {
   if (!h) return LBM_SW_E_ARG;
   if (n < 0) return fail(h, LBM_SW_E_ARG, "step: n must be >= 0 (got %d)", n);
   if (!h->has_state) return fail(h, LBM_SW_E_STATE, "step: no state set (call set_state or set_populations)");
+  if (h->p.dim == 1 && h->kernel == LBM_SW_KERNEL_CLUSTER && n > 0) {
+    const bool fp64 = h->p.precision == LBM_SW_FP64;
+    const int max_cells = fp64 ? lbm::cluster1d_max_cells<double>() : lbm::cluster1d_max_cells<float>();
+    if (h->p.nx <= max_cells) {
+      cudaError_t e = fp64 ? lbm::launch_step1d_cluster<double>(args<double>(h, h->cur), consts(h), n, h->stream)
+                           : lbm::launch_step1d_cluster<float>(args<float>(h, h->cur), consts(h), n, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cluster step launch");
+      h->cur ^= 1;
+      h->steps_done += n;
+      h->launches += 1;
+      return LBM_SW_OK;
+    }
+  }
   while (n > 0) {
     if (h->graph_chunk > 0 && n >= h->graph_chunk) {
       if (!h->graph[h->cur]) {
@@ -406,7 +424,12 @@ int lbm_sw_synchronize(lbm_sw* h) {
 int lbm_sw_get_info(const lbm_sw* h, lbm_sw_info* out) {
   if (!h || !out) return LBM_SW_E_ARG;
   out->q = h->q;
-  out->kernel = h->p.dim == 1 ? LBM_SW_KERNEL_SIMPLE : h->kernel;
+  out->kernel = h->kernel;
+  if (h->p.dim == 1 && h->kernel == LBM_SW_KERNEL_CLUSTER) {
+    const int max_cells = h->p.precision == LBM_SW_FP64 ? lbm::cluster1d_max_cells<double>()
+                                                        : lbm::cluster1d_max_cells<float>();
+    if (h->p.nx > max_cells) out->kernel = LBM_SW_KERNEL_SIMPLE;
+  }
   out->pitch = static_cast<size_t>(h->pitch);
   out->population_bytes = static_cast<size_t>(h->q) * h->p.nx * h->p.ny * h->elem;
   out->bytes_per_update = 2.0 * h->q * static_cast<double>(h->elem);

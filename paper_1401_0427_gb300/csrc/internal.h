@@ -55,6 +55,12 @@ cudaError_t launch_convert(const Tin* in, Tout* out, long long n, cudaStream_t s
 // ---- 1D launchers (kernels_1d.cu) ----
 template <class T>
 cudaError_t launch_step1d(const StepArgs<T>& a, const ConstsD& k, cudaStream_t st);
+// All nsteps steps of a line in one thread-block-cluster launch (src -> dst); lines of up to
+// cluster1d_max_cells<T>() cells.
+template <class T>
+int cluster1d_max_cells();
+template <class T>
+cudaError_t launch_step1d_cluster(const StepArgs<T>& a, const ConstsD& k, int nsteps, cudaStream_t st);
 template <class T>
 cudaError_t launch_init1d(const StepArgs<T>& a, const ConstsD& k, const double* h, const double* hu,
                           cudaStream_t st);

@@ -3,11 +3,13 @@
 // Pass 1: each block walks whole rows (grid-stride over rows), forms h, hu, hv of
 // every cell in the storage precision (pair-symmetric sums), accumulates them in
 // FP64, keeps min h and counts cells with NaN/Inf or h <= 0; warp shuffles then
-// shared memory reduce the block to one partial of 5 doubles.
+// shared memory reduce the block to one partial of 5 doubles.  The handle's aligned
+// planes are read with 16-byte vectors; any other pitch with scalar loads.
 // Pass 2: one block folds the partials in a fixed order.  Same input, same bits.
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <type_traits>
 
 #include "internal.h"
 #include "scheme.cuh"
@@ -97,6 +99,59 @@ __global__ void __launch_bounds__(kThreads) diag_partials(const StepArgs<T> A, d
   }
 }
 
+// Pass 1 with 16-byte vector loads (V = 4 FP32 or 2 FP64 cells per thread and plane); needs
+// rows that start 16-byte aligned and a pitch that is a multiple of V (the handle's layout).
+template <class T, int Q>
+__global__ void __launch_bounds__(kThreads) diag_partials_vec(const StepArgs<T> A, double* __restrict__ part) {
+  constexpr int V = 16 / sizeof(T);
+  using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  Acc a{0.0, 0.0, 0.0, DBL_MAX, 0.0};
+  for (int y = blockIdx.x; y < A.ny; y += gridDim.x) {
+    const T* row = A.src + static_cast<long long>(y) * A.pitch;
+    for (int x0 = threadIdx.x * V; x0 < A.nx; x0 += kThreads * V) {
+      T f[Q][V];
+#pragma unroll
+      for (int p = 0; p < Q; ++p) {
+        const Vec t = __ldg(reinterpret_cast<const Vec*>(row + p * A.plane + x0));
+        const T* tv = reinterpret_cast<const T*>(&t);
+#pragma unroll
+        for (int k = 0; k < V; ++k) f[p][k] = tv[k];
+      }
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        if (x0 + k >= A.nx) break;
+        T h, qx, qy = T(0);
+        if constexpr (Q == 13) {
+          T g[13];
+#pragma unroll
+          for (int p = 0; p < 13; ++p) g[p] = f[p][k];
+          moments13(g, h, qx, qy);
+        } else {
+          T g[5];
+#pragma unroll
+          for (int p = 0; p < 5; ++p) g[p] = f[p][k];
+          moments5(g, h, qx);
+        }
+        const double hd = static_cast<double>(h), ud = static_cast<double>(qx), vd = static_cast<double>(qy);
+        a.h += hd;
+        a.hu += ud;
+        a.hv += vd;
+        a.hmin = fmin(a.hmin, hd);
+        if (!(hd > 0.0) || !isfinite(hd) || !isfinite(ud) || !isfinite(vd)) a.bad += 1.0;
+      }
+    }
+  }
+  a = block_reduce(a);
+  if (threadIdx.x == 0) {
+    double* o = part + 5 * blockIdx.x;
+    o[0] = a.h;
+    o[1] = a.hu;
+    o[2] = a.hv;
+    o[3] = a.hmin;
+    o[4] = a.bad;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) diag_final(const double* __restrict__ part, int nblocks,
                                                       double* __restrict__ out) {
   Acc a{0.0, 0.0, 0.0, DBL_MAX, 0.0};
@@ -122,9 +177,9 @@ template <class T>
 cudaError_t launch_diagnostics(const StepArgs<T>& a, int q, double* partials, double* out, cudaStream_t st) {
   const int nblocks = a.ny < kMaxBlocks ? a.ny : kMaxBlocks;
   if (q == 13)
-    diag_partials<T, 13><<<nblocks, kThreads, 0, st>>>(a, partials);
+    diag_partials_vec<T, 13><<<nblocks, kThreads, 0, st>>>(a, partials);
   else
-    diag_partials<T, 5><<<nblocks, kThreads, 0, st>>>(a, partials);
+    diag_partials_vec<T, 5><<<nblocks, kThreads, 0, st>>>(a, partials);
   diag_final<<<1, kThreads, 0, st>>>(partials, nblocks, out);
   return cudaGetLastError();
 }

@@ -22,7 +22,7 @@ PERIODIC, WALL, OUTFLOW, INFLOW = 0, 1, 2, 3
 XM, XP, YM, YP = 0, 1, 2, 3
 FP32, FP64 = 0, 1
 POST_COLLISION, PRE_COLLISION = 0, 1
-KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_VEC = 0, 1, 2
+KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_VEC, KERNEL_CLUSTER = 0, 1, 2, 3
 
 OK, E_ARG, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE, E_NOMEM = 0, -1, -2, -3, -4, -5, -6
 

@@ -127,4 +127,4 @@ def test_state_errors_and_counters():
 def test_1d_info():
     with lbm_sw.Simulation(1000, 1, dim=1, precision=lbm_sw.FP64, bc=(W, W), stream=torch_stream()) as sim:
         info = sim.info()
-        assert info.q == 5 and info.bytes_per_update == 80.0
+        assert info.q == 5 and info.bytes_per_update == 80.0 and info.kernel == lbm_sw.KERNEL_CLUSTER

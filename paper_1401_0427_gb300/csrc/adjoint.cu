@@ -1,4 +1,5 @@
-// Discrete adjoint of the fused D2Q5Q4Q4 step, with sqrt(T) checkpointing.
+// Discrete adjoint of the fused D2Q5Q4Q4 step, with sqrt(T) checkpointing (a scalar
+// one-thread-per-cell kernel for the SIMPLE kernel choice, a vectorised one otherwise).
 //
 // Forward (post-collision storage): F*^0 = E(W^0); for n = 1..T, F^n = S(F*^{n-1}),
 // W^n = M F^n (sums of the families), F*^n = C(F^n) = F^n + s (E(W^n) - F^n), where
@@ -26,6 +27,7 @@
 
 #include "internal.h"
 #include "scheme.cuh"
+#include "step2d_vec.cuh"
 
 namespace lbm {
 namespace {
@@ -130,6 +132,177 @@ __global__ void __launch_bounds__(256) adjoint_step(const AdjArgs<T> A, const Co
       const T z = q < 5 ? zh : (q < 9 ? zx : zy);
       A.phi_out[q * A.plane + c] = oms * psi[q] + K.s * z;
     }
+  }
+}
+
+// The adjoint step with the layout of the vectorised forward step: a thread owns V
+// consecutive cells of a row, loads 16-byte vectors of Phi and W, and shifts the
+// x-moving families by one cell with warp shuffles, in the reverse direction of the
+// forward pull (+x movers read x + 1, -x movers x - 1, +y movers row y + 1, -y movers
+// row y - 1).  Front-side rules (the side a population leaves through) are applied
+// first, then the back-side OUTFLOW additions, as in reverse_pull.
+template <class T, int BY>
+__global__ void __launch_bounds__(32 * BY) adjoint_step_vec(const AdjArgs<T> A, const Consts<T> K) {
+  using VV = V16<T>;
+  constexpr int V = VV::n;
+  const int lane = threadIdx.x;
+  const int nx = A.nx, ny = A.ny;
+  const long long P = A.plane;
+  const T* __restrict__ S = A.phi_in;
+  const int x0 = (blockIdx.x * 32 + lane) * V;
+  const bool active = x0 < nx;
+  for (int y = blockIdx.y * BY + threadIdx.y; y < ny; y += gridDim.y * BY) {  // warp-uniform
+    const long long row = static_cast<long long>(y) * A.pitch;
+    T c0[V], xp[3][V], xm[3][V], yp[3][V], ym[3][V], w[3][V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      c0[k] = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) xp[c][k] = xm[c][k] = yp[c][k] = ym[c][k] = w[c][k] = T(0);
+    }
+    if (active) {
+      VV::load(S + row + x0, c0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        VV::load(S + (1 + 4 * c) * P + row + x0, xp[c]);
+        VV::load(S + (3 + 4 * c) * P + row + x0, xm[c]);
+        VV::load(A.w + c * P + row + x0, w[c]);
+      }
+    }
+    // +y movers (2, 6, 10) were pulled by row y + 1
+    {
+      const int bcs = A.bc[LBM_SW_SIDE_YP];
+      if (y < ny - 1 || bcs == LBM_SW_BC_PERIODIC) {
+        const long long r = static_cast<long long>(y < ny - 1 ? y + 1 : 0) * A.pitch;
+        if (active)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) VV::load(S + (2 + 4 * c) * P + r + x0, yp[c]);
+      } else if (bcs == LBM_SW_BC_WALL) {  // handed to the mirror partners 4, 8, 12 at this row
+        if (active)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) VV::load(S + (4 + 4 * c) * P + row + x0, yp[c]);
+#pragma unroll
+        for (int k = 0; k < V; ++k) yp[2][k] = -yp[2][k];
+      }
+      if (y == 0 && A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_OUTFLOW && active) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T o[V];
+          VV::load(S + (2 + 4 * c) * P + row + x0, o);
+#pragma unroll
+          for (int k = 0; k < V; ++k) yp[c][k] = yp[c][k] + o[k];
+        }
+      }
+    }
+    // -y movers (4, 8, 12) were pulled by row y - 1
+    {
+      const int bcs = A.bc[LBM_SW_SIDE_YM];
+      if (y > 0 || bcs == LBM_SW_BC_PERIODIC) {
+        const long long r = static_cast<long long>(y > 0 ? y - 1 : ny - 1) * A.pitch;
+        if (active)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) VV::load(S + (4 + 4 * c) * P + r + x0, ym[c]);
+      } else if (bcs == LBM_SW_BC_WALL) {
+        if (active)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) VV::load(S + (2 + 4 * c) * P + row + x0, ym[c]);
+#pragma unroll
+        for (int k = 0; k < V; ++k) ym[2][k] = -ym[2][k];
+      }
+      if (y == ny - 1 && A.bc[LBM_SW_SIDE_YP] == LBM_SW_BC_OUTFLOW && active) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T o[V];
+          VV::load(S + (4 + 4 * c) * P + row + x0, o);
+#pragma unroll
+          for (int k = 0; k < V; ++k) ym[c][k] = ym[c][k] + o[k];
+        }
+      }
+    }
+    // x: R[c][k] = value at x0 + k + 1 of the +x movers, L[c][k] = at x0 + k - 1 of the -x movers
+    T R[3][V], L[3][V];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T dn = __shfl_down_sync(kFullMask, xp[c][0], 1);
+      T up = __shfl_up_sync(kFullMask, xm[c][V - 1], 1);
+      if (lane == 31) dn = (x0 + V < nx) ? S[(1 + 4 * c) * P + row + x0 + V] : T(0);
+      if (lane == 0) up = (active && x0 > 0) ? S[(3 + 4 * c) * P + row + x0 - 1] : T(0);
+#pragma unroll
+      for (int k = 0; k < V - 1; ++k) R[c][k] = xp[c][k + 1];
+      R[c][V - 1] = dn;
+      L[c][0] = up;
+#pragma unroll
+      for (int k = 1; k < V; ++k) L[c][k] = xm[c][k - 1];
+    }
+    const int kk = nx - 1 - x0;
+    const bool right = kk >= 0 && kk < V;
+    // front sides: +x movers leave through x+, -x movers through x-
+    if (right) {
+      T rv[3];
+      switch (A.bc[LBM_SW_SIDE_XP]) {
+        case LBM_SW_BC_PERIODIC:
+#pragma unroll
+          for (int c = 0; c < 3; ++c) rv[c] = S[(1 + 4 * c) * P + row];
+          break;
+        case LBM_SW_BC_WALL:
+          rv[0] = pick(xm[0], kk);
+          rv[1] = -pick(xm[1], kk);
+          rv[2] = pick(xm[2], kk);
+          break;
+        default:
+          rv[0] = rv[1] = rv[2] = T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < V; ++k)
+        if (k == kk)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) R[c][k] = rv[c];
+    }
+    if (x0 == 0) {
+      switch (A.bc[LBM_SW_SIDE_XM]) {
+        case LBM_SW_BC_PERIODIC:
+#pragma unroll
+          for (int c = 0; c < 3; ++c) L[c][0] = S[(3 + 4 * c) * P + row + nx - 1];
+          break;
+        case LBM_SW_BC_WALL:
+          L[0][0] = xp[0][0];
+          L[1][0] = -xp[1][0];
+          L[2][0] = xp[2][0];
+          break;
+        default:
+          L[0][0] = L[1][0] = L[2][0] = T(0);
+      }
+    }
+    // back sides: an OUTFLOW ghost copied the cell's own value into it
+    if (x0 == 0 && A.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_OUTFLOW)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) R[c][0] = R[c][0] + xp[c][0];
+    if (right && A.bc[LBM_SW_SIDE_XP] == LBM_SW_BC_OUTFLOW) {
+#pragma unroll
+      for (int k = 0; k < V; ++k)
+        if (k == kk)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) L[c][k] = L[c][k] + xm[c][k];
+    }
+
+    T out[13][V];
+    const T oms = T(1) - K.s;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const T psi[13] = {c0[k],   R[0][k], yp[0][k], L[0][k], ym[0][k], R[1][k], yp[1][k],
+                         L[1][k], ym[1][k], R[2][k], yp[2][k], L[2][k], ym[2][k]};
+      const bool valid = x0 + k < nx;
+      T zh = T(0), zx = T(0), zy = T(0);
+      if (valid) equilibrium_vjp(w[0][k], w[1][k], w[2][k], psi, K, zh, zx, zy);
+#pragma unroll
+      for (int q = 0; q < 13; ++q) {
+        const T z = q < 5 ? zh : (q < 9 ? zx : zy);
+        out[q][k] = valid ? oms * psi[q] + K.s * z : T(0);
+      }
+    }
+    if (active)
+#pragma unroll
+      for (int q = 0; q < 13; ++q) VV::store(A.phi_out + q * P + row + x0, out[q]);
   }
 }
 
@@ -252,7 +425,15 @@ int run_adjoint(lbm_sw* h, lbm_sw_tape* t, const double* gh, const double* gu, c
       A.pitch = pitch;
       A.plane = P;
       for (int s = 0; s < 4; ++s) A.bc[s] = h->p.bc[s];
-      lbm::adjoint_step<T><<<grid, block, 0, st>>>(A, K);
+      if (h->kernel == LBM_SW_KERNEL_SIMPLE) {
+        lbm::adjoint_step<T><<<grid, block, 0, st>>>(A, K);
+      } else {
+        constexpr int BY = 4;
+        constexpr int V = lbm::V16<T>::n;
+        const dim3 vb(32, BY);
+        const dim3 vg((nx + 32 * V - 1) / (32 * V), static_cast<unsigned>((ny + BY - 1) / BY < 65535 ? (ny + BY - 1) / BY : 65535));
+        lbm::adjoint_step_vec<T, BY><<<vg, vb, 0, st>>>(A, K);
+      }
       TAPE_CUDA(t, cudaGetLastError(), "adjoint step launch");
       cur ^= 1;
     }

@@ -162,6 +162,18 @@ LBM_SW_API int lbm_sw_set_state(lbm_sw* h, const double* depth, const double* hu
  * (launch failure; kernel faults surface at the next synchronising call). */
 LBM_SW_API int lbm_sw_step(lbm_sw* h, int n);
 
+/* Relax each moment at its own rate: the MRT form of Eq. 2-relaxation,
+ * m*_l = m_l + s_l (m_l^eq - m_l), on the moment bases the paper gives.  rates[count]:
+ *   2D (count 13): rho, J_x, J_y, eps_rho, XX_rho, q_x, f_xx, f_xy, XX_u, q_y, f_yx, f_yy, XX_v
+ *                  (section 3; J_x = lam (f1 - f3), eps_rho = f1 + f2 + f3 + f4 - 4 f0, ...);
+ *   1D (count 5):  rho, J_rho, eps_rho, q, J_q (section 2; eps_rho = lam^2 (f+ + f- - 2 f0)).
+ * The entries of the conserved moments (rho, q_x, q_y / rho, q) are ignored.  Every other
+ * rate must lie in [0, 2); all equal to s reproduces the BGK step up to rounding.
+ * rates == NULL returns to BGK with the rate s of the parameters.  Applies to the following
+ * steps and to lbm_sw_set_populations(PRE_COLLISION).  The adjoint (lbm_sw_tape_create)
+ * supports BGK only.  Errors: LBM_SW_E_ARG. */
+LBM_SW_API int lbm_sw_set_relaxation(lbm_sw* h, const double* rates, int count);
+
 /* Write the conserved moments (h = sum f, hu = sum gx, hv = sum gy; Eq.
  * 1-hyp-N-vconserv) of the current state as FP64 [ny][nx] arrays.  With host
  * arrays the call synchronises; with device arrays it is asynchronous on the stream.

@@ -469,6 +469,10 @@ int lbm_sw_tape_create(lbm_sw* h, int steps, int interval, lbm_sw_tape** out) {
     h->err = "tape_create: the adjoint is available for 2D handles";
     return LBM_SW_E_ARG;
   }
+  if (h->mrt) {
+    h->err = "tape_create: the adjoint supports the BGK relaxation only (lbm_sw_set_relaxation(h, NULL, 0))";
+    return LBM_SW_E_ARG;
+  }
   if (steps < 1 || interval < 0 || interval > steps) {
     h->err = "tape_create: need steps >= 1 and 0 <= interval <= steps";
     return LBM_SW_E_ARG;

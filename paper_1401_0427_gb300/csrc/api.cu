@@ -415,6 +415,33 @@ int lbm_sw_set_populations(lbm_sw* h, const void* src, int on_device, int form) 
   return LBM_SW_OK;
 }
 
+int lbm_sw_set_relaxation(lbm_sw* h, const double* rates, int count) {
+  if (!h) return LBM_SW_E_ARG;
+  if (!rates) {
+    h->mrt = false;
+  } else {
+    const int want = h->p.dim == 1 ? 5 : 13;
+    if (count != want) return fail(h, LBM_SW_E_ARG, "set_relaxation: %d rates expected (got %d)", want, count);
+    static const int map2[10] = {1, 2, 3, 4, 6, 7, 8, 10, 11, 12};
+    static const int map1[3] = {1, 2, 4};
+    const int n = h->p.dim == 1 ? 3 : 10;
+    const int* map = h->p.dim == 1 ? map1 : map2;
+    for (int i = 0; i < n; ++i) {
+      const double r = rates[map[i]];
+      if (!(r >= 0.0 && r < 2.0)) return fail(h, LBM_SW_E_ARG, "set_relaxation: rate %d = %g is not in [0, 2)", map[i], r);
+    }
+    for (int i = 0; i < 10; ++i) h->mrt_rates[i] = i < n ? rates[map[i]] : 0.0;
+    h->mrt = true;
+  }
+  // the captured graphs hold the old constants
+  for (int i = 0; i < 2; ++i)
+    if (h->graph[i]) {
+      cudaGraphExecDestroy(h->graph[i]);
+      h->graph[i] = nullptr;
+    }
+  return LBM_SW_OK;
+}
+
 int lbm_sw_synchronize(lbm_sw* h) {
   if (!h) return LBM_SW_E_ARG;
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");

@@ -27,6 +27,8 @@ struct StepArgs {
 
 struct ConstsD {  // scheme constants before conversion to T
   double g, lambda, s, a;
+  bool mrt = false;        // relax each non-conserved moment at its own rate
+  double rates[10] = {};   // MRT rates (Consts::r order); unused when mrt is false
 };
 
 // ---- 2D launchers (kernels_2d.cu) ----
@@ -105,6 +107,8 @@ struct lbm_sw {
   double* diag_out = nullptr;         // device, 8 doubles
   double* diag_host = nullptr;        // pinned host, 8 doubles
   int kernel = LBM_SW_KERNEL_VEC;
+  bool mrt = false;          // set by lbm_sw_set_relaxation
+  double mrt_rates[10] = {};
   int graph_chunk = 64;
   bool has_state = false;
   long long steps_done = 0;
@@ -131,6 +135,11 @@ inline StepArgs<T> handle_args(const lbm_sw* h, int src_buf) {
   return a;
 }
 
-inline ConstsD handle_consts(const lbm_sw* h) { return ConstsD{h->p.g, h->p.lambda, h->p.s, h->p.a}; }
+inline ConstsD handle_consts(const lbm_sw* h) {
+  ConstsD k{h->p.g, h->p.lambda, h->p.s, h->p.a};
+  k.mrt = h->mrt;
+  for (int i = 0; i < 10; ++i) k.rates[i] = h->mrt_rates[i];
+  return k;
+}
 
 }  // namespace lbm

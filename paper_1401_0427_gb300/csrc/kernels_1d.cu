@@ -34,14 +34,14 @@ __device__ __forceinline__ T pull1(const StepArgs<T>& A, int p, int i) {
   }
 }
 
-template <class T>
+template <class T, bool MRT>
 __global__ void __launch_bounds__(256) step1d(const StepArgs<T> A, const Consts<T> K) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nx; i += gridDim.x * blockDim.x) {
     T f[5];
     f[0] = A.src[i];
 #pragma unroll
     for (int p = 1; p < 5; ++p) f[p] = pull1(A, p, i);
-    collide5(f, K);
+    collide5_any<T, MRT>(f, K);
 #pragma unroll
     for (int p = 0; p < 5; ++p) A.dst[p * A.plane + i] = f[p];
   }
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) step1d(const StepArgs<T> A, const Consts<
 // planes); the cells next to a CTA's ends are read from the neighbouring CTAs' shared
 // memory (distributed shared memory), and one cluster barrier per step separates the
 // reads of one buffer from the writes of the next step.
-template <class T>
+template <class T, bool MRT>
 __global__ void __launch_bounds__(1024) step1d_cluster(const StepArgs<T> A, const Consts<T> K, int nsteps,
                                                        int chunk) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(1024) step1d_cluster(const StepArgs<T> A, cons
           }
         }
       }
-      collide5(f, K);
+      collide5_any<T, MRT>(f, K);
 #pragma unroll
       for (int p = 0; p < 5; ++p) nxt[p * chunk + c] = f[p];
     }
@@ -132,13 +132,13 @@ __global__ void init1d(const StepArgs<T> A, const Consts<T> K, const double* __r
   }
 }
 
-template <class T>
+template <class T, bool MRT>
 __global__ void collide1d_dense(const StepArgs<T> A, const Consts<T> K, const T* __restrict__ dense) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nx; i += gridDim.x * blockDim.x) {
     T f[5];
 #pragma unroll
     for (int p = 0; p < 5; ++p) f[p] = dense[p * static_cast<long long>(A.nx) + i];
-    collide5(f, K);
+    collide5_any<T, MRT>(f, K);
 #pragma unroll
     for (int p = 0; p < 5; ++p) A.dst[p * A.plane + i] = f[p];
   }
@@ -181,8 +181,16 @@ unsigned blocks_for(int n, int threads) {
 }  // namespace
 
 template <class T>
+Consts<T> consts1(const ConstsD& kd) {
+  return kd.mrt ? make_consts_mrt<T>(kd.g, kd.lambda, kd.s, kd.a, kd.rates, 3) : make_consts<T>(kd.g, kd.lambda, kd.s, kd.a);
+}
+
+template <class T>
 cudaError_t launch_step1d(const StepArgs<T>& a, const ConstsD& kd, cudaStream_t st) {
-  step1d<T><<<blocks_for(a.nx, 128), 128, 0, st>>>(a, make_consts<T>(kd.g, kd.lambda, kd.s, kd.a));
+  if (kd.mrt)
+    step1d<T, true><<<blocks_for(a.nx, 128), 128, 0, st>>>(a, consts1<T>(kd));
+  else
+    step1d<T, false><<<blocks_for(a.nx, 128), 128, 0, st>>>(a, consts1<T>(kd));
   return cudaGetLastError();
 }
 
@@ -192,8 +200,8 @@ int cluster1d_max_cells() {
   if (max_blocks == 0) {
     // a 16-CTA cluster where the device allows it, else the portable 8
     max_blocks = 8;
-    if (cudaFuncSetAttribute(step1d_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-        cudaFuncSetAttribute(step1d_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(step1d_cluster<T, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+        cudaFuncSetAttribute(step1d_cluster<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(2 * 5 * 1024 * sizeof(T))) == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(16);
@@ -207,7 +215,7 @@ int cluster1d_max_cells() {
       cfg.attrs = &attr;
       cfg.numAttrs = 1;
       int clusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&clusters, step1d_cluster<T>, &cfg) == cudaSuccess && clusters > 0)
+      if (cudaOccupancyMaxActiveClusters(&clusters, step1d_cluster<T, false>, &cfg) == cudaSuccess && clusters > 0)
         max_blocks = 16;
     }
     cudaGetLastError();
@@ -215,8 +223,8 @@ int cluster1d_max_cells() {
   return max_blocks * 1024;
 }
 
-template <class T>
-cudaError_t launch_step1d_cluster(const StepArgs<T>& a, const ConstsD& kd, int nsteps, cudaStream_t st) {
+template <class T, bool MRT>
+cudaError_t launch_cluster_t(const StepArgs<T>& a, const ConstsD& kd, int nsteps, cudaStream_t st) {
   const int max_cells = cluster1d_max_cells<T>();
   const int max_blocks = max_cells / 1024;
   int blocks = (a.nx + 63) / 64;  // at least 64 cells per CTA
@@ -225,11 +233,11 @@ cudaError_t launch_step1d_cluster(const StepArgs<T>& a, const ConstsD& kd, int n
   const int chunk = (a.nx + blocks - 1) / blocks;
   const int threads = ((chunk + 31) / 32) * 32;
   const size_t smem = 2 * 5 * static_cast<size_t>(chunk) * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(step1d_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(step1d_cluster<T, MRT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(2 * 5 * 1024 * sizeof(T)));
   if (e != cudaSuccess) return e;
   if (blocks > 8) {
-    e = cudaFuncSetAttribute(step1d_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(step1d_cluster<T, MRT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg = {};
@@ -244,7 +252,12 @@ cudaError_t launch_step1d_cluster(const StepArgs<T>& a, const ConstsD& kd, int n
   attr.val.clusterDim.z = 1;
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, step1d_cluster<T>, a, make_consts<T>(kd.g, kd.lambda, kd.s, kd.a), nsteps, chunk);
+  return cudaLaunchKernelEx(&cfg, step1d_cluster<T, MRT>, a, consts1<T>(kd), nsteps, chunk);
+}
+
+template <class T>
+cudaError_t launch_step1d_cluster(const StepArgs<T>& a, const ConstsD& kd, int nsteps, cudaStream_t st) {
+  return kd.mrt ? launch_cluster_t<T, true>(a, kd, nsteps, st) : launch_cluster_t<T, false>(a, kd, nsteps, st);
 }
 
 template <class T>
@@ -256,8 +269,10 @@ cudaError_t launch_init1d(const StepArgs<T>& a, const ConstsD& kd, const double*
 
 template <class T>
 cudaError_t launch_collide1d_dense(const StepArgs<T>& a, const ConstsD& kd, const T* dense, cudaStream_t st) {
-  collide1d_dense<T><<<blocks_for(a.nx, 128), 128, 0, st>>>(a, make_consts<T>(kd.g, kd.lambda, kd.s, kd.a),
-                                                             dense);
+  if (kd.mrt)
+    collide1d_dense<T, true><<<blocks_for(a.nx, 128), 128, 0, st>>>(a, consts1<T>(kd), dense);
+  else
+    collide1d_dense<T, false><<<blocks_for(a.nx, 128), 128, 0, st>>>(a, consts1<T>(kd), dense);
   return cudaGetLastError();
 }
 

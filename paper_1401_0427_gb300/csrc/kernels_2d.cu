@@ -71,7 +71,7 @@ __device__ __forceinline__ T pull_one(const StepArgs<T>& A, int p, int x, int y)
   }
 }
 
-template <class T>
+template <class T, bool MRT>
 __global__ void __launch_bounds__(256) step2d_simple(const StepArgs<T> A, const Consts<T> K) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < A.ny; y += gridDim.y * blockDim.y) {
@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(256) step2d_simple(const StepArgs<T> A, const 
     T f[13];
 #pragma unroll
     for (int p = 0; p < 13; ++p) f[p] = pull_one(A, p, x, y);
-    collide13(f, K);
+    T h, qx, qy;
+    collide13_any<T, MRT>(f, K, h, qx, qy);
 #pragma unroll
     for (int p = 0; p < 13; ++p) A.dst[p * A.plane + y * A.pitch + x] = f[p];
   }
@@ -95,12 +96,12 @@ __global__ void __launch_bounds__(256) step2d_simple(const StepArgs<T> A, const 
 // rows are warp-uniform, so only the first and last row and the warps holding
 // x = 0 or x = nx - 1 take a boundary branch.
 // --------------------------------------------------------------------------
-template <class T, int BY>
+template <class T, int BY, bool MRT>
 __global__ void __launch_bounds__(32 * BY) step2d_vec(const StepArgs<T> A, const Consts<T> K) {
   constexpr int V = V16<T>::n;
   const int x0 = (blockIdx.x * 32 + threadIdx.x) * V;
   for (int y = blockIdx.y * BY + threadIdx.y; y < A.ny; y += gridDim.y * BY)  // warp-uniform
-    vec_row<T, false>(A, K, y, x0, threadIdx.x, nullptr);
+    vec_row<T, false, MRT>(A, K, y, x0, threadIdx.x, nullptr);
 }
 
 // The same step, also writing the moments (h, hu, hv) of the new state to three planes
@@ -131,7 +132,7 @@ __global__ void init2d(const StepArgs<T> A, const Consts<T> K, const double* __r
   }
 }
 
-template <class T>
+template <class T, bool MRT>
 __global__ void collide2d_dense(const StepArgs<T> A, const Consts<T> K, const T* __restrict__ dense) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const long long n = static_cast<long long>(A.nx) * A.ny;
@@ -141,7 +142,8 @@ __global__ void collide2d_dense(const StepArgs<T> A, const Consts<T> K, const T*
     T f[13];
 #pragma unroll
     for (int p = 0; p < 13; ++p) f[p] = dense[p * n + c];
-    collide13(f, K);
+    T h, qx, qy;
+    collide13_any<T, MRT>(f, K, h, qx, qy);
 #pragma unroll
     for (int p = 0; p < 13; ++p) A.dst[p * A.plane + y * A.pitch + x] = f[p];
   }
@@ -221,17 +223,23 @@ dim3 cell_grid(int nx, int ny, dim3 block) {
 
 template <class T>
 cudaError_t launch_step2d(const StepArgs<T>& a, const ConstsD& kd, int variant, cudaStream_t st) {
-  const Consts<T> K = make_consts<T>(kd.g, kd.lambda, kd.s, kd.a);
+  const Consts<T> K = to_consts<T>(kd);
   if (variant == LBM_SW_KERNEL_SIMPLE) {
     const dim3 block(32, 8);
-    step2d_simple<T><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, K);
+    if (kd.mrt)
+      step2d_simple<T, true><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, K);
+    else
+      step2d_simple<T, false><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, K);
   } else {
     constexpr int BY = 4;
     constexpr int V = V16<T>::n;
     const dim3 block(32, BY);
     const dim3 grid((a.nx + 32 * V - 1) / (32 * V),
                     static_cast<unsigned>(std::min<long long>((a.ny + BY - 1) / BY, 65535)));
-    step2d_vec<T, BY><<<grid, block, 0, st>>>(a, K);
+    if (kd.mrt)
+      step2d_vec<T, BY, true><<<grid, block, 0, st>>>(a, K);
+    else
+      step2d_vec<T, BY, false><<<grid, block, 0, st>>>(a, K);
   }
   return cudaGetLastError();
 }
@@ -278,8 +286,10 @@ cudaError_t launch_init2d(const StepArgs<T>& a, const ConstsD& kd, const double*
 template <class T>
 cudaError_t launch_collide2d_dense(const StepArgs<T>& a, const ConstsD& kd, const T* dense, cudaStream_t st) {
   const dim3 block(128, 2);
-  collide2d_dense<T><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(
-      a, make_consts<T>(kd.g, kd.lambda, kd.s, kd.a), dense);
+  if (kd.mrt)
+    collide2d_dense<T, true><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, to_consts<T>(kd), dense);
+  else
+    collide2d_dense<T, false><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, to_consts<T>(kd), dense);
   return cudaGetLastError();
 }
 

@@ -43,6 +43,11 @@ struct Consts {
   T c;       // 1 / (2 lambda)
   T half_g;  // g / 2
   T inv4g;   // 1 / (4 g)
+  // Rates of the non-conserved moments for the MRT collision (Eq. 2-relaxation with
+  // distinct s_l), in the order of the paper's moment bases:
+  //   2D: J_x, J_y, eps, XX_rho | f_xx, f_xy, XX_u | f_yx, f_yy, XX_v   (r[0..9])
+  //   1D: J_rho, eps_rho, J_q                                            (r[0..2])
+  T r[10];
 };
 
 template <class T>
@@ -53,6 +58,15 @@ __host__ Consts<T> make_consts(double g, double lambda, double s, double a) {
   k.c = static_cast<T>(1.0 / (2.0 * lambda));
   k.half_g = static_cast<T>(g / 2.0);
   k.inv4g = static_cast<T>(1.0 / (4.0 * g));
+  for (int i = 0; i < 10; ++i) k.r[i] = k.s;
+  return k;
+}
+
+// Constants with MRT rates (10 in 2D, 3 in 1D, in the order documented on Consts::r).
+template <class T>
+__host__ Consts<T> make_consts_mrt(double g, double lambda, double s, double a, const double* rates, int n) {
+  Consts<T> k = make_consts<T>(g, lambda, s, a);
+  for (int i = 0; i < n && i < 10; ++i) k.r[i] = static_cast<T>(rates[i]);
   return k;
 }
 
@@ -113,6 +127,62 @@ __device__ __forceinline__ void collide13(T f[13], const Consts<T>& k) {
   collide13(f, k, h, qx, qy);
 }
 
+// MRT form: f* = f + M^-1 S M (f^eq - f), with M the 13 moments of section 3 (rho, J_x,
+// J_y, eps, XX_rho; q_x, f_xx, f_xy, XX_u; q_y, f_yx, f_yy, XX_v), S = diag of the rates
+// (0 on the conserved rho, q_x, q_y).  Family by family, with d = f^eq - f:
+//   f:  dJx/lam = r0 (d1 - d3), dJy/lam = r1 (d2 - d4), deps = r2 (d1 + d2 + d3 + d4 - 4 d0),
+//       dXX = r3 (d1 - d2 + d3 - d4); back: df0 = -deps/5, s13 = (deps/5 + dXX)/2,
+//       s24 = (deps/5 - dXX)/2, df1,3 = (s13 +- dJx/lam)/2, df2,4 = (s24 +- dJy/lam)/2;
+//   gx: dfxx/lam = r4 (g1 - g3), dfxy/lam = r5 (g2 - g4), dXX_u = r6 (g1 - g2 + g3 - g4);
+//       back: dg1,3 = (dXX_u/2 +- dfxx/lam)/2, dg2,4 = (-dXX_u/2 +- dfxy/lam)/2;  gy alike (r7..r9).
+template <class T>
+__device__ __forceinline__ void mrt_family4(const T d[4], T ra, T rb, T rx, T g[4]) {
+  const T a = ra * (d[0] - d[2]);
+  const T b = rb * (d[1] - d[3]);
+  const T xx = T(0.5) * rx * ((d[0] + d[2]) - (d[1] + d[3]));
+  g[0] = T(0.5) * (xx + a);
+  g[2] = T(0.5) * (xx - a);
+  g[1] = T(0.5) * (-xx + b);
+  g[3] = T(0.5) * (-xx - b);
+}
+
+template <class T>
+__device__ __forceinline__ void collide13_mrt(T f[13], const Consts<T>& k, T& h, T& qx, T& qy) {
+  moments13(f, h, qx, qy);
+  T e[13];
+  equilibrium13(h, qx, qy, k, e);
+  T d[13];
+#pragma unroll
+  for (int j = 0; j < 13; ++j) d[j] = e[j] - f[j];
+  const T jx = k.r[0] * (d[1] - d[3]);
+  const T jy = k.r[1] * (d[2] - d[4]);
+  const T e5 = k.r[2] * ((d[1] + d[2]) + (d[3] + d[4]) - T(4) * d[0]) * T(0.2);
+  const T xx = k.r[3] * ((d[1] + d[3]) - (d[2] + d[4]));
+  const T s13 = T(0.5) * (e5 + xx), s24 = T(0.5) * (e5 - xx);
+  f[0] = f[0] - e5;
+  f[1] = f[1] + T(0.5) * (s13 + jx);
+  f[3] = f[3] + T(0.5) * (s13 - jx);
+  f[2] = f[2] + T(0.5) * (s24 + jy);
+  f[4] = f[4] + T(0.5) * (s24 - jy);
+  T gx[4], gy[4];
+  mrt_family4(d + 5, k.r[4], k.r[5], k.r[6], gx);
+  mrt_family4(d + 9, k.r[7], k.r[8], k.r[9], gy);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    f[5 + j] = f[5 + j] + gx[j];
+    f[9 + j] = f[9 + j] + gy[j];
+  }
+}
+
+// Relaxation of either form (the BGK path keeps its explicitly rounded operations).
+template <class T, bool MRT>
+__device__ __forceinline__ void collide13_any(T f[13], const Consts<T>& k, T& h, T& qx, T& qy) {
+  if (MRT)
+    collide13_mrt(f, k, h, qx, qy);
+  else
+    collide13(f, k, h, qx, qy);
+}
+
 // ---- 1D: populations f0, f+, f-, g+, g- ----
 template <class T>
 __device__ __forceinline__ void moments5(const T f[5], T& h, T& q) {
@@ -146,6 +216,37 @@ __device__ __forceinline__ void collide5(T f[5], const Consts<T>& k) {
   equilibrium5(h, q, k, e);
 #pragma unroll
   for (int j = 0; j < 5; ++j) f[j] = fmad(k.s, sub(e[j], f[j]), f[j]);
+}
+
+// MRT form in 1D on the moments of section 2 (rho, J_rho = lam (f+ - f-),
+// eps_rho = lam^2 (f+ + f- - 2 f0), q, J_q = lam (g+ - g-)); with d = f^eq - f:
+// dJ/lam = r0 (d+ - d-), deps/lam^2 = r1 (d+ + d- - 2 d0), dJq/lam = r2 (dg+ - dg-);
+// back: sum = deps/(3 lam^2), df0 = -sum, df+- = (sum +- dJ/lam)/2, dg+- = +- dJq/(2 lam).
+template <class T>
+__device__ __forceinline__ void collide5_mrt(T f[5], const Consts<T>& k) {
+  T h, q;
+  moments5(f, h, q);
+  T e[5];
+  equilibrium5(h, q, k, e);
+  T d[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) d[j] = e[j] - f[j];
+  const T j1 = k.r[0] * (d[1] - d[2]);
+  const T sm = k.r[1] * ((d[1] + d[2]) - T(2) * d[0]) * T(1.0 / 3.0);
+  const T jq = k.r[2] * (d[3] - d[4]) * T(0.5);
+  f[0] = f[0] - sm;
+  f[1] = f[1] + T(0.5) * (sm + j1);
+  f[2] = f[2] + T(0.5) * (sm - j1);
+  f[3] = f[3] + jq;
+  f[4] = f[4] - jq;
+}
+
+template <class T, bool MRT>
+__device__ __forceinline__ void collide5_any(T f[5], const Consts<T>& k) {
+  if (MRT)
+    collide5_mrt(f, k);
+  else
+    collide5(f, k);
 }
 
 }  // namespace lbm

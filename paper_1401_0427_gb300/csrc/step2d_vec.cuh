@@ -18,6 +18,12 @@ namespace lbm {
 
 constexpr unsigned kFullMask = 0xffffffffu;
 
+// Device constants of a host-side ConstsD (MRT rates included).
+template <class T>
+inline Consts<T> to_consts(const ConstsD& k) {
+  return k.mrt ? make_consts_mrt<T>(k.g, k.lambda, k.s, k.a, k.rates, 10) : make_consts<T>(k.g, k.lambda, k.s, k.a);
+}
+
 template <class T>
 struct V16;
 template <>
@@ -55,7 +61,7 @@ __device__ __forceinline__ T pick(const T (&a)[V], int i) {
 // One row segment: cells x0 .. x0 + V - 1 of row y (x0 >= nx: the lane only takes part
 // in the shuffles).  With STORE_W the moments (h, hu, hv) of the new state are also
 // written to w_out (three planes with the population pitch).
-template <class T, bool STORE_W>
+template <class T, bool STORE_W, bool MRT = false>
 __device__ __forceinline__ void vec_row(const StepArgs<T>& A, const Consts<T>& K, int y, int x0, int lane,
                                         T* __restrict__ w_out) {
   using VV = V16<T>;
@@ -204,7 +210,7 @@ __device__ __forceinline__ void vec_row(const StepArgs<T>& A, const Consts<T>& K
     T f[13] = {c0[k],    L[0][k], yp[0][k], R[0][k], ym[0][k], L[1][k], yp[1][k],
                R[1][k], ym[1][k], L[2][k], yp[2][k], R[2][k], ym[2][k]};
     T wh, wx, wy;
-    collide13(f, K, wh, wx, wy);
+    collide13_any<T, MRT>(f, K, wh, wx, wy);
     const bool valid = x0 + k < nx;  // padding cells are stored as zero
 #pragma unroll
     for (int p = 0; p < 13; ++p) out[p][k] = valid ? f[p] : T(0);

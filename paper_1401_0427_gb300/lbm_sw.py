@@ -117,6 +117,7 @@ SIGNATURES = {
     "lbm_sw_destroy": (None, [_H]),
     "lbm_sw_set_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lbm_sw_step": (ctypes.c_int, [_H, ctypes.c_int]),
+    "lbm_sw_set_relaxation": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "lbm_sw_get_moments": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lbm_sw_diagnostics": (ctypes.c_int, [_H, _DP]),
     "lbm_sw_get_populations": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
@@ -210,6 +211,15 @@ def lbm_sw_set_state(h: int, depth: int, hu: int, hv: int | None, on_device: boo
 
 def lbm_sw_step(h: int, n: int) -> None:
     _check(load().lbm_sw_step(h, int(n)), h, "lbm_sw_step")
+
+
+def lbm_sw_set_relaxation(h: int, rates=None) -> None:
+    """MRT rates in the paper's moment order (13 in 2D, 5 in 1D), or None for BGK."""
+    if rates is None:
+        _check(load().lbm_sw_set_relaxation(h, None, 0), h, "lbm_sw_set_relaxation")
+        return
+    arr = (ctypes.c_double * len(rates))(*[float(r) for r in rates])
+    _check(load().lbm_sw_set_relaxation(h, arr, len(rates)), h, "lbm_sw_set_relaxation")
 
 
 def lbm_sw_get_moments(h: int, depth: int, hu: int, hv: int | None, on_device: bool) -> None:
@@ -436,6 +446,9 @@ class Simulation:
 
     def step(self, n: int = 1):
         lbm_sw_step(self.handle, n)
+
+    def set_relaxation(self, rates=None):
+        lbm_sw_set_relaxation(self.handle, rates)
 
     def moments(self):
         h = np.empty((self.ny, self.nx))

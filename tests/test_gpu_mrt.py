@@ -1,0 +1,89 @@
+"""MRT relaxation on the GPU (each moment of the paper's bases at its own rate, Eq.
+2-relaxation) against the oracle's MRT collision, which is pinned to the printed moment
+definitions (tests/test_oracle_equilibria.py)."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_0427_gb300 import inputs, lbm_sw
+
+from gpu_helpers import FP32_ELEM_TOL, FP64_TOL, gpu_post, oracle_post, rel_max, torch_stream
+
+pytestmark = pytest.mark.gpu
+
+P, W, O, I = lbm_sw.PERIODIC, lbm_sw.WALL, lbm_sw.OUTFLOW, lbm_sw.INFLOW
+INFLOW = [(1.3, 0.2, -0.1), (0.9, -0.15, 0.05), (1.1, 0.05, 0.12), (1.2, -0.08, -0.2)]
+RATES_2D = [0.0, 1.1, 1.2, 1.3, 1.4, 0.0, 1.5, 1.6, 1.7, 0.0, 1.75, 1.65, 0.9]
+RATES_1D = [0.0, 1.3, 1.6, 0.0, 1.9]
+
+
+@pytest.mark.parametrize("precision", [lbm_sw.FP64, lbm_sw.FP32])
+@pytest.mark.parametrize("kernel", [lbm_sw.KERNEL_SIMPLE, lbm_sw.KERNEL_VEC])
+@pytest.mark.parametrize("bc", [(P, P, P, P), (W, O, I, W), (I, W, P, P)], ids=["PPPP", "WOIW", "IWPP"])
+@pytest.mark.parametrize("nx,ny", [(1, 1), (5, 7), (130, 9), (257, 3)])
+def test_2d_mrt_matches_oracle(nx, ny, bc, kernel, precision):
+    F0 = inputs.random_populations(13, ny, nx, seed=6000 + nx)
+    if precision == lbm_sw.FP32:
+        F0 = F0.astype(np.float32).astype(np.float64)
+    p = oracle.params(nx, ny, a=0.05, bc=bc, inflow=INFLOW, s_moments=RATES_2D)
+    for steps in (1, 4):
+        got = gpu_post(F0, steps, dim=2, precision=precision, bc=bc, inflow=INFLOW, a=0.05, kernel=kernel,
+                       mrt_rates=RATES_2D)
+        err = rel_max(got, oracle_post(F0, steps, p, 2))
+        assert err <= (FP64_TOL if precision == lbm_sw.FP64 else FP32_ELEM_TOL), (steps, err)
+
+
+@pytest.mark.parametrize("precision", [lbm_sw.FP64, lbm_sw.FP32])
+@pytest.mark.parametrize("kernel", [lbm_sw.KERNEL_SIMPLE, lbm_sw.KERNEL_CLUSTER])
+@pytest.mark.parametrize("bc", [(P, P), (W, W), (O, I)], ids=str)
+@pytest.mark.parametrize("n", [1, 31, 1000])
+def test_1d_mrt_matches_oracle(n, bc, kernel, precision):
+    inflow = [(1.3, 0.2, 0.0), (0.9, -0.15, 0.0), None, None]
+    F0 = inputs.random_populations(5, 1, n, seed=6100 + n)
+    if precision == lbm_sw.FP32:
+        F0 = F0.astype(np.float32).astype(np.float64)
+    p = oracle.params(n, a=0.15, bc=bc, inflow=inflow, s_moments=RATES_1D)
+    for steps in (1, 5):
+        got = gpu_post(F0, steps, dim=1, precision=precision, bc=bc, inflow=inflow, a=0.15, kernel=kernel,
+                       mrt_rates=RATES_1D)
+        err = rel_max(got, oracle_post(F0, steps, p, 1))
+        assert err <= (FP64_TOL if precision == lbm_sw.FP64 else FP32_ELEM_TOL), (steps, err)
+
+
+def test_equal_rates_reproduce_bgk_and_reset():
+    F0 = inputs.random_populations(13, 40, 70, seed=6200)
+    bgk = gpu_post(F0, 30, dim=2, precision=lbm_sw.FP64, bc=(W, O, P, P), inflow=INFLOW, a=0.05)
+    mrt = gpu_post(F0, 30, dim=2, precision=lbm_sw.FP64, bc=(W, O, P, P), inflow=INFLOW, a=0.05,
+                   mrt_rates=[1.8] * 13)
+    assert rel_max(mrt, bgk) <= 1e-13
+    with lbm_sw.Simulation(70, 40, precision=lbm_sw.FP64, bc=(W, O, P, P), inflow=INFLOW, graph_chunk=8,
+                           stream=torch_stream()) as sim:
+        sim.set_relaxation(RATES_2D)
+        sim.set_populations(F0, form=lbm_sw.PRE_COLLISION)
+        sim.step(16)  # captures graphs with the MRT constants
+        sim.set_relaxation(None)
+        sim.step(14)  # the graphs must be rebuilt for BGK
+        mixed = sim.populations()
+    p_mrt = oracle.params(70, 40, a=0.05, bc=(W, O, P, P), inflow=INFLOW, s_moments=RATES_2D)
+    p_bgk = oracle.params(70, 40, a=0.05, bc=(W, O, P, P), inflow=INFLOW)
+    F = oracle.run_2d(F0, 16, p_mrt)             # 16 MRT steps from F0 (pre-collision)
+    F = oracle.collide_2d(F, p_mrt)              # the state the GPU stores after them
+    F = oracle.collide_2d(oracle.run_2d(oracle.stream_2d(F, p_bgk), 13, p_bgk), p_bgk)
+    assert rel_max(mixed, F) <= FP64_TOL
+
+
+def test_mrt_validation_and_adjoint_rejects_mrt():
+    with lbm_sw.Simulation(16, 8, stream=torch_stream()) as sim:
+        with pytest.raises(lbm_sw.LbmSwError) as ei:
+            sim.set_relaxation([1.0] * 5)
+        assert "13 rates" in str(ei.value)
+        bad = list(RATES_2D)
+        bad[3] = 2.5
+        with pytest.raises(lbm_sw.LbmSwError):
+            sim.set_relaxation(bad)
+        sim.set_relaxation(RATES_2D)
+        sim.set_state(np.ones((8, 16)), np.zeros((8, 16)), np.zeros((8, 16)))
+        with pytest.raises(lbm_sw.LbmSwError) as ei:
+            lbm_sw.Tape(sim, 10)
+        assert "BGK" in str(ei.value)

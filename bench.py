@@ -242,11 +242,17 @@ def run_ours(args, world, rank, local):
     prec = lbm_sw.FP64 if args.precision == "fp64" else lbm_sw.FP32
     dt_name = "f64" if prec == lbm_sw.FP64 else "f32"
 
-    sim = lbm_sw.Simulation(N, N, precision=prec, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream)
+    kernel = lbm_sw.KERNEL_TEMPORAL if args.kernel == "temporal" else lbm_sw.KERNEL_VEC
+    sim = lbm_sw.Simulation(N, N, precision=prec, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream,
+                            kernel=kernel)
     sim.set_state(*W0)
+    unit = 4 if args.kernel == "temporal" else 1  # steps per kernel launch
+    if args.steps % unit:
+        raise SystemExit(f"--steps must be a multiple of {unit} for --kernel {args.kernel}")
+    nlaunch = args.steps // unit
     launches0 = sim.info().kernel_launches
     for _ in range(args.warmup):
-        sim.step(1)
+        sim.step(unit)
     sim.synchronize()
 
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
@@ -255,13 +261,13 @@ def run_ours(args, world, rank, local):
     clocks.start()
     time.sleep(0.3)
 
-    events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(nlaunch + 1)]
     barrier(world)
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
     events[0].record(stream)
-    for i in range(args.steps):
-        sim.step(1)
+    for i in range(nlaunch):
+        sim.step(unit)
         events[i + 1].record(stream)
     torch.cuda.synchronize()
     t_wall1 = time.perf_counter()
@@ -270,7 +276,7 @@ def run_ours(args, world, rank, local):
     clocks.stop()
 
     total_ms = events[0].elapsed_time(events[-1])
-    per_launch = [events[i].elapsed_time(events[i + 1]) for i in range(args.steps)]
+    per_launch = [events[i].elapsed_time(events[i + 1]) for i in range(nlaunch)]
     launches = sim.info().kernel_launches - launches0 - args.warmup
     total_ms = max_over_ranks(world, total_ms)
     diag = sim.diagnostics()
@@ -284,7 +290,9 @@ def run_ours(args, world, rank, local):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": f"{peak_kind} (copy bandwidth)",
                 "frac_of_nominal_8tbs": achieved / 8000.0,
-                "kernel": "step2d_vec<float>" if dt_name == "f32" else "step2d_vec<double>",
+                "kernel": ("step2d_temporal<4, 128>" if unit == 4 else "step2d_vec<float>") if dt_name == "f32"
+                else "step2d_vec<double>",
+                "steps_per_launch": unit,
                 "algorithmic_bytes_per_launch": BYTES_PER_LUP[dt_name] * cells,
                 "median_launch_ms": float(np.median(per_launch))}
     sim.close()
@@ -340,6 +348,7 @@ def variants(args, W0, stream, lbm_sw, torch):
     out["_l1"] = {"relative_l1_h": float(np.abs(hs["fp32"] - hs["fp64"]).sum() / np.abs(hs["fp64"]).sum()),
                   "steps": JOB_STEPS, "against": "FP64 run of the same workload (equal to the FP64 oracle "
                                                  "within 1e-12 in the parity tests)"}
+    out["fp32_temporal"] = temporal_variant(W0, stream, lbm_sw, torch, args.steps)
     out["batched_256"] = batched_variant(stream, lbm_sw, torch)
     out["shock_reflection_512"] = shock_reflection_variant(stream, lbm_sw, torch)
     out["shock_tube_1d_1000"] = shock_tube_variant(stream, lbm_sw, torch)
@@ -355,6 +364,20 @@ def _timed(stream, torch, fn):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) * 1e-3
+
+
+def temporal_variant(W0, stream, lbm_sw, torch, steps: int):
+    """The same workload with 4 fused steps per launch (temporal blocking through shared
+    memory; bit-identical results)."""
+    steps = steps - steps % 4
+    with lbm_sw.Simulation(N, N, precision=lbm_sw.FP32, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream,
+                           kernel=lbm_sw.KERNEL_TEMPORAL) as sim:
+        sim.set_state(*W0)
+        sim.step(8)
+        t = _timed(stream, torch, lambda: sim.step(steps))
+    per_launch = t / (steps // 4)
+    return {"MLUPS": N * N * steps / t / 1e6, "ms_per_step": t / steps * 1e3, "steps_per_launch": 4,
+            "GB_per_s_state": BYTES_PER_LUP["f32"] * N * N / per_launch / 1e9}
 
 
 def batched_variant(stream, lbm_sw, torch, steps: int = 500):
@@ -552,6 +575,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--side", type=int, default=4096, help="grid side (profiling of smaller cases only)")
     ap.add_argument("--count", type=int, default=256, help="instances of the batched profiling case")
+    ap.add_argument("--kernel", choices=["vec", "temporal"], default="vec",
+                    help="step kernel of the timed loop (vec: one step per launch; temporal: 4 per launch)")
     ap.add_argument("--case", choices=["step", "batched", "adjoint", "shock_tube", "diag"], default="step",
                     help="kernel to run for profiling (only 'step' prints the benchmark line)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",

@@ -107,6 +107,10 @@ typedef struct lbm_sw lbm_sw;
 #define LBM_SW_KERNEL_CLUSTER 3 /* 1D: all n steps of lbm_sw_step in one thread-block-cluster
                                    launch, the line held in shared memory (up to 16384 cells on a
                                    GB300; longer lines use SIMPLE) */
+#define LBM_SW_KERNEL_TEMPORAL 4 /* 2D FP32 BGK: temporal_steps steps per launch (temporal
+                                    blocking: a row wavefront through shared memory, 104/k bytes of
+                                    HBM traffic per cell update plus halos); the remainder of n and
+                                    other cases use VEC; results equal VEC bit for bit */
 
 typedef struct lbm_sw_params {
   int dim;             /* 1 (D1Q3Q2) or 2 (D2Q5Q4Q4) */
@@ -121,7 +125,8 @@ typedef struct lbm_sw_params {
   void* stream;        /* cudaStream_t borrowed from the caller (NULL = legacy default) */
   int kernel;          /* LBM_SW_KERNEL_*: AUTO, SIMPLE, VEC (2D) or CLUSTER (1D) */
   int graph_chunk;     /* steps per captured CUDA graph in lbm_sw_step; 0 = default, < 0 = off */
-  int reserved[6];     /* must be zero */
+  int temporal_steps;  /* steps fused per launch by the TEMPORAL kernel: 2, 3 or 4; 0 = default (4) */
+  int reserved[5];     /* must be zero */
 } lbm_sw_params;
 
 typedef struct lbm_sw_info {

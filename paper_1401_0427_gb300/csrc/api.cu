@@ -46,16 +46,18 @@ lbm::StepArgs<T> args(const lbm_sw* h, int src_buf) {
 
 lbm::ConstsD consts(const lbm_sw* h) { return lbm::handle_consts(h); }
 
-// One step from buffer `from` into the other buffer, on stream st.
+// One step from buffer `from` into the other buffer, on stream st (the TEMPORAL choice
+// takes single steps with the VEC kernel).
 cudaError_t launch_one_step(lbm_sw* h, int from, cudaStream_t st) {
+  const int variant = h->kernel == LBM_SW_KERNEL_TEMPORAL ? LBM_SW_KERNEL_VEC : h->kernel;
   if (h->p.precision == LBM_SW_FP64) {
     auto a = args<double>(h, from);
     return h->p.dim == 1 ? lbm::launch_step1d<double>(a, consts(h), st)
-                         : lbm::launch_step2d<double>(a, consts(h), h->kernel, st);
+                         : lbm::launch_step2d<double>(a, consts(h), variant, st);
   }
   auto a = args<float>(h, from);
   return h->p.dim == 1 ? lbm::launch_step1d<float>(a, consts(h), st)
-                       : lbm::launch_step2d<float>(a, consts(h), h->kernel, st);
+                       : lbm::launch_step2d<float>(a, consts(h), variant, st);
 }
 
 // Capture graph_chunk steps starting from buffer `from` (graph_chunk is even, so the
@@ -104,11 +106,14 @@ int validate(const lbm_sw_params* p, lbm_sw* h) {
   for (int pair = 0; pair < nsides; pair += 2)
     if ((p->bc[pair] == LBM_SW_BC_PERIODIC) != (p->bc[pair + 1] == LBM_SW_BC_PERIODIC))
       return fail(h, LBM_SW_E_ARG, "periodic sides come in pairs (bc[%d], bc[%d])", pair, pair + 1);
-  if (p->kernel < LBM_SW_KERNEL_AUTO || p->kernel > LBM_SW_KERNEL_CLUSTER)
+  if (p->kernel < LBM_SW_KERNEL_AUTO || p->kernel > LBM_SW_KERNEL_TEMPORAL)
     return fail(h, LBM_SW_E_ARG, "kernel must be a LBM_SW_KERNEL_* value");
-  if ((p->dim == 2 && p->kernel == LBM_SW_KERNEL_CLUSTER) || (p->dim == 1 && p->kernel == LBM_SW_KERNEL_VEC))
-    return fail(h, LBM_SW_E_ARG, "kernel: CLUSTER is for 1D handles, VEC for 2D handles");
-  for (int r = 0; r < 6; ++r)
+  if ((p->dim == 2 && p->kernel == LBM_SW_KERNEL_CLUSTER) ||
+      (p->dim == 1 && (p->kernel == LBM_SW_KERNEL_VEC || p->kernel == LBM_SW_KERNEL_TEMPORAL)))
+    return fail(h, LBM_SW_E_ARG, "kernel: CLUSTER is for 1D handles, VEC and TEMPORAL for 2D handles");
+  if (p->temporal_steps != 0 && !lbm::temporal_steps_supported(p->temporal_steps))
+    return fail(h, LBM_SW_E_ARG, "temporal_steps must be 0, 2, 3 or 4");
+  for (int r = 0; r < 5; ++r)
     if (p->reserved[r] != 0) return fail(h, LBM_SW_E_ARG, "reserved fields must be zero");
   return LBM_SW_OK;
 }
@@ -199,6 +204,7 @@ int lbm_sw_create(const lbm_sw_params* p, lbm_sw** out) {
     h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? LBM_SW_KERNEL_VEC : p->kernel;
   else
     h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? LBM_SW_KERNEL_CLUSTER : p->kernel;
+  h->temporal_k = p->temporal_steps ? p->temporal_steps : 4;
   h->graph_chunk = p->graph_chunk == 0 ? 64 : (p->graph_chunk < 0 ? 0 : p->graph_chunk + (p->graph_chunk & 1));
 
   auto bail = [&](int code) {
@@ -208,6 +214,8 @@ int lbm_sw_create(const lbm_sw_params* p, lbm_sw** out) {
     return code;
   };
   if (cudaGetDevice(&h->device) != cudaSuccess) return bail(LBM_SW_E_CUDA);
+  if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+    return bail(LBM_SW_E_CUDA);
   const size_t bytes = state_bytes(h);
   for (int i = 0; i < 2; ++i) {
     if (cudaMalloc(&h->buf[i], bytes) != cudaSuccess) return bail(LBM_SW_E_NOMEM);
@@ -287,6 +295,32 @@ int lbm_sw_step(lbm_sw* h, int n) {
       h->launches += 1;
       return LBM_SW_OK;
     }
+  }
+  if (h->p.dim == 2 && h->kernel == LBM_SW_KERNEL_TEMPORAL && h->p.precision == LBM_SW_FP32 && !h->mrt) {
+    const int K = h->temporal_k;
+    while (n >= K) {
+      cudaError_t e = lbm::launch_step2d_temporal(args<float>(h, h->cur), consts(h), K, h->stream, h->sm_count);
+      if (e != cudaSuccess) return cuda_fail(h, e, "temporal step launch");
+      h->cur ^= 1;
+      n -= K;
+      h->steps_done += K;
+      h->launches += 1;
+    }
+    const int saved = h->kernel;
+    h->kernel = LBM_SW_KERNEL_VEC;  // the remainder, one step per launch
+    while (n > 0) {
+      cudaError_t e = launch_one_step(h, h->cur, h->stream);
+      if (e != cudaSuccess) {
+        h->kernel = saved;
+        return cuda_fail(h, e, "step kernel launch");
+      }
+      h->cur ^= 1;
+      n -= 1;
+      h->steps_done += 1;
+      h->launches += 1;
+    }
+    h->kernel = saved;
+    return LBM_SW_OK;
   }
   while (n > 0) {
     if (h->graph_chunk > 0 && n >= h->graph_chunk) {

@@ -54,6 +54,11 @@ cudaError_t launch_moments2d_planes(const StepArgs<T>& a, T* w_out, cudaStream_t
 template <class Tin, class Tout>
 cudaError_t launch_convert(const Tin* in, Tout* out, long long n, cudaStream_t st);
 
+// k fused steps per launch (temporal.cu; FP32, BGK; k in {2, 3, 4}): src -> dst.
+bool temporal_steps_supported(int k);
+cudaError_t launch_step2d_temporal(const StepArgs<float>& a, const ConstsD& kd, int k, cudaStream_t st,
+                                   int sm_count);
+
 // ---- 1D launchers (kernels_1d.cu) ----
 template <class T>
 cudaError_t launch_step1d(const StepArgs<T>& a, const ConstsD& k, cudaStream_t st);
@@ -107,6 +112,8 @@ struct lbm_sw {
   double* diag_out = nullptr;         // device, 8 doubles
   double* diag_host = nullptr;        // pinned host, 8 doubles
   int kernel = LBM_SW_KERNEL_VEC;
+  int temporal_k = 4;
+  int sm_count = 152;
   bool mrt = false;          // set by lbm_sw_set_relaxation
   double mrt_rates[10] = {};
   int graph_chunk = 64;

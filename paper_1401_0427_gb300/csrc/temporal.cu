@@ -1,0 +1,267 @@
+// K fused D2Q5Q4Q4 steps per launch (temporal blocking), FP32.
+//
+// A CTA owns an output strip of W = COLS - 2K columns and a segment of rows.  One thread
+// per column of the strip plus a K-column halo on each side sweeps a row wavefront down
+// the segment: at iteration j it brings one row of the launch's input state (level 0)
+// into shared memory with cp.async (two rows ahead), then computes, for t = 1 .. K, one
+// row of time level t from three rows of level t - 1 (a three-row ring per level in
+// shared memory); level K is written straight to HBM.  Each level loses one column on
+// each side of the strip and one row at each end of the segment, so the halos are
+// recomputed (a fraction 2K/W of the columns and 2K/H of the rows).  HBM traffic per
+// lattice update is 104/K bytes plus the halo share, against 104 for one step per launch.
+//
+// Every cell update is the same pull + collide13 as the single-step kernels, on the same
+// values, so K steps of this kernel equal K single steps bit for bit.
+#include <cuda_pipeline.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "scheme.cuh"
+
+namespace lbm {
+namespace {
+
+template <int K, int COLS>
+struct TemporalShape {
+  static constexpr int W = COLS - 2 * K;      // output columns per strip
+  static constexpr int L0 = 5;                // level-0 ring (prefetch distance 2)
+  static constexpr int RING = 3;              // rows kept per intermediate level
+  static constexpr size_t smem_floats() { return static_cast<size_t>(COLS) * 13 * (L0 + RING * (K - 1)); }
+  // Compact rings for all-periodic domains, where row R of level t - 1 is read in three
+  // plane groups at three different times: the -y movers (4, 8, 12) as row R + 1 in the
+  // iteration that writes them (1 slot), f0 and the x movers (0, 1, 3, 5, 7, 9, 11) as row
+  // R one iteration later (2 slots), the +y movers (2, 6, 10) as row R - 1 two iterations
+  // later (3 slots); level 0 arrives two iterations early (3, 4 and 5 slots).
+  static constexpr int A0 = 3, B0 = 4, C0 = 5, A1 = 1, B1 = 2, C1 = 3;
+  static constexpr int L0_FLOATS = COLS * (3 * A0 + 7 * B0 + 3 * C0);
+  static constexpr int LV_FLOATS = COLS * (3 * A1 + 7 * B1 + 3 * C1);
+  static constexpr size_t compact_floats() { return static_cast<size_t>(L0_FLOATS) + (K - 1) * LV_FLOATS; }
+};
+
+// Plane p -> (group, index): A = {4, 8, 12}, B = {0, 1, 3, 5, 7, 9, 11}, C = {2, 6, 10}.
+__host__ __device__ constexpr int plane_group(int p) {
+  return (p == 4 || p == 8 || p == 12) ? 0 : ((p == 2 || p == 6 || p == 10) ? 2 : 1);
+}
+__host__ __device__ constexpr int plane_index(int p) {
+  return plane_group(p) == 0 ? (p - 4) / 4 : (plane_group(p) == 2 ? (p - 2) / 4 : (p == 0 ? 0 : (p + 1) / 2));
+}
+
+// Population p arriving at tile cell (c, R) at level t, from level t - 1 held in shared
+// memory: base(row) gives the plane-0 address of a ring row; neighbour columns c -+ 1 and
+// rows R -+ 1 are in the tile; sides of the domain that are not periodic use the boundary
+// rule of the single-step kernels (the cell's own level t - 1 values or the inflow state).
+template <int COLS>
+__device__ __forceinline__ void pull_level(const float* row_m, const float* row_0, const float* row_p, int c,
+                                           bool at_xm, bool at_xp, bool at_ym, bool at_yp, const int bc[4],
+                                           const float* __restrict__ inflow_feq, float f[13]) {
+  auto v = [&](const float* row, int p, int col) { return row[p * COLS + col]; };
+  f[0] = v(row_0, 0, c);
+#pragma unroll
+  for (int fam = 0; fam < 3; ++fam) {
+    const int p1 = 1 + 4 * fam, p2 = 2 + 4 * fam, p3 = 3 + 4 * fam, p4 = 4 + 4 * fam;
+    // +x movers from c - 1
+    if (!at_xm) {
+      f[p1] = v(row_0, p1, c - 1);
+    } else {
+      const int b = bc[LBM_SW_SIDE_XM];
+      if (b == LBM_SW_BC_WALL) f[p1] = fam == 1 ? -v(row_0, p3, c) : v(row_0, p3, c);
+      else if (b == LBM_SW_BC_OUTFLOW) f[p1] = v(row_0, p1, c);
+      else f[p1] = inflow_feq[LBM_SW_SIDE_XM * 13 + p1];
+    }
+    // -x movers from c + 1
+    if (!at_xp) {
+      f[p3] = v(row_0, p3, c + 1);
+    } else {
+      const int b = bc[LBM_SW_SIDE_XP];
+      if (b == LBM_SW_BC_WALL) f[p3] = fam == 1 ? -v(row_0, p1, c) : v(row_0, p1, c);
+      else if (b == LBM_SW_BC_OUTFLOW) f[p3] = v(row_0, p3, c);
+      else f[p3] = inflow_feq[LBM_SW_SIDE_XP * 13 + p3];
+    }
+    // +y movers from row R - 1
+    if (!at_ym) {
+      f[p2] = v(row_m, p2, c);
+    } else {
+      const int b = bc[LBM_SW_SIDE_YM];
+      if (b == LBM_SW_BC_WALL) f[p2] = fam == 2 ? -v(row_0, p4, c) : v(row_0, p4, c);
+      else if (b == LBM_SW_BC_OUTFLOW) f[p2] = v(row_0, p2, c);
+      else f[p2] = inflow_feq[LBM_SW_SIDE_YM * 13 + p2];
+    }
+    // -y movers from row R + 1
+    if (!at_yp) {
+      f[p4] = v(row_p, p4, c);
+    } else {
+      const int b = bc[LBM_SW_SIDE_YP];
+      if (b == LBM_SW_BC_WALL) f[p4] = fam == 2 ? -v(row_0, p2, c) : v(row_0, p2, c);
+      else if (b == LBM_SW_BC_OUTFLOW) f[p4] = v(row_0, p4, c);
+      else f[p4] = inflow_feq[LBM_SW_SIDE_YP * 13 + p4];
+    }
+  }
+}
+
+// PER: every side is periodic (no boundary rule, every tile cell is a domain cell).
+template <int K, int COLS, bool PER>
+__global__ void __launch_bounds__(COLS, (K <= 2 ? 4 : (K == 3 ? 3 : (PER ? 3 : 2))))
+    step2d_temporal(const StepArgs<float> A, const Consts<float> Kc, int seg_rows) {
+  using S = TemporalShape<K, COLS>;
+  extern __shared__ __align__(16) float smem[];
+  const int c = threadIdx.x;
+  const int nx = A.nx, ny = A.ny;
+  const bool px = PER || A.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC;
+  const bool py = PER || A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
+  const int x0 = blockIdx.x * S::W;
+  const int ys = blockIdx.y * seg_rows;
+  const int ye = min(ys + seg_rows, ny);
+  const int gx_raw = x0 - K + c;
+  const bool col_live = px || (gx_raw >= 0 && gx_raw < nx);
+  const int gx = px ? ((gx_raw % nx) + nx) % nx : gx_raw;
+  const bool at_xm = !px && gx_raw == 0;
+  const bool at_xp = !px && gx_raw == nx - 1;
+  const int iters = (ye - ys) + 2 * K;
+
+  // ---- shared-memory addressing ----
+  // full rings (any boundary): level 0 [L0][13][COLS], level t [RING][13][COLS]
+  // compact rings (all periodic): per level, group A [slots][3][COLS], B [slots][7][COLS],
+  // C [slots][3][COLS] (see TemporalShape)
+  auto lvl0_full = [&](int slot) { return smem + static_cast<size_t>(slot) * 13 * COLS; };
+  auto ring_full = [&](int t, int slot) {
+    return smem + static_cast<size_t>(S::L0) * 13 * COLS + static_cast<size_t>(t - 1) * S::RING * 13 * COLS +
+           static_cast<size_t>(slot) * 13 * COLS;
+  };
+  // compact: address of plane p of the row in group slots (sa, sb, sc) of level t (0 = input)
+  auto compact = [&](int t, int p, int sa, int sb, int sc) -> float* {
+    float* base = t == 0 ? smem : smem + S::L0_FLOATS + static_cast<size_t>(t - 1) * S::LV_FLOATS;
+    const int na = t == 0 ? S::A0 : S::A1, nb = t == 0 ? S::B0 : S::B1;
+    const int g = plane_group(p), i = plane_index(p);
+    if (g == 0) return base + (sa * 3 + i) * COLS;
+    base += na * 3 * COLS;
+    if (g == 1) return base + (sb * 7 + i) * COLS;
+    base += nb * 7 * COLS;
+    return base + (sc * 3 + i) * COLS;
+  };
+
+  auto issue_row = [&](int j) {
+    if (j < iters) {
+      const int r = ys - K + j;
+      const bool live = py || (r >= 0 && r < ny);
+      if (live && col_live) {
+        const int gr = py ? ((r % ny) + ny) % ny : r;
+        const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
+#pragma unroll
+        for (int p = 0; p < 13; ++p) {
+          float* s = PER ? compact(0, p, j % S::A0, j % S::B0, j % S::C0) + c : lvl0_full(j % S::L0) + p * COLS + c;
+          __pipeline_memcpy_async(s, g + p * A.plane, sizeof(float));
+        }
+      }
+    }
+    __pipeline_commit();
+  };
+
+  issue_row(0);
+  issue_row(1);
+  for (int j = 0; j < iters; ++j) {
+    issue_row(j + 2);
+    __pipeline_wait_prior(2);  // row j has landed (this thread's copies)
+    __syncthreads();           // ... and every thread's
+#pragma unroll
+    for (int t = 1; t <= K; ++t) {
+      const int R = ys - K + j - t;  // row of level t computed now
+      const bool row_ok = R >= ys - K + t && R < ye + K - t;
+      const bool row_live = py || (R >= 0 && R < ny);
+      if (row_ok && row_live && col_live && c >= t && c < COLS - t) {
+        float f[13];
+        if (PER) {
+          // level t - 1: row R + 1 written this iteration, R the last one, R - 1 the one before
+          const int ja = t == 1 ? j % S::A0 : 0;
+          const int jb = t == 1 ? (j + S::B0 - 1) % S::B0 : (j + 1) % S::B1;
+          const int jc = t == 1 ? (j + S::C0 - 2) % S::C0 : (j + 1) % S::C1;
+          f[0] = compact(t - 1, 0, ja, jb, jc)[c];
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            f[1 + 4 * fam] = compact(t - 1, 1 + 4 * fam, ja, jb, jc)[c - 1];
+            f[2 + 4 * fam] = compact(t - 1, 2 + 4 * fam, ja, jb, jc)[c];
+            f[3 + 4 * fam] = compact(t - 1, 3 + 4 * fam, ja, jb, jc)[c + 1];
+            f[4 + 4 * fam] = compact(t - 1, 4 + 4 * fam, ja, jb, jc)[c];
+          }
+        } else {
+          const float *rm, *r0, *rp;
+          if (t == 1) {  // level 0 rows R - 1, R, R + 1 are iterations j - 2, j - 1, j
+            rm = lvl0_full((j + S::L0 - 2) % S::L0);
+            r0 = lvl0_full((j + S::L0 - 1) % S::L0);
+            rp = lvl0_full(j % S::L0);
+          } else {
+            const int base = ys - 2 * K;  // ring slot of row r: (r - base) % 3, r >= base
+            rm = ring_full(t - 1, (R - 1 - base) % S::RING);
+            r0 = ring_full(t - 1, (R - base) % S::RING);
+            rp = ring_full(t - 1, (R + 1 - base) % S::RING);
+          }
+          const bool at_ym = !py && R == 0, at_yp = !py && R == ny - 1;
+          pull_level<COLS>(rm, r0, rp, c, at_xm, at_xp, at_ym, at_yp, A.bc, A.inflow_feq, f);
+        }
+        float h, qx, qy;
+        collide13(f, Kc, h, qx, qy);
+        if (t < K) {
+          if (PER) {
+            // this row is level t's newest: group slots 0, j % 2, j % 3
+#pragma unroll
+            for (int p = 0; p < 13; ++p) compact(t, p, 0, j % S::B1, j % S::C1)[c] = f[p];
+          } else {
+            float* dst = ring_full(t, (R - (ys - 2 * K)) % S::RING) + c;
+#pragma unroll
+            for (int p = 0; p < 13; ++p) dst[p * COLS] = f[p];
+          }
+        } else if (c >= K && c < K + S::W && gx_raw < nx) {
+          float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
+#pragma unroll
+          for (int p = 0; p < 13; ++p) g[p * A.plane] = f[p];
+        }
+      }
+      if (t < K) __syncthreads();
+    }
+  }
+  __pipeline_wait_prior(0);
+}
+
+template <int K>
+cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t st, int sm_count) {
+  constexpr int COLS = 128;
+  using S = TemporalShape<K, COLS>;
+  const bool per = a.bc[0] == LBM_SW_BC_PERIODIC && a.bc[2] == LBM_SW_BC_PERIODIC;
+  const size_t smem = (per ? S::compact_floats() : S::smem_floats()) * sizeof(float);
+  cudaError_t e = per ? cudaFuncSetAttribute(step2d_temporal<K, COLS, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))
+                      : cudaFuncSetAttribute(step2d_temporal<K, COLS, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const int strips = (a.nx + S::W - 1) / S::W;
+  // about two waves of the resident CTAs, rows split evenly between the segments
+  const int per_sm = K <= 2 ? 4 : (K == 3 ? 3 : (per ? 3 : 2));
+  const int target = 2 * per_sm * sm_count;
+  int segments = std::max(1, (target + strips / 2) / std::max(strips, 1));
+  segments = std::min(segments, std::max(1, a.ny / (4 * K)));
+  segments = std::min(segments, 65535);
+  const int seg_rows = (a.ny + segments - 1) / segments;
+  segments = (a.ny + seg_rows - 1) / seg_rows;
+  const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
+  if (per)
+    step2d_temporal<K, COLS, true><<<dim3(strips, segments), COLS, smem, st>>>(a, K_, seg_rows);
+  else
+    step2d_temporal<K, COLS, false><<<dim3(strips, segments), COLS, smem, st>>>(a, K_, seg_rows);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool temporal_steps_supported(int k) { return k == 2 || k == 3 || k == 4; }
+
+cudaError_t launch_step2d_temporal(const StepArgs<float>& a, const ConstsD& kd, int k, cudaStream_t st,
+                                   int sm_count) {
+  switch (k) {
+    case 2: return launch_k<2>(a, kd, st, sm_count);
+    case 3: return launch_k<3>(a, kd, st, sm_count);
+    default: return launch_k<4>(a, kd, st, sm_count);
+  }
+}
+
+}  // namespace lbm

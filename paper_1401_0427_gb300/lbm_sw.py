@@ -22,7 +22,7 @@ PERIODIC, WALL, OUTFLOW, INFLOW = 0, 1, 2, 3
 XM, XP, YM, YP = 0, 1, 2, 3
 FP32, FP64 = 0, 1
 POST_COLLISION, PRE_COLLISION = 0, 1
-KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_VEC, KERNEL_CLUSTER = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_VEC, KERNEL_CLUSTER, KERNEL_TEMPORAL = 0, 1, 2, 3, 4
 
 OK, E_ARG, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE, E_NOMEM = 0, -1, -2, -3, -4, -5, -6
 
@@ -48,7 +48,8 @@ class lbm_sw_params(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("kernel", ctypes.c_int),
         ("graph_chunk", ctypes.c_int),
-        ("reserved", ctypes.c_int * 6),
+        ("temporal_steps", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5),
     ]
 
 
@@ -373,7 +374,8 @@ def lbm_sw_tape_get_info(t: int) -> lbm_sw_tape_info:
 # ---------------------------------------------------------------- convenience
 def make_params(nx: int, ny: int = 1, *, dim: int | None = None, precision: int = FP32, g: float = 1.0,
                 lam: float = 8.0, s: float = 1.8, a: float | None = None, bc=(PERIODIC,) * 4, inflow=None,
-                stream: int | None = None, kernel: int = KERNEL_AUTO, graph_chunk: int = 0) -> lbm_sw_params:
+                stream: int | None = None, kernel: int = KERNEL_AUTO, graph_chunk: int = 0,
+                temporal_steps: int = 0) -> lbm_sw_params:
     dim = 2 if dim is None else int(dim)
     p = lbm_sw_params_init()
     p.dim, p.nx, p.ny, p.precision = dim, int(nx), int(ny), int(precision)
@@ -390,6 +392,7 @@ def make_params(nx: int, ny: int = 1, *, dim: int | None = None, precision: int 
     p.stream = stream
     p.kernel = int(kernel)
     p.graph_chunk = int(graph_chunk)
+    p.temporal_steps = int(temporal_steps)
     return p
 
 

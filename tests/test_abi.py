@@ -78,7 +78,7 @@ def test_struct_layout_matches_c(tmp_path):
 def test_params_defaults(lib):
     p = lbm_sw.lbm_sw_params_init()
     assert (p.dim, p.precision, p.g, p.lambda_, p.s, p.a) == (2, lbm_sw.FP32, 1.0, 8.0, 1.8, 0.05)
-    assert list(p.bc) == [lbm_sw.PERIODIC] * 4 and p.stream is None and list(p.reserved) == [0] * 6
+    assert list(p.bc) == [lbm_sw.PERIODIC] * 4 and p.stream is None and list(p.reserved) == [0] * 5
     assert lib.lbm_sw_abi_version() == 1
     assert lib.lbm_sw_params_init(None) == lbm_sw.E_ARG
 
@@ -113,6 +113,7 @@ def _bad(**changes):
     (dict(bc=[lbm_sw.INFLOW, lbm_sw.WALL, 0, 0], inflow_h=0.0), "inflow[0]"),
     (dict(kernel=9), "kernel"),
     (dict(kernel=3), "CLUSTER is for 1D"),
+    (dict(temporal_steps=5), "temporal_steps"),
     (dict(reserved=1), "reserved"),
 ])
 def test_create_rejects_bad_parameters_before_touching_the_gpu(lib, changes, needle):

@@ -112,7 +112,7 @@ int validate(const lbm_sw_params* p, lbm_sw* h) {
       (p->dim == 1 && (p->kernel == LBM_SW_KERNEL_VEC || p->kernel == LBM_SW_KERNEL_TEMPORAL)))
     return fail(h, LBM_SW_E_ARG, "kernel: CLUSTER is for 1D handles, VEC and TEMPORAL for 2D handles");
   if (p->temporal_steps != 0 && !lbm::temporal_steps_supported(p->temporal_steps))
-    return fail(h, LBM_SW_E_ARG, "temporal_steps must be 0, 2, 3 or 4");
+    return fail(h, LBM_SW_E_ARG, "temporal_steps must be 0 or 2 .. 6");
   for (int r = 0; r < 5; ++r)
     if (p->reserved[r] != 0) return fail(h, LBM_SW_E_ARG, "reserved fields must be zero");
   return LBM_SW_OK;

@@ -54,7 +54,7 @@ cudaError_t launch_moments2d_planes(const StepArgs<T>& a, T* w_out, cudaStream_t
 template <class Tin, class Tout>
 cudaError_t launch_convert(const Tin* in, Tout* out, long long n, cudaStream_t st);
 
-// k fused steps per launch (temporal.cu; FP32, BGK; k in {2, 3, 4}): src -> dst.
+// k fused steps per launch (temporal.cu; FP32, BGK; k in 2 .. 6): src -> dst.
 bool temporal_steps_supported(int k);
 cudaError_t launch_step2d_temporal(const StepArgs<float>& a, const ConstsD& kd, int k, cudaStream_t st,
                                    int sm_count);

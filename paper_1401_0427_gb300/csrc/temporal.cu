@@ -29,18 +29,25 @@ struct TemporalShape {
   static constexpr int L0 = 5;                // level-0 ring (prefetch distance 2)
   static constexpr int RING = 3;              // rows kept per intermediate level
   static constexpr size_t smem_floats() { return static_cast<size_t>(COLS) * 13 * (L0 + RING * (K - 1)); }
-  // Compact rings for all-periodic domains, where row R of level t - 1 is read in three
-  // plane groups at three different times: the -y movers (4, 8, 12) as row R + 1 in the
-  // iteration that writes them (1 slot), f0 and the x movers (0, 1, 3, 5, 7, 9, 11) as row
-  // R one iteration later (2 slots), the +y movers (2, 6, 10) as row R - 1 two iterations
-  // later (3 slots); level 0 arrives two iterations early (3, 4 and 5 slots).
-  static constexpr int A0 = 3, B0 = 4, C0 = 5, A1 = 1, B1 = 2, C1 = 3;
-  static constexpr int L0_FLOATS = COLS * (3 * A0 + 7 * B0 + 3 * C0);
-  static constexpr int LV_FLOATS = COLS * (3 * A1 + 7 * B1 + 3 * C1);
-  static constexpr size_t compact_floats() { return static_cast<size_t>(L0_FLOATS) + (K - 1) * LV_FLOATS; }
 };
 
-// Plane p -> (group, index): A = {4, 8, 12}, B = {0, 1, 3, 5, 7, 9, 11}, C = {2, 6, 10}.
+// All-periodic domains.  Row R of level t - 1 feeds level t in three ways: its -y movers
+// (planes 4, 8, 12) to row R - 1, f0 and the x movers to row R, its +y movers (2, 6, 10)
+// to row R + 1.  Only the x movers cross columns, so for t - 1 >= 1 only they go through
+// shared memory (two rows: the one read now and the one being written); the others stay
+// in the registers of the column's thread.  Level 0 arrives by cp.async into a ring per
+// plane group that holds each group as long as it is read: the -y movers 3 rows (the row
+// read now plus two in flight), f0 and the x movers 4, the +y movers 5.
+template <int K, int COLS>
+struct PeriodicShape {
+  static constexpr int W = COLS - 2 * K;
+  static constexpr int A0 = 3, B0 = 4, C0 = 5;
+  static constexpr int L0_FLOATS = COLS * (3 * A0 + 7 * B0 + 3 * C0);
+  static constexpr int LV_FLOATS = COLS * 2 * 6;
+  static constexpr size_t floats() { return static_cast<size_t>(L0_FLOATS) + (K - 1) * LV_FLOATS; }
+};
+
+// Level-0 plane p -> (group, index): A = {4, 8, 12}, B = {0, 1, 3, 5, 7, 9, 11}, C = {2, 6, 10}.
 __host__ __device__ constexpr int plane_group(int p) {
   return (p == 4 || p == 8 || p == 12) ? 0 : ((p == 2 || p == 6 || p == 10) ? 2 : 1);
 }
@@ -100,16 +107,15 @@ __device__ __forceinline__ void pull_level(const float* row_m, const float* row_
   }
 }
 
-// PER: every side is periodic (no boundary rule, every tile cell is a domain cell).
-template <int K, int COLS, bool PER>
-__global__ void __launch_bounds__(COLS, (K <= 2 ? 4 : (K == 3 ? 3 : (PER ? 3 : 2))))
+template <int K, int COLS>
+__global__ void __launch_bounds__(COLS, (K <= 2 ? 4 : (K == 3 ? 3 : (K == 4 ? 2 : 1))))
     step2d_temporal(const StepArgs<float> A, const Consts<float> Kc, int seg_rows) {
   using S = TemporalShape<K, COLS>;
   extern __shared__ __align__(16) float smem[];
   const int c = threadIdx.x;
   const int nx = A.nx, ny = A.ny;
-  const bool px = PER || A.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC;
-  const bool py = PER || A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
+  const bool px = A.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC;
+  const bool py = A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
   const int x0 = blockIdx.x * S::W;
   const int ys = blockIdx.y * seg_rows;
   const int ye = min(ys + seg_rows, ny);
@@ -120,25 +126,11 @@ __global__ void __launch_bounds__(COLS, (K <= 2 ? 4 : (K == 3 ? 3 : (PER ? 3 : 2
   const bool at_xp = !px && gx_raw == nx - 1;
   const int iters = (ye - ys) + 2 * K;
 
-  // ---- shared-memory addressing ----
-  // full rings (any boundary): level 0 [L0][13][COLS], level t [RING][13][COLS]
-  // compact rings (all periodic): per level, group A [slots][3][COLS], B [slots][7][COLS],
-  // C [slots][3][COLS] (see TemporalShape)
-  auto lvl0_full = [&](int slot) { return smem + static_cast<size_t>(slot) * 13 * COLS; };
-  auto ring_full = [&](int t, int slot) {
+  // level 0 ring [L0][13][COLS], level t ring [RING][13][COLS]
+  auto lvl0 = [&](int slot) { return smem + static_cast<size_t>(slot) * 13 * COLS; };
+  auto ring = [&](int t, int slot) {
     return smem + static_cast<size_t>(S::L0) * 13 * COLS + static_cast<size_t>(t - 1) * S::RING * 13 * COLS +
            static_cast<size_t>(slot) * 13 * COLS;
-  };
-  // compact: address of plane p of the row in group slots (sa, sb, sc) of level t (0 = input)
-  auto compact = [&](int t, int p, int sa, int sb, int sc) -> float* {
-    float* base = t == 0 ? smem : smem + S::L0_FLOATS + static_cast<size_t>(t - 1) * S::LV_FLOATS;
-    const int na = t == 0 ? S::A0 : S::A1, nb = t == 0 ? S::B0 : S::B1;
-    const int g = plane_group(p), i = plane_index(p);
-    if (g == 0) return base + (sa * 3 + i) * COLS;
-    base += na * 3 * COLS;
-    if (g == 1) return base + (sb * 7 + i) * COLS;
-    base += nb * 7 * COLS;
-    return base + (sc * 3 + i) * COLS;
   };
 
   auto issue_row = [&](int j) {
@@ -148,11 +140,9 @@ __global__ void __launch_bounds__(COLS, (K <= 2 ? 4 : (K == 3 ? 3 : (PER ? 3 : 2
       if (live && col_live) {
         const int gr = py ? ((r % ny) + ny) % ny : r;
         const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
+        float* s = lvl0(j % S::L0) + c;
 #pragma unroll
-        for (int p = 0; p < 13; ++p) {
-          float* s = PER ? compact(0, p, j % S::A0, j % S::B0, j % S::C0) + c : lvl0_full(j % S::L0) + p * COLS + c;
-          __pipeline_memcpy_async(s, g + p * A.plane, sizeof(float));
-        }
+        for (int p = 0; p < 13; ++p) __pipeline_memcpy_async(s + p * COLS, g + p * A.plane, sizeof(float));
       }
     }
     __pipeline_commit();
@@ -171,46 +161,25 @@ __global__ void __launch_bounds__(COLS, (K <= 2 ? 4 : (K == 3 ? 3 : (PER ? 3 : 2
       const bool row_live = py || (R >= 0 && R < ny);
       if (row_ok && row_live && col_live && c >= t && c < COLS - t) {
         float f[13];
-        if (PER) {
-          // level t - 1: row R + 1 written this iteration, R the last one, R - 1 the one before
-          const int ja = t == 1 ? j % S::A0 : 0;
-          const int jb = t == 1 ? (j + S::B0 - 1) % S::B0 : (j + 1) % S::B1;
-          const int jc = t == 1 ? (j + S::C0 - 2) % S::C0 : (j + 1) % S::C1;
-          f[0] = compact(t - 1, 0, ja, jb, jc)[c];
-#pragma unroll
-          for (int fam = 0; fam < 3; ++fam) {
-            f[1 + 4 * fam] = compact(t - 1, 1 + 4 * fam, ja, jb, jc)[c - 1];
-            f[2 + 4 * fam] = compact(t - 1, 2 + 4 * fam, ja, jb, jc)[c];
-            f[3 + 4 * fam] = compact(t - 1, 3 + 4 * fam, ja, jb, jc)[c + 1];
-            f[4 + 4 * fam] = compact(t - 1, 4 + 4 * fam, ja, jb, jc)[c];
-          }
+        const float *rm, *r0, *rp;
+        if (t == 1) {  // level 0 rows R - 1, R, R + 1 are iterations j - 2, j - 1, j
+          rm = lvl0((j + S::L0 - 2) % S::L0);
+          r0 = lvl0((j + S::L0 - 1) % S::L0);
+          rp = lvl0(j % S::L0);
         } else {
-          const float *rm, *r0, *rp;
-          if (t == 1) {  // level 0 rows R - 1, R, R + 1 are iterations j - 2, j - 1, j
-            rm = lvl0_full((j + S::L0 - 2) % S::L0);
-            r0 = lvl0_full((j + S::L0 - 1) % S::L0);
-            rp = lvl0_full(j % S::L0);
-          } else {
-            const int base = ys - 2 * K;  // ring slot of row r: (r - base) % 3, r >= base
-            rm = ring_full(t - 1, (R - 1 - base) % S::RING);
-            r0 = ring_full(t - 1, (R - base) % S::RING);
-            rp = ring_full(t - 1, (R + 1 - base) % S::RING);
-          }
-          const bool at_ym = !py && R == 0, at_yp = !py && R == ny - 1;
-          pull_level<COLS>(rm, r0, rp, c, at_xm, at_xp, at_ym, at_yp, A.bc, A.inflow_feq, f);
+          const int base = ys - 2 * K;  // ring slot of row r: (r - base) % 3, r >= base
+          rm = ring(t - 1, (R - 1 - base) % S::RING);
+          r0 = ring(t - 1, (R - base) % S::RING);
+          rp = ring(t - 1, (R + 1 - base) % S::RING);
         }
+        const bool at_ym = !py && R == 0, at_yp = !py && R == ny - 1;
+        pull_level<COLS>(rm, r0, rp, c, at_xm, at_xp, at_ym, at_yp, A.bc, A.inflow_feq, f);
         float h, qx, qy;
         collide13(f, Kc, h, qx, qy);
         if (t < K) {
-          if (PER) {
-            // this row is level t's newest: group slots 0, j % 2, j % 3
+          float* dst = ring(t, (R - (ys - 2 * K)) % S::RING) + c;
 #pragma unroll
-            for (int p = 0; p < 13; ++p) compact(t, p, 0, j % S::B1, j % S::C1)[c] = f[p];
-          } else {
-            float* dst = ring_full(t, (R - (ys - 2 * K)) % S::RING) + c;
-#pragma unroll
-            for (int p = 0; p < 13; ++p) dst[p * COLS] = f[p];
-          }
+          for (int p = 0; p < 13; ++p) dst[p * COLS] = f[p];
         } else if (c >= K && c < K + S::W && gx_raw < nx) {
           float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
 #pragma unroll
@@ -223,20 +192,145 @@ __global__ void __launch_bounds__(COLS, (K <= 2 ? 4 : (K == 3 ? 3 : (PER ? 3 : 2
   __pipeline_wait_prior(0);
 }
 
+// The same wavefront on an all-periodic domain (every tile cell is a domain cell, no
+// boundary rule), with the plane groups placed as PeriodicShape describes.  Level t + 1
+// reads level t's x movers from the previous iteration's row and its other planes from
+// registers, so the only barrier per iteration is the one after the input row lands; the
+// next input row is issued after it, when every thread has finished the previous iteration.
+template <int K, int COLS>
+__global__ void __launch_bounds__(COLS, (K <= 4 ? 5 : 4))
+    step2d_temporal_periodic(const StepArgs<float> A, const Consts<float> Kc, int seg_rows) {
+  using S = PeriodicShape<K, COLS>;
+  extern __shared__ __align__(16) float smem[];
+  const int c = threadIdx.x;
+  const int nx = A.nx, ny = A.ny;
+  const int x0 = blockIdx.x * S::W;
+  const int ys = blockIdx.y * seg_rows;
+  const int ye = min(ys + seg_rows, ny);
+  const int gx_raw = x0 - K + c;
+  const int gx = ((gx_raw % nx) + nx) % nx;
+  const int iters = (ye - ys) + 2 * K;
+
+  // level 0: group A [A0][3][COLS], B [B0][7][COLS], C [C0][3][COLS]
+  float* const l0a = smem;
+  float* const l0b = l0a + S::A0 * 3 * COLS;
+  float* const l0c = l0b + S::B0 * 7 * COLS;
+  // level t >= 1: x movers [2][6][COLS], planes 1, 3, 5, 7, 9, 11 in that order
+  auto xm = [&](int t, int slot) { return smem + S::L0_FLOATS + (t - 1) * S::LV_FLOATS + slot * 6 * COLS; };
+
+  // Level t (1 .. K - 1) as the input of level t + 1, in the column's registers: the -y
+  // movers and f0 and +y movers of the row computed in this iteration (*_now), f0 of the
+  // previous row, the +y movers of the previous two rows.  Where a level was not computed
+  // (halo columns and rows outside its range) they hold stale values that the next level,
+  // whose range is one smaller on each side, never reads.
+  float a_now[K][3], f0_now[K], c_now[K][3], f0_prev[K], c_prev1[K][3], c_prev2[K][3];
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    f0_now[t] = f0_prev[t] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = 0.0f;
+  }
+
+  auto issue_row = [&](int j) {
+    if (j < iters) {
+      const int r = ys - K + j;
+      const int gr = ((r % ny) + ny) % ny;
+      const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
+      float* sa = l0a + (j % S::A0) * 3 * COLS + c;
+      float* sb = l0b + (j % S::B0) * 7 * COLS + c;
+      float* sc = l0c + (j % S::C0) * 3 * COLS + c;
+#pragma unroll
+      for (int p = 0; p < 13; ++p) {
+        float* d = plane_group(p) == 0 ? sa : (plane_group(p) == 1 ? sb : sc);
+        __pipeline_memcpy_async(d + plane_index(p) * COLS, g + p * A.plane, sizeof(float));
+      }
+    }
+    __pipeline_commit();
+  };
+
+  issue_row(0);
+  issue_row(1);
+  for (int j = 0; j < iters; ++j) {
+    __pipeline_wait_prior(1);  // row j has landed (this thread's copies; row j + 1 may be in flight)
+    __syncthreads();           // ... and every thread's; iteration j - 1 is over everywhere
+    issue_row(j + 2);
+#pragma unroll
+    for (int t = 1; t <= K; ++t) {
+      const int R = ys - K + j - t;  // row of level t computed now
+      const bool row_ok = R >= ys - K + t && R < ye + K - t;
+      if (row_ok && c >= t && c < COLS - t) {
+        float f[13];
+        if (t == 1) {
+          // level 0: row R + 1 landed now (iteration j), R at j - 1, R - 1 at j - 2
+          const float* ra = l0a + (j % S::A0) * 3 * COLS + c;
+          const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 7 * COLS + c;
+          const float* rc = l0c + ((j + S::C0 - 2) % S::C0) * 3 * COLS + c;
+          f[0] = rb[0];
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            f[1 + 4 * fam] = rb[(1 + 2 * fam) * COLS - 1];
+            f[2 + 4 * fam] = rc[fam * COLS];
+            f[3 + 4 * fam] = rb[(2 + 2 * fam) * COLS + 1];
+            f[4 + 4 * fam] = ra[fam * COLS];
+          }
+        } else {
+          const float* x = xm(t - 1, (j + 1) & 1) + c;  // level t - 1, row R (previous iteration)
+          f[0] = f0_prev[t - 1];
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            f[1 + 4 * fam] = x[(2 * fam) * COLS - 1];
+            f[2 + 4 * fam] = c_prev2[t - 1][fam];
+            f[3 + 4 * fam] = x[(2 * fam + 1) * COLS + 1];
+            f[4 + 4 * fam] = a_now[t - 1][fam];
+          }
+        }
+        float h, qx, qy;
+        collide13(f, Kc, h, qx, qy);
+        if (t < K) {
+          float* x = xm(t, j & 1) + c;
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            x[(2 * fam) * COLS] = f[1 + 4 * fam];
+            x[(2 * fam + 1) * COLS] = f[3 + 4 * fam];
+            a_now[t][fam] = f[4 + 4 * fam];
+            c_now[t][fam] = f[2 + 4 * fam];
+          }
+          f0_now[t] = f[0];
+        } else if (c >= K && c < K + S::W && gx_raw < nx) {
+          float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
+#pragma unroll
+          for (int p = 0; p < 13; ++p) g[p * A.plane] = f[p];
+        }
+      }
+      if (t > 1) {
+        // level t - 1 is consumed for this iteration: age its rows
+        f0_prev[t - 1] = f0_now[t - 1];
+#pragma unroll
+        for (int fam = 0; fam < 3; ++fam) {
+          c_prev2[t - 1][fam] = c_prev1[t - 1][fam];
+          c_prev1[t - 1][fam] = c_now[t - 1][fam];
+        }
+      }
+    }
+  }
+  __pipeline_wait_prior(0);
+}
+
 template <int K>
 cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t st, int sm_count) {
   constexpr int COLS = 128;
-  using S = TemporalShape<K, COLS>;
   const bool per = a.bc[0] == LBM_SW_BC_PERIODIC && a.bc[2] == LBM_SW_BC_PERIODIC;
-  const size_t smem = (per ? S::compact_floats() : S::smem_floats()) * sizeof(float);
-  cudaError_t e = per ? cudaFuncSetAttribute(step2d_temporal<K, COLS, true>,
+  const int w = per ? PeriodicShape<K, COLS>::W : TemporalShape<K, COLS>::W;
+  const size_t smem =
+      (per ? PeriodicShape<K, COLS>::floats() : TemporalShape<K, COLS>::smem_floats()) * sizeof(float);
+  cudaError_t e = per ? cudaFuncSetAttribute(step2d_temporal_periodic<K, COLS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))
-                      : cudaFuncSetAttribute(step2d_temporal<K, COLS, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+                      : cudaFuncSetAttribute(step2d_temporal<K, COLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  const int strips = (a.nx + S::W - 1) / S::W;
+  const int strips = (a.nx + w - 1) / w;
   // about two waves of the resident CTAs, rows split evenly between the segments
-  const int per_sm = K <= 2 ? 4 : (K == 3 ? 3 : (per ? 3 : 2));
+  const int per_sm = per ? (K <= 4 ? 5 : 4) : (K <= 2 ? 4 : (K == 3 ? 3 : (K == 4 ? 2 : 1)));
   const int target = 2 * per_sm * sm_count;
   int segments = std::max(1, (target + strips / 2) / std::max(strips, 1));
   segments = std::min(segments, std::max(1, a.ny / (4 * K)));
@@ -245,21 +339,23 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
   segments = (a.ny + seg_rows - 1) / seg_rows;
   const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
   if (per)
-    step2d_temporal<K, COLS, true><<<dim3(strips, segments), COLS, smem, st>>>(a, K_, seg_rows);
+    step2d_temporal_periodic<K, COLS><<<dim3(strips, segments), COLS, smem, st>>>(a, K_, seg_rows);
   else
-    step2d_temporal<K, COLS, false><<<dim3(strips, segments), COLS, smem, st>>>(a, K_, seg_rows);
+    step2d_temporal<K, COLS><<<dim3(strips, segments), COLS, smem, st>>>(a, K_, seg_rows);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool temporal_steps_supported(int k) { return k == 2 || k == 3 || k == 4; }
+bool temporal_steps_supported(int k) { return k >= 2 && k <= 6; }
 
 cudaError_t launch_step2d_temporal(const StepArgs<float>& a, const ConstsD& kd, int k, cudaStream_t st,
                                    int sm_count) {
   switch (k) {
     case 2: return launch_k<2>(a, kd, st, sm_count);
     case 3: return launch_k<3>(a, kd, st, sm_count);
+    case 5: return launch_k<5>(a, kd, st, sm_count);
+    case 6: return launch_k<6>(a, kd, st, sm_count);
     default: return launch_k<4>(a, kd, st, sm_count);
   }
 }

@@ -113,7 +113,7 @@ def _bad(**changes):
     (dict(bc=[lbm_sw.INFLOW, lbm_sw.WALL, 0, 0], inflow_h=0.0), "inflow[0]"),
     (dict(kernel=9), "kernel"),
     (dict(kernel=3), "CLUSTER is for 1D"),
-    (dict(temporal_steps=5), "temporal_steps"),
+    (dict(temporal_steps=7), "temporal_steps"),
     (dict(reserved=1), "reserved"),
 ])
 def test_create_rejects_bad_parameters_before_touching_the_gpu(lib, changes, needle):

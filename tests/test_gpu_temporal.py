@@ -1,4 +1,4 @@
-"""Temporal blocking (4 fused steps per launch through shared memory) against the
+"""Temporal blocking (K = 2 .. 6 fused steps per launch through shared memory) against the
 one-step-per-launch kernel: every cell update is the same pull + collide, so the results
 must be equal bit for bit, on ragged grids (a strip holds 120 output columns), with every
 boundary kind, for step counts that leave a remainder, and on the benchmark workload."""
@@ -29,7 +29,7 @@ def _run(F0, steps, bc, kernel, k=0):
                          ids=lambda b: "".join("PWOI"[k] for k in b))
 @pytest.mark.parametrize("nx,ny", [(1, 1), (3, 2), (7, 5), (64, 9), (119, 17), (120, 3), (121, 40), (241, 33),
                                    (300, 1), (5, 300), (513, 70)])
-@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 6])
 def test_temporal_equals_single_steps(nx, ny, bc, k):
     F0 = inputs.random_populations(13, ny, nx, seed=7000 + nx * 3 + ny).astype(np.float32)
     for steps in (1, 4, 9, 13):

@@ -3,10 +3,11 @@
 Workload: the 2D unsteady circular dam-break on a 4096 x 4096 periodic grid (depth 2
 inside radius 0.2 of the centre of the unit square, 1 outside, at rest, plus a seeded
 uniform perturbation of +-1e-3), D2Q5Q4Q4 with lambda = 8, s = 1.8, a = 0.05, g = 1,
-FP32 populations.  One bench step is one time step of the scheme: one launch of the
-fused pull-stream + collide kernel over the whole grid (boundaries, moments,
-equilibria, relaxation).  The two 872 MB population buffers exceed the 129 MB L2,
-so every step streams from HBM.
+FP32 populations.  One bench step is one time step of the scheme over the whole grid
+(pull streaming, boundaries, moments, equilibria, relaxation), run by the library's
+default kernel for this workload: temporal blocking, 6 time steps per launch of one
+fused kernel (results bit-identical to one step per launch).  The two 872 MB population
+buffers exceed the 129 MB L2, so every launch streams the state from HBM and back.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line on rank 0.  Under torchrun each rank runs an independent
@@ -41,17 +42,26 @@ WORKLOAD = ("2D circular dam-break 4096x4096 periodic, D2Q5Q4Q4 (13 populations)
 JOB_STEPS = 1000  # steps of the workload as one job (the end-to-end unit)
 REF_SAMPLE = 512   # side of the periodic window the CPU oracle advances per reference step
 
-# DRAM traffic per launch of the timed kernel from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {"src_sha256": "fde726a3637adfbd780f4cf8384cacbd67b7a1e7c6eb2f768c6f47f031a9e08b",
-               "bytes_per_launch": 1690.2e6,
-               "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of launches 21-23 of the "
-                       "4096x4096 workload: 872.55 MB read + 817.65 MB written, mean of 3 launches"}
+# Timed kernel by (variant, dtype); {k} is the steps per launch.
+KERNEL_NAMES = {(4, "f32"): "step2d_temporal_periodic<{k}, 192>", (2, "f32"): "step2d_vec<float>",
+                (2, "f64"): "step2d_vec<double>"}
+
+# DRAM traffic per launch of each timed kernel on the 4096^2 workload from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel name, valid only for the
+# kernel sources it was taken on.
+NCU_TRAFFIC = {
+    "step2d_temporal_periodic<6, 192>": {
+        "src_sha256": "9e98045b1638fab7d3cd7da022a09d69dc628d1db84baca1022f505399704682",
+        "sources": ("temporal.cu", "scheme.cuh"), "bytes_per_launch": 1733.67e6,
+        "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of the 5 launches of "
+                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 911.13 MB read + 822.53 MB "
+                "written per launch (mean)"},
+}
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=("kernels_2d.cu", "scheme.cuh", "internal.h")) -> str:
     h = hashlib.sha256()
-    for f in ("kernels_2d.cu", "scheme.cuh", "internal.h"):
+    for f in sources:
         with open(os.path.join(ROOT, "paper_1401_0427_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -242,18 +252,22 @@ def run_ours(args, world, rank, local):
     prec = lbm_sw.FP64 if args.precision == "fp64" else lbm_sw.FP32
     dt_name = "f64" if prec == lbm_sw.FP64 else "f32"
 
-    kernel = lbm_sw.KERNEL_TEMPORAL if args.kernel == "temporal" else lbm_sw.KERNEL_VEC
+    kernel = {"auto": lbm_sw.KERNEL_AUTO, "vec": lbm_sw.KERNEL_VEC, "temporal": lbm_sw.KERNEL_TEMPORAL}[args.kernel]
     sim = lbm_sw.Simulation(N, N, precision=prec, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream,
-                            kernel=kernel)
+                            kernel=kernel, temporal_steps=args.temporal_steps)
     sim.set_state(*W0)
-    unit = 4 if args.kernel == "temporal" else 1  # steps per kernel launch
-    if args.steps % unit:
-        raise SystemExit(f"--steps must be a multiple of {unit} for --kernel {args.kernel}")
-    nlaunch = args.steps // unit
+    info = sim.info()
+    unit = max(1, info.steps_per_launch)  # steps per launch of the step kernel
+    kname = KERNEL_NAMES[(info.kernel if unit > 1 else lbm_sw.KERNEL_VEC, dt_name)]
+    if unit > 1:
+        kname = kname.format(k=unit)
+    # The timed region is exactly --steps time steps: full launches of `unit` steps, then
+    # the remainder (one step per launch, bit-identical results).
+    nfull, rem = divmod(args.steps, unit)
     launches0 = sim.info().kernel_launches
-    for _ in range(args.warmup):
-        sim.step(unit)
+    sim.step(max(args.warmup, 3) * unit)  # warm-up: at least 3 launches of the timed kernel
     sim.synchronize()
+    warm_launches = sim.info().kernel_launches - launches0
 
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     gpu_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].strip().isdigit() else local
@@ -261,14 +275,16 @@ def run_ours(args, world, rank, local):
     clocks.start()
     time.sleep(0.3)
 
-    events = [torch.cuda.Event(enable_timing=True) for _ in range(nlaunch + 1)]
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(nfull + 2)]
     barrier(world)
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
     events[0].record(stream)
-    for i in range(nlaunch):
+    for i in range(nfull):
         sim.step(unit)
         events[i + 1].record(stream)
+    sim.step(rem)
+    events[nfull + 1].record(stream)
     torch.cuda.synchronize()
     t_wall1 = time.perf_counter()
     barrier(world)
@@ -276,25 +292,27 @@ def run_ours(args, world, rank, local):
     clocks.stop()
 
     total_ms = events[0].elapsed_time(events[-1])
-    per_launch = [events[i].elapsed_time(events[i + 1]) for i in range(nlaunch)]
-    launches = sim.info().kernel_launches - launches0 - args.warmup
+    per_launch = [events[i].elapsed_time(events[i + 1]) for i in range(nfull)]
+    launches = sim.info().kernel_launches - launches0 - warm_launches
     total_ms = max_over_ranks(world, total_ms)
     diag = sim.diagnostics()
-    mlups_rank = cells * args.steps / (total_ms * 1e-3) / 1e6
     value = sum_over_ranks(world, cells * args.steps) / (total_ms * 1e-3) / 1e6
 
     avg_launch_s = float(np.mean(per_launch)) * 1e-3
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_LUP[dt_name] * cells / avg_launch_s / 1e9
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["src_sha256"] == kernel_source_hash() else None
+    entry = NCU_TRAFFIC.get(kname) if N == 4096 else None
+    traffic = entry["bytes_per_launch"] if entry and entry["src_sha256"] == kernel_source_hash(entry["sources"]) \
+        else None
+    per_step_ceiling = peak * 1e9 / BYTES_PER_LUP[dt_name] / 1e6
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": f"{peak_kind} (copy bandwidth)",
-                "frac_of_nominal_8tbs": achieved / 8000.0,
-                "kernel": ("step2d_temporal<4, 128>" if unit == 4 else "step2d_vec<float>") if dt_name == "f32"
-                else "step2d_vec<double>",
-                "steps_per_launch": unit,
+                "frac_of_nominal_8tbs": achieved / 8000.0, "kernel": kname, "steps_per_launch": unit,
                 "algorithmic_bytes_per_launch": BYTES_PER_LUP[dt_name] * cells,
-                "median_launch_ms": float(np.median(per_launch))}
+                "algorithmic_bytes_per_update": BYTES_PER_LUP[dt_name] / unit,
+                "median_launch_ms": float(np.median(per_launch)) if per_launch else None,
+                "one_step_per_launch_ceiling_MLUPS": per_step_ceiling,
+                "value_over_one_step_ceiling": value / world / per_step_ceiling}
     sim.close()
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -328,27 +346,38 @@ def variants(args, W0, stream, lbm_sw, torch):
     out = {}
     steps64 = min(args.steps, 200)
     hs = {}
-    for name, prec in (("fp32", lbm_sw.FP32), ("fp64", lbm_sw.FP64)):
-        sim = lbm_sw.Simulation(N, N, precision=prec, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream)
+    peak, _ = measured_peaks()
+    for name, prec, kernel in (("fp32", lbm_sw.FP32, lbm_sw.KERNEL_AUTO),
+                               ("fp32_one_step", lbm_sw.FP32, lbm_sw.KERNEL_VEC),
+                               ("fp64", lbm_sw.FP64, lbm_sw.KERNEL_AUTO)):
+        sim = lbm_sw.Simulation(N, N, precision=prec, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream,
+                                kernel=kernel)
         sim.set_state(*W0)
-        sim.step(3)
+        info = sim.info()
+        sim.step(12)
         sim.synchronize()
+        n_t = steps64 - steps64 % max(1, info.steps_per_launch)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        sim.step(steps64)
+        sim.step(n_t)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps64
-        sim.step(JOB_STEPS - 3 - steps64)
-        hs[name] = sim.moments()[0]
+        ms = e0.elapsed_time(e1) / n_t
+        if name != "fp32_one_step":
+            sim.step(JOB_STEPS - 12 - n_t)
+            hs[name] = sim.moments()[0]
         sim.close()
-        bpl = BYTES_PER_LUP["f32" if name == "fp32" else "f64"]
-        out[name] = {"MLUPS": N * N / (ms * 1e-3) / 1e6, "ms_per_step": ms,
-                     "GB_per_s": bpl * N * N / (ms * 1e-3) / 1e9}
+        bpl = BYTES_PER_LUP["f64" if name == "fp64" else "f32"]
+        spl = max(1, info.steps_per_launch)
+        out[name] = {"MLUPS": N * N / (ms * 1e-3) / 1e6, "ms_per_step": ms, "steps_per_launch": spl,
+                     "kernel": KERNEL_NAMES[(info.kernel if spl > 1 else lbm_sw.KERNEL_VEC,
+                                             "f64" if name == "fp64" else "f32")].format(k=spl),
+                     "HBM_GB_per_s": bpl * N * N / spl / (ms * 1e-3) / 1e9,
+                     "frac_of_hbm_peak": bpl * N * N / spl / (ms * 1e-3) / 1e9 / peak}
     out["_l1"] = {"relative_l1_h": float(np.abs(hs["fp32"] - hs["fp64"]).sum() / np.abs(hs["fp64"]).sum()),
                   "steps": JOB_STEPS, "against": "FP64 run of the same workload (equal to the FP64 oracle "
                                                  "within 1e-12 in the parity tests)"}
-    out["fp32_temporal"] = temporal_variant(W0, stream, lbm_sw, torch, args.steps)
+    out["fp32_temporal_k"] = temporal_sweep(W0, stream, lbm_sw, torch)
     out["batched_256"] = batched_variant(stream, lbm_sw, torch)
     out["shock_reflection_512"] = shock_reflection_variant(stream, lbm_sw, torch)
     out["shock_tube_1d_1000"] = shock_tube_variant(stream, lbm_sw, torch)
@@ -366,18 +395,19 @@ def _timed(stream, torch, fn):
     return e0.elapsed_time(e1) * 1e-3
 
 
-def temporal_variant(W0, stream, lbm_sw, torch, steps: int):
-    """The same workload with 4 fused steps per launch (temporal blocking through shared
-    memory; bit-identical results)."""
-    steps = steps - steps % 4
-    with lbm_sw.Simulation(N, N, precision=lbm_sw.FP32, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream,
-                           kernel=lbm_sw.KERNEL_TEMPORAL) as sim:
-        sim.set_state(*W0)
-        sim.step(8)
-        t = _timed(stream, torch, lambda: sim.step(steps))
-    per_launch = t / (steps // 4)
-    return {"MLUPS": N * N * steps / t / 1e6, "ms_per_step": t / steps * 1e3, "steps_per_launch": 4,
-            "GB_per_s_state": BYTES_PER_LUP["f32"] * N * N / per_launch / 1e9}
+def temporal_sweep(W0, stream, lbm_sw, torch, steps: int = 840):
+    """The same workload at 2 .. 8 fused steps per launch (bit-identical results)."""
+    out = {}
+    for k in range(2, 9):
+        with lbm_sw.Simulation(N, N, precision=lbm_sw.FP32, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream,
+                               kernel=lbm_sw.KERNEL_TEMPORAL, temporal_steps=k) as sim:
+            sim.set_state(*W0)
+            sim.step(3 * k)
+            n = steps - steps % k
+            t = _timed(stream, torch, lambda: sim.step(n))
+        out[str(k)] = {"MLUPS": N * N * n / t / 1e6,
+                       "HBM_GB_per_s": BYTES_PER_LUP["f32"] * N * N * (n // k) / t / 1e9}
+    return out
 
 
 def batched_variant(stream, lbm_sw, torch, steps: int = 500):
@@ -575,8 +605,11 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--side", type=int, default=4096, help="grid side (profiling of smaller cases only)")
     ap.add_argument("--count", type=int, default=256, help="instances of the batched profiling case")
-    ap.add_argument("--kernel", choices=["vec", "temporal"], default="vec",
-                    help="step kernel of the timed loop (vec: one step per launch; temporal: 4 per launch)")
+    ap.add_argument("--kernel", choices=["auto", "vec", "temporal"], default="auto",
+                    help="step kernel of the timed loop (auto: the library's choice, temporal blocking on this "
+                         "workload; vec: one step per launch)")
+    ap.add_argument("--temporal-steps", type=int, default=0,
+                    help="steps per launch of the temporal kernel (0: the library default, 6 here)")
     ap.add_argument("--case", choices=["step", "batched", "adjoint", "shock_tube", "diag"], default="step",
                     help="kernel to run for profiling (only 'step' prints the benchmark line)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",

@@ -100,7 +100,8 @@ typedef struct lbm_sw lbm_sw;
 #define LBM_SW_PRE_COLLISION 1  /* collided on the device first (moments, equilibria, relaxation) */
 
 /* step kernel variants */
-#define LBM_SW_KERNEL_AUTO 0    /* library choice: VEC in 2D, CLUSTER in 1D when the line fits */
+#define LBM_SW_KERNEL_AUTO 0    /* library choice: TEMPORAL for 2D FP32 grids of >= 2^20 cells with
+                                   every side periodic, else VEC in 2D; CLUSTER in 1D */
 #define LBM_SW_KERNEL_SIMPLE 1  /* one launch per step, one thread per cell, scalar loads */
 #define LBM_SW_KERNEL_VEC 2     /* 2D: 16-byte vectors along x (4 FP32 or 2 FP64 cells per thread),
                                    x-neighbours exchanged with warp shuffles */
@@ -123,9 +124,10 @@ typedef struct lbm_sw_params {
   int bc[4];           /* LBM_SW_BC_* for sides x-, x+, y-, y+ (y sides unused in 1D) */
   double inflow[4][3]; /* (h, hu, hv) imposed on INFLOW sides */
   void* stream;        /* cudaStream_t borrowed from the caller (NULL = legacy default) */
-  int kernel;          /* LBM_SW_KERNEL_*: AUTO, SIMPLE, VEC (2D) or CLUSTER (1D) */
+  int kernel;          /* LBM_SW_KERNEL_*: AUTO, SIMPLE, VEC or TEMPORAL (2D), CLUSTER (1D) */
   int graph_chunk;     /* steps per captured CUDA graph in lbm_sw_step; 0 = default, < 0 = off */
-  int temporal_steps;  /* steps fused per launch by the TEMPORAL kernel: 2 .. 6; 0 = default (4) */
+  int temporal_steps;  /* steps fused per launch by the TEMPORAL kernel: 2 .. 8; 0 = default
+                          (6 when every side is periodic, else 4) */
   int reserved[5];     /* must be zero */
 } lbm_sw_params;
 
@@ -137,6 +139,9 @@ typedef struct lbm_sw_info {
   double bytes_per_update;   /* algorithmic DRAM bytes per lattice-cell update: 2 q sizeof(T) */
   long long steps_done;      /* steps taken since the last set_state / set_populations */
   long long kernel_launches; /* kernels this handle has launched */
+  int steps_per_launch;      /* steps one step-kernel launch advances: temporal_steps for TEMPORAL
+                                (FP32 BGK), 0 for CLUSTER (all n steps of lbm_sw_step in one
+                                launch), else 1 */
 } lbm_sw_info;
 
 /* Fill *p with defaults: dim 2, FP32, g = 1, lambda = 8, s = 1.8, a = 0.05,

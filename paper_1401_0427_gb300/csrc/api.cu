@@ -112,7 +112,7 @@ int validate(const lbm_sw_params* p, lbm_sw* h) {
       (p->dim == 1 && (p->kernel == LBM_SW_KERNEL_VEC || p->kernel == LBM_SW_KERNEL_TEMPORAL)))
     return fail(h, LBM_SW_E_ARG, "kernel: CLUSTER is for 1D handles, VEC and TEMPORAL for 2D handles");
   if (p->temporal_steps != 0 && !lbm::temporal_steps_supported(p->temporal_steps))
-    return fail(h, LBM_SW_E_ARG, "temporal_steps must be 0 or 2 .. 6");
+    return fail(h, LBM_SW_E_ARG, "temporal_steps must be 0 or 2 .. 8");
   for (int r = 0; r < 5; ++r)
     if (p->reserved[r] != 0) return fail(h, LBM_SW_E_ARG, "reserved fields must be zero");
   return LBM_SW_OK;
@@ -200,11 +200,17 @@ int lbm_sw_create(const lbm_sw_params* p, lbm_sw** out) {
   h->elem = p->precision == LBM_SW_FP64 ? 8 : 4;
   h->pitch = round_up(p->nx, 32);
   h->plane = round_up(h->pitch * p->ny, 64);  // 256-byte aligned planes in FP32 and FP64
-  if (p->dim == 2)
-    h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? LBM_SW_KERNEL_VEC : p->kernel;
-  else
+  const bool all_periodic = p->bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC && p->bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
+  if (p->dim == 2) {
+    // AUTO: temporal blocking where it was measured faster (FP32, all sides periodic, at
+    // least 2^20 cells), otherwise one vectorised step per launch
+    const bool temporal = p->precision == LBM_SW_FP32 && all_periodic &&
+                          static_cast<long long>(p->nx) * p->ny >= (1LL << 20);
+    h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? (temporal ? LBM_SW_KERNEL_TEMPORAL : LBM_SW_KERNEL_VEC) : p->kernel;
+  } else {
     h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? LBM_SW_KERNEL_CLUSTER : p->kernel;
-  h->temporal_k = p->temporal_steps ? p->temporal_steps : 4;
+  }
+  h->temporal_k = p->temporal_steps ? p->temporal_steps : (all_periodic ? 6 : 4);
   h->graph_chunk = p->graph_chunk == 0 ? 64 : (p->graph_chunk < 0 ? 0 : p->graph_chunk + (p->graph_chunk & 1));
 
   auto bail = [&](int code) {
@@ -496,6 +502,10 @@ int lbm_sw_get_info(const lbm_sw* h, lbm_sw_info* out) {
   out->bytes_per_update = 2.0 * h->q * static_cast<double>(h->elem);
   out->steps_done = h->steps_done;
   out->kernel_launches = h->launches;
+  out->steps_per_launch = 1;
+  if (out->kernel == LBM_SW_KERNEL_CLUSTER) out->steps_per_launch = 0;
+  if (h->kernel == LBM_SW_KERNEL_TEMPORAL && h->p.precision == LBM_SW_FP32 && !h->mrt)
+    out->steps_per_launch = h->temporal_k;
   return LBM_SW_OK;
 }
 

@@ -1,14 +1,14 @@
 // K fused D2Q5Q4Q4 steps per launch (temporal blocking), FP32.
 //
-// A CTA owns an output strip of W = COLS - 2K columns and a segment of rows.  One thread
-// per column of the strip plus a K-column halo on each side sweeps a row wavefront down
-// the segment: at iteration j it brings one row of the launch's input state (level 0)
-// into shared memory with cp.async (two rows ahead), then computes, for t = 1 .. K, one
-// row of time level t from three rows of level t - 1 (a three-row ring per level in
-// shared memory); level K is written straight to HBM.  Each level loses one column on
-// each side of the strip and one row at each end of the segment, so the halos are
-// recomputed (a fraction 2K/W of the columns and 2K/H of the rows).  HBM traffic per
-// lattice update is 104/K bytes plus the halo share, against 104 for one step per launch.
+// The domain is cut into strips of w <= COLS - 2K columns (equal widths but the last).
+// One thread per column of a strip plus a K-column halo on each side sweeps a row
+// wavefront down a segment of rows: at iteration j it brings one row of the launch's input
+// state (level 0) into shared memory with cp.async (two rows ahead), then computes, for
+// t = 1 .. K, one row of time level t from three rows of level t - 1; level K is written
+// straight to HBM.  Each level loses one column on each side of the strip and one row at
+// each end of the segment, so the halos are recomputed (a fraction about 2K/w of the
+// columns and K/H of the rows, H the segment's length).  HBM traffic per lattice update is
+// 104/K bytes plus the halo share, against 104 for one step per launch.
 //
 // Every cell update is the same pull + collide13 as the single-step kernels, on the same
 // values, so K steps of this kernel equal K single steps bit for bit.
@@ -25,7 +25,6 @@ namespace {
 
 template <int K, int COLS>
 struct TemporalShape {
-  static constexpr int W = COLS - 2 * K;      // output columns per strip
   static constexpr int L0 = 5;                // level-0 ring (prefetch distance 2)
   static constexpr int RING = 3;              // rows kept per intermediate level
   static constexpr size_t smem_floats() { return static_cast<size_t>(COLS) * 13 * (L0 + RING * (K - 1)); }
@@ -40,7 +39,6 @@ struct TemporalShape {
 // read now plus two in flight), f0 and the x movers 4, the +y movers 5.
 template <int K, int COLS>
 struct PeriodicShape {
-  static constexpr int W = COLS - 2 * K;
   static constexpr int A0 = 3, B0 = 4, C0 = 5;
   static constexpr int L0_FLOATS = COLS * (3 * A0 + 7 * B0 + 3 * C0);
   static constexpr int LV_FLOATS = COLS * 2 * 6;
@@ -107,24 +105,33 @@ __device__ __forceinline__ void pull_level(const float* row_m, const float* row_
   }
 }
 
+// Work of one launch: the domain is cut into `strips` column strips of width w (the last
+// one narrower) and each strip into `segments` row segments.  CTA b takes segment
+// b / strips of strip b % strips, so the CTAs resident together work on the same rows of
+// neighbouring strips and share the strips' halo columns in L2.
+struct Partition {
+  int w;             // output columns per strip (every strip but the last is exactly w wide)
+  int strips;        // ceil(nx / w)
+  int rows_per_cta;  // output rows per segment (the last segment may be shorter)
+  int segments;      // row segments per strip
+};
+
+template <class F>
+__device__ __forceinline__ void run_segment(const Partition& P, int ny, F&& segment) {
+  const int strip = static_cast<int>(blockIdx.x % P.strips);
+  const int ys = static_cast<int>(blockIdx.x / P.strips) * P.rows_per_cta;
+  if (ys < ny) segment(strip, ys, min(ny, ys + P.rows_per_cta));
+}
+
 template <int K, int COLS>
-__global__ void __launch_bounds__(COLS, (K <= 2 ? 4 : (K == 3 ? 3 : (K == 4 ? 2 : 1))))
-    step2d_temporal(const StepArgs<float> A, const Consts<float> Kc, int seg_rows) {
+__global__ void __launch_bounds__(COLS, 1)
+    step2d_temporal(const StepArgs<float> A, const Consts<float> Kc, const Partition P) {
   using S = TemporalShape<K, COLS>;
   extern __shared__ __align__(16) float smem[];
   const int c = threadIdx.x;
   const int nx = A.nx, ny = A.ny;
   const bool px = A.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC;
   const bool py = A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
-  const int x0 = blockIdx.x * S::W;
-  const int ys = blockIdx.y * seg_rows;
-  const int ye = min(ys + seg_rows, ny);
-  const int gx_raw = x0 - K + c;
-  const bool col_live = px || (gx_raw >= 0 && gx_raw < nx);
-  const int gx = px ? ((gx_raw % nx) + nx) % nx : gx_raw;
-  const bool at_xm = !px && gx_raw == 0;
-  const bool at_xp = !px && gx_raw == nx - 1;
-  const int iters = (ye - ys) + 2 * K;
 
   // level 0 ring [L0][13][COLS], level t ring [RING][13][COLS]
   auto lvl0 = [&](int slot) { return smem + static_cast<size_t>(slot) * 13 * COLS; };
@@ -133,63 +140,73 @@ __global__ void __launch_bounds__(COLS, (K <= 2 ? 4 : (K == 3 ? 3 : (K == 4 ? 2 
            static_cast<size_t>(slot) * 13 * COLS;
   };
 
-  auto issue_row = [&](int j) {
-    if (j < iters) {
-      const int r = ys - K + j;
-      const bool live = py || (r >= 0 && r < ny);
-      if (live && col_live) {
-        const int gr = py ? ((r % ny) + ny) % ny : r;
-        const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
-        float* s = lvl0(j % S::L0) + c;
-#pragma unroll
-        for (int p = 0; p < 13; ++p) __pipeline_memcpy_async(s + p * COLS, g + p * A.plane, sizeof(float));
-      }
-    }
-    __pipeline_commit();
-  };
+  run_segment(P, ny, [&](int strip, int ys, int ye) {
+    const int gx_raw = strip * P.w - K + c;
+    const bool in_tile = c < P.w + 2 * K;
+    const bool col_live = in_tile && (px || (gx_raw >= 0 && gx_raw < nx));
+    const int gx = px ? ((gx_raw % nx) + nx) % nx : gx_raw;
+    const bool at_xm = !px && gx_raw == 0;
+    const bool at_xp = !px && gx_raw == nx - 1;
+    const int iters = (ye - ys) + 2 * K;
 
-  issue_row(0);
-  issue_row(1);
-  for (int j = 0; j < iters; ++j) {
-    issue_row(j + 2);
-    __pipeline_wait_prior(2);  // row j has landed (this thread's copies)
-    __syncthreads();           // ... and every thread's
+    auto issue_row = [&](int j) {
+      if (j < iters) {
+        const int r = ys - K + j;
+        const bool live = py || (r >= 0 && r < ny);
+        if (live && col_live) {
+          const int gr = py ? ((r % ny) + ny) % ny : r;
+          const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
+          float* s = lvl0(j % S::L0) + c;
 #pragma unroll
-    for (int t = 1; t <= K; ++t) {
-      const int R = ys - K + j - t;  // row of level t computed now
-      const bool row_ok = R >= ys - K + t && R < ye + K - t;
-      const bool row_live = py || (R >= 0 && R < ny);
-      if (row_ok && row_live && col_live && c >= t && c < COLS - t) {
-        float f[13];
-        const float *rm, *r0, *rp;
-        if (t == 1) {  // level 0 rows R - 1, R, R + 1 are iterations j - 2, j - 1, j
-          rm = lvl0((j + S::L0 - 2) % S::L0);
-          r0 = lvl0((j + S::L0 - 1) % S::L0);
-          rp = lvl0(j % S::L0);
-        } else {
-          const int base = ys - 2 * K;  // ring slot of row r: (r - base) % 3, r >= base
-          rm = ring(t - 1, (R - 1 - base) % S::RING);
-          r0 = ring(t - 1, (R - base) % S::RING);
-          rp = ring(t - 1, (R + 1 - base) % S::RING);
-        }
-        const bool at_ym = !py && R == 0, at_yp = !py && R == ny - 1;
-        pull_level<COLS>(rm, r0, rp, c, at_xm, at_xp, at_ym, at_yp, A.bc, A.inflow_feq, f);
-        float h, qx, qy;
-        collide13(f, Kc, h, qx, qy);
-        if (t < K) {
-          float* dst = ring(t, (R - (ys - 2 * K)) % S::RING) + c;
-#pragma unroll
-          for (int p = 0; p < 13; ++p) dst[p * COLS] = f[p];
-        } else if (c >= K && c < K + S::W && gx_raw < nx) {
-          float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
-#pragma unroll
-          for (int p = 0; p < 13; ++p) g[p * A.plane] = f[p];
+          for (int p = 0; p < 13; ++p) __pipeline_memcpy_async(s + p * COLS, g + p * A.plane, sizeof(float));
         }
       }
-      if (t < K) __syncthreads();
+      __pipeline_commit();
+    };
+
+    issue_row(0);
+    issue_row(1);
+    for (int j = 0; j < iters; ++j) {
+      issue_row(j + 2);
+      __pipeline_wait_prior(2);  // row j has landed (this thread's copies)
+      __syncthreads();           // ... and every thread's
+#pragma unroll
+      for (int t = 1; t <= K; ++t) {
+        const int R = ys - K + j - t;  // row of level t computed now
+        const bool row_ok = R >= ys - K + t && R < ye + K - t;
+        const bool row_live = py || (R >= 0 && R < ny);
+        if (row_ok && row_live && col_live && c >= t && c < P.w + 2 * K - t) {
+          float f[13];
+          const float *rm, *r0, *rp;
+          if (t == 1) {  // level 0 rows R - 1, R, R + 1 are iterations j - 2, j - 1, j
+            rm = lvl0((j + S::L0 - 2) % S::L0);
+            r0 = lvl0((j + S::L0 - 1) % S::L0);
+            rp = lvl0(j % S::L0);
+          } else {
+            const int base = ys - 2 * K;  // ring slot of row r: (r - base) % 3, r >= base
+            rm = ring(t - 1, (R - 1 - base) % S::RING);
+            r0 = ring(t - 1, (R - base) % S::RING);
+            rp = ring(t - 1, (R + 1 - base) % S::RING);
+          }
+          const bool at_ym = !py && R == 0, at_yp = !py && R == ny - 1;
+          pull_level<COLS>(rm, r0, rp, c, at_xm, at_xp, at_ym, at_yp, A.bc, A.inflow_feq, f);
+          float h, qx, qy;
+          collide13(f, Kc, h, qx, qy);
+          if (t < K) {
+            float* dst = ring(t, (R - (ys - 2 * K)) % S::RING) + c;
+#pragma unroll
+            for (int p = 0; p < 13; ++p) dst[p * COLS] = f[p];
+          } else if (c >= K && c < K + P.w && gx_raw < nx) {
+            float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
+#pragma unroll
+            for (int p = 0; p < 13; ++p) g[p * A.plane] = f[p];
+          }
+        }
+        if (t < K) __syncthreads();
+      }
     }
-  }
-  __pipeline_wait_prior(0);
+    __pipeline_wait_prior(0);
+  });
 }
 
 // The same wavefront on an all-periodic domain (every tile cell is a domain cell, no
@@ -198,18 +215,12 @@ __global__ void __launch_bounds__(COLS, (K <= 2 ? 4 : (K == 3 ? 3 : (K == 4 ? 2 
 // registers, so the only barrier per iteration is the one after the input row lands; the
 // next input row is issued after it, when every thread has finished the previous iteration.
 template <int K, int COLS>
-__global__ void __launch_bounds__(COLS, (K <= 4 ? 5 : 4))
-    step2d_temporal_periodic(const StepArgs<float> A, const Consts<float> Kc, int seg_rows) {
+__global__ void __launch_bounds__(COLS, COLS == 192 ? 2 : (K <= 4 ? 5 : 3))
+    step2d_temporal_periodic(const StepArgs<float> A, const Consts<float> Kc, const Partition P) {
   using S = PeriodicShape<K, COLS>;
   extern __shared__ __align__(16) float smem[];
   const int c = threadIdx.x;
   const int nx = A.nx, ny = A.ny;
-  const int x0 = blockIdx.x * S::W;
-  const int ys = blockIdx.y * seg_rows;
-  const int ye = min(ys + seg_rows, ny);
-  const int gx_raw = x0 - K + c;
-  const int gx = ((gx_raw % nx) + nx) % nx;
-  const int iters = (ye - ys) + 2 * K;
 
   // level 0: group A [A0][3][COLS], B [B0][7][COLS], C [C0][3][COLS]
   float* const l0a = smem;
@@ -218,136 +229,168 @@ __global__ void __launch_bounds__(COLS, (K <= 4 ? 5 : 4))
   // level t >= 1: x movers [2][6][COLS], planes 1, 3, 5, 7, 9, 11 in that order
   auto xm = [&](int t, int slot) { return smem + S::L0_FLOATS + (t - 1) * S::LV_FLOATS + slot * 6 * COLS; };
 
-  // Level t (1 .. K - 1) as the input of level t + 1, in the column's registers: the -y
-  // movers and f0 and +y movers of the row computed in this iteration (*_now), f0 of the
-  // previous row, the +y movers of the previous two rows.  Where a level was not computed
-  // (halo columns and rows outside its range) they hold stale values that the next level,
-  // whose range is one smaller on each side, never reads.
-  float a_now[K][3], f0_now[K], c_now[K][3], f0_prev[K], c_prev1[K][3], c_prev2[K][3];
-#pragma unroll
-  for (int t = 0; t < K; ++t) {
-    f0_now[t] = f0_prev[t] = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = 0.0f;
-  }
+  run_segment(P, ny, [&](int strip, int ys, int ye) {
+    const int gx_raw = strip * P.w - K + c;
+    const bool in_tile = c < P.w + 2 * K;
+    const int gx = ((gx_raw % nx) + nx) % nx;
+    const int iters = (ye - ys) + 2 * K;
 
-  auto issue_row = [&](int j) {
-    if (j < iters) {
-      const int r = ys - K + j;
-      const int gr = ((r % ny) + ny) % ny;
-      const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
-      float* sa = l0a + (j % S::A0) * 3 * COLS + c;
-      float* sb = l0b + (j % S::B0) * 7 * COLS + c;
-      float* sc = l0c + (j % S::C0) * 3 * COLS + c;
+    // Level t (1 .. K - 1) as the input of level t + 1, in the column's registers: the -y
+    // movers, f0 and +y movers of the row computed in this iteration (*_now), f0 of the
+    // previous row, the +y movers of the previous two rows.  Where a level was not
+    // computed (halo columns and rows outside its range) they hold stale values that the
+    // next level, whose range is one smaller on each side, never reads.
+    float a_now[K][3], f0_now[K], c_now[K][3], f0_prev[K], c_prev1[K][3], c_prev2[K][3];
 #pragma unroll
-      for (int p = 0; p < 13; ++p) {
-        float* d = plane_group(p) == 0 ? sa : (plane_group(p) == 1 ? sb : sc);
-        __pipeline_memcpy_async(d + plane_index(p) * COLS, g + p * A.plane, sizeof(float));
+    for (int t = 0; t < K; ++t) {
+      f0_now[t] = f0_prev[t] = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = 0.0f;
+    }
+
+    auto issue_row = [&](int j) {
+      if (j < iters && in_tile) {
+        const int r = ys - K + j;
+        const int gr = ((r % ny) + ny) % ny;
+        const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
+        float* sa = l0a + (j % S::A0) * 3 * COLS + c;
+        float* sb = l0b + (j % S::B0) * 7 * COLS + c;
+        float* sc = l0c + (j % S::C0) * 3 * COLS + c;
+#pragma unroll
+        for (int p = 0; p < 13; ++p) {
+          float* d = plane_group(p) == 0 ? sa : (plane_group(p) == 1 ? sb : sc);
+          __pipeline_memcpy_async(d + plane_index(p) * COLS, g + p * A.plane, sizeof(float));
+        }
+      }
+      __pipeline_commit();
+    };
+
+    issue_row(0);
+    issue_row(1);
+    for (int j = 0; j < iters; ++j) {
+      __pipeline_wait_prior(1);  // row j has landed (this thread's copies; row j + 1 may be in flight)
+      __syncthreads();           // ... and every thread's; iteration j - 1 is over everywhere
+      issue_row(j + 2);
+#pragma unroll
+      for (int t = 1; t <= K; ++t) {
+        const int R = ys - K + j - t;  // row of level t computed now
+        const bool row_ok = R >= ys - K + t && R < ye + K - t;
+        if (row_ok && c >= t && c < P.w + 2 * K - t) {
+          float f[13];
+          if (t == 1) {
+            // level 0: row R + 1 landed now (iteration j), R at j - 1, R - 1 at j - 2
+            const float* ra = l0a + (j % S::A0) * 3 * COLS + c;
+            const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 7 * COLS + c;
+            const float* rc = l0c + ((j + S::C0 - 2) % S::C0) * 3 * COLS + c;
+            f[0] = rb[0];
+#pragma unroll
+            for (int fam = 0; fam < 3; ++fam) {
+              f[1 + 4 * fam] = rb[(1 + 2 * fam) * COLS - 1];
+              f[2 + 4 * fam] = rc[fam * COLS];
+              f[3 + 4 * fam] = rb[(2 + 2 * fam) * COLS + 1];
+              f[4 + 4 * fam] = ra[fam * COLS];
+            }
+          } else {
+            const float* x = xm(t - 1, (j + 1) & 1) + c;  // level t - 1, row R (previous iteration)
+            f[0] = f0_prev[t - 1];
+#pragma unroll
+            for (int fam = 0; fam < 3; ++fam) {
+              f[1 + 4 * fam] = x[(2 * fam) * COLS - 1];
+              f[2 + 4 * fam] = c_prev2[t - 1][fam];
+              f[3 + 4 * fam] = x[(2 * fam + 1) * COLS + 1];
+              f[4 + 4 * fam] = a_now[t - 1][fam];
+            }
+          }
+          float h, qx, qy;
+          collide13(f, Kc, h, qx, qy);
+          if (t < K) {
+            float* x = xm(t, j & 1) + c;
+#pragma unroll
+            for (int fam = 0; fam < 3; ++fam) {
+              x[(2 * fam) * COLS] = f[1 + 4 * fam];
+              x[(2 * fam + 1) * COLS] = f[3 + 4 * fam];
+              a_now[t][fam] = f[4 + 4 * fam];
+              c_now[t][fam] = f[2 + 4 * fam];
+            }
+            f0_now[t] = f[0];
+          } else if (c >= K && c < K + P.w && gx_raw < nx) {
+            float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
+#pragma unroll
+            for (int p = 0; p < 13; ++p) g[p * A.plane] = f[p];
+          }
+        }
+        if (t > 1) {
+          // level t - 1 is consumed for this iteration: age its rows
+          f0_prev[t - 1] = f0_now[t - 1];
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            c_prev2[t - 1][fam] = c_prev1[t - 1][fam];
+            c_prev1[t - 1][fam] = c_now[t - 1][fam];
+          }
+        }
       }
     }
-    __pipeline_commit();
-  };
+    __pipeline_wait_prior(0);
+  });
+}
 
-  issue_row(0);
-  issue_row(1);
-  for (int j = 0; j < iters; ++j) {
-    __pipeline_wait_prior(1);  // row j has landed (this thread's copies; row j + 1 may be in flight)
-    __syncthreads();           // ... and every thread's; iteration j - 1 is over everywhere
-    issue_row(j + 2);
-#pragma unroll
-    for (int t = 1; t <= K; ++t) {
-      const int R = ys - K + j - t;  // row of level t computed now
-      const bool row_ok = R >= ys - K + t && R < ye + K - t;
-      if (row_ok && c >= t && c < COLS - t) {
-        float f[13];
-        if (t == 1) {
-          // level 0: row R + 1 landed now (iteration j), R at j - 1, R - 1 at j - 2
-          const float* ra = l0a + (j % S::A0) * 3 * COLS + c;
-          const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 7 * COLS + c;
-          const float* rc = l0c + ((j + S::C0 - 2) % S::C0) * 3 * COLS + c;
-          f[0] = rb[0];
-#pragma unroll
-          for (int fam = 0; fam < 3; ++fam) {
-            f[1 + 4 * fam] = rb[(1 + 2 * fam) * COLS - 1];
-            f[2 + 4 * fam] = rc[fam * COLS];
-            f[3 + 4 * fam] = rb[(2 + 2 * fam) * COLS + 1];
-            f[4 + 4 * fam] = ra[fam * COLS];
-          }
-        } else {
-          const float* x = xm(t - 1, (j + 1) & 1) + c;  // level t - 1, row R (previous iteration)
-          f[0] = f0_prev[t - 1];
-#pragma unroll
-          for (int fam = 0; fam < 3; ++fam) {
-            f[1 + 4 * fam] = x[(2 * fam) * COLS - 1];
-            f[2 + 4 * fam] = c_prev2[t - 1][fam];
-            f[3 + 4 * fam] = x[(2 * fam + 1) * COLS + 1];
-            f[4 + 4 * fam] = a_now[t - 1][fam];
-          }
-        }
-        float h, qx, qy;
-        collide13(f, Kc, h, qx, qy);
-        if (t < K) {
-          float* x = xm(t, j & 1) + c;
-#pragma unroll
-          for (int fam = 0; fam < 3; ++fam) {
-            x[(2 * fam) * COLS] = f[1 + 4 * fam];
-            x[(2 * fam + 1) * COLS] = f[3 + 4 * fam];
-            a_now[t][fam] = f[4 + 4 * fam];
-            c_now[t][fam] = f[2 + 4 * fam];
-          }
-          f0_now[t] = f[0];
-        } else if (c >= K && c < K + S::W && gx_raw < nx) {
-          float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
-#pragma unroll
-          for (int p = 0; p < 13; ++p) g[p * A.plane] = f[p];
-        }
-      }
-      if (t > 1) {
-        // level t - 1 is consumed for this iteration: age its rows
-        f0_prev[t - 1] = f0_now[t - 1];
-#pragma unroll
-        for (int fam = 0; fam < 3; ++fam) {
-          c_prev2[t - 1][fam] = c_prev1[t - 1][fam];
-          c_prev1[t - 1][fam] = c_now[t - 1][fam];
-        }
-      }
-    }
-  }
-  __pipeline_wait_prior(0);
+// Resident CTAs per SM of a kernel at its dynamic shared-memory size (asked once).
+inline int resident_ctas(const void* fn, int threads, size_t smem) {
+  int r = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fn, threads, smem) != cudaSuccess) return 1;
+  return std::max(r, 1);
+}
+
+// Strips of equal width <= wmax, then row segments: about `waves` waves of the resident
+// CTAs (`slots` of them), rounded down to whole segments per strip, no segment shorter
+// than 2K rows (the wavefront's fill) unless the domain is.
+inline Partition partition(int nx, int ny, int wmax, int K, int slots, int waves) {
+  Partition P;
+  P.strips = (nx + wmax - 1) / wmax;
+  P.w = (nx + P.strips - 1) / P.strips;
+  const int min_rows = std::min(2 * K, ny);
+  int seg = std::max(1, (waves * slots) / P.strips);
+  seg = std::min(seg, std::max(1, ny / min_rows));
+  P.rows_per_cta = (ny + seg - 1) / seg;
+  P.segments = (ny + P.rows_per_cta - 1) / P.rows_per_cta;
+  return P;
+}
+
+// Launch one kernel of K steps.  Column counts: 192 for the periodic kernel (its shared
+// memory allows two CTAs per SM at K = 6 .. 8), 128 for the general one (full rings).
+template <int K, bool PER>
+cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t st, int sm_count) {
+  constexpr int COLS = PER ? 192 : 128;
+  const size_t smem = (PER ? PeriodicShape<K, COLS>::floats() : TemporalShape<K, COLS>::smem_floats()) * sizeof(float);
+  const void* fn;
+  if constexpr (PER)
+    fn = reinterpret_cast<const void*>(step2d_temporal_periodic<K, COLS>);
+  else
+    fn = reinterpret_cast<const void*>(step2d_temporal<K, COLS>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  static int resident = 0;  // the same on every GPU of one model
+  if (resident == 0) resident = resident_ctas(fn, COLS, smem);
+  // one wave of the resident CTAs for the periodic kernel, two for the other
+  const Partition P = partition(a.nx, a.ny, COLS - 2 * K, K, resident * std::max(sm_count, 1), PER ? 1 : 2);
+  const int grid = P.strips * P.segments;
+  const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
+  if constexpr (PER)
+    step2d_temporal_periodic<K, COLS><<<grid, COLS, smem, st>>>(a, K_, P);
+  else
+    step2d_temporal<K, COLS><<<grid, COLS, smem, st>>>(a, K_, P);
+  return cudaGetLastError();
 }
 
 template <int K>
 cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t st, int sm_count) {
-  constexpr int COLS = 128;
-  const bool per = a.bc[0] == LBM_SW_BC_PERIODIC && a.bc[2] == LBM_SW_BC_PERIODIC;
-  const int w = per ? PeriodicShape<K, COLS>::W : TemporalShape<K, COLS>::W;
-  const size_t smem =
-      (per ? PeriodicShape<K, COLS>::floats() : TemporalShape<K, COLS>::smem_floats()) * sizeof(float);
-  cudaError_t e = per ? cudaFuncSetAttribute(step2d_temporal_periodic<K, COLS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))
-                      : cudaFuncSetAttribute(step2d_temporal<K, COLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  const int strips = (a.nx + w - 1) / w;
-  // about two waves of the resident CTAs, rows split evenly between the segments
-  const int per_sm = per ? (K <= 4 ? 5 : 4) : (K <= 2 ? 4 : (K == 3 ? 3 : (K == 4 ? 2 : 1)));
-  const int target = 2 * per_sm * sm_count;
-  int segments = std::max(1, (target + strips / 2) / std::max(strips, 1));
-  segments = std::min(segments, std::max(1, a.ny / (4 * K)));
-  segments = std::min(segments, 65535);
-  const int seg_rows = (a.ny + segments - 1) / segments;
-  segments = (a.ny + seg_rows - 1) / seg_rows;
-  const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
-  if (per)
-    step2d_temporal_periodic<K, COLS><<<dim3(strips, segments), COLS, smem, st>>>(a, K_, seg_rows);
-  else
-    step2d_temporal<K, COLS><<<dim3(strips, segments), COLS, smem, st>>>(a, K_, seg_rows);
-  return cudaGetLastError();
+  const bool per = a.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC && a.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
+  return per ? launch_k<K, true>(a, kd, st, sm_count) : launch_k<K, false>(a, kd, st, sm_count);
 }
 
 }  // namespace
 
-bool temporal_steps_supported(int k) { return k >= 2 && k <= 6; }
+bool temporal_steps_supported(int k) { return k >= 2 && k <= 8; }
 
 cudaError_t launch_step2d_temporal(const StepArgs<float>& a, const ConstsD& kd, int k, cudaStream_t st,
                                    int sm_count) {
@@ -356,6 +399,8 @@ cudaError_t launch_step2d_temporal(const StepArgs<float>& a, const ConstsD& kd, 
     case 3: return launch_k<3>(a, kd, st, sm_count);
     case 5: return launch_k<5>(a, kd, st, sm_count);
     case 6: return launch_k<6>(a, kd, st, sm_count);
+    case 7: return launch_k<7>(a, kd, st, sm_count);
+    case 8: return launch_k<8>(a, kd, st, sm_count);
     default: return launch_k<4>(a, kd, st, sm_count);
   }
 }

@@ -62,6 +62,7 @@ class lbm_sw_info(ctypes.Structure):
         ("bytes_per_update", ctypes.c_double),
         ("steps_done", ctypes.c_longlong),
         ("kernel_launches", ctypes.c_longlong),
+        ("steps_per_launch", ctypes.c_int),
     ]
 
 

@@ -61,8 +61,9 @@ def test_struct_layout_matches_c(tmp_path):
         ' printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_sw_params), offsetof(lbm_sw_params, g),\n'
         "   offsetof(lbm_sw_params, bc), offsetof(lbm_sw_params, inflow), offsetof(lbm_sw_params, stream),\n"
         "   offsetof(lbm_sw_params, kernel), offsetof(lbm_sw_params, reserved));\n"
-        ' printf("%zu %zu %zu %zu\\n", sizeof(lbm_sw_info), offsetof(lbm_sw_info, pitch),\n'
-        "   offsetof(lbm_sw_info, bytes_per_update), offsetof(lbm_sw_info, kernel_launches));\n"
+        ' printf("%zu %zu %zu %zu %zu\\n", sizeof(lbm_sw_info), offsetof(lbm_sw_info, pitch),\n'
+        "   offsetof(lbm_sw_info, bytes_per_update), offsetof(lbm_sw_info, kernel_launches),\n"
+        "   offsetof(lbm_sw_info, steps_per_launch));\n"
         " return 0; }\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -70,7 +71,8 @@ def test_struct_layout_matches_c(tmp_path):
     P, I = lbm_sw.lbm_sw_params, lbm_sw.lbm_sw_info
     py_params = [ctypes.sizeof(P), P.g.offset, P.bc.offset, P.inflow.offset, P.stream.offset, P.kernel.offset,
                  P.reserved.offset]
-    py_info = [ctypes.sizeof(I), I.pitch.offset, I.bytes_per_update.offset, I.kernel_launches.offset]
+    py_info = [ctypes.sizeof(I), I.pitch.offset, I.bytes_per_update.offset, I.kernel_launches.offset,
+               I.steps_per_launch.offset]
     assert [int(v) for v in c_params.split()] == py_params
     assert [int(v) for v in c_info.split()] == py_info
 
@@ -113,7 +115,7 @@ def _bad(**changes):
     (dict(bc=[lbm_sw.INFLOW, lbm_sw.WALL, 0, 0], inflow_h=0.0), "inflow[0]"),
     (dict(kernel=9), "kernel"),
     (dict(kernel=3), "CLUSTER is for 1D"),
-    (dict(temporal_steps=7), "temporal_steps"),
+    (dict(temporal_steps=9), "temporal_steps"),
     (dict(reserved=1), "reserved"),
 ])
 def test_create_rejects_bad_parameters_before_touching_the_gpu(lib, changes, needle):

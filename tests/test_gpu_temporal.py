@@ -1,7 +1,8 @@
-"""Temporal blocking (K = 2 .. 6 fused steps per launch through shared memory) against the
+"""Temporal blocking (K = 2 .. 8 fused steps per launch through shared memory) against the
 one-step-per-launch kernel: every cell update is the same pull + collide, so the results
-must be equal bit for bit, on ragged grids (a strip holds 120 output columns), with every
-boundary kind, for step counts that leave a remainder, and on the benchmark workload."""
+must be equal bit for bit, on ragged grids (a strip holds up to 128 - 2K output columns
+with walls, inflow or outflow and 192 - 2K on all-periodic domains), with every boundary
+kind, for step counts that leave a remainder, and on the 4096^2 dam-break."""
 
 import numpy as np
 import pytest
@@ -29,7 +30,7 @@ def _run(F0, steps, bc, kernel, k=0):
                          ids=lambda b: "".join("PWOI"[k] for k in b))
 @pytest.mark.parametrize("nx,ny", [(1, 1), (3, 2), (7, 5), (64, 9), (119, 17), (120, 3), (121, 40), (241, 33),
                                    (300, 1), (5, 300), (513, 70)])
-@pytest.mark.parametrize("k", [2, 3, 4, 5, 6])
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 6, 7, 8])
 def test_temporal_equals_single_steps(nx, ny, bc, k):
     F0 = inputs.random_populations(13, ny, nx, seed=7000 + nx * 3 + ny).astype(np.float32)
     for steps in (1, 4, 9, 13):
@@ -48,3 +49,26 @@ def test_temporal_equals_single_steps_on_the_benchmark_workload():
             sim.step(1000)
             out.append(sim.moments()[0])
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("nx,ny,bc,precision,want", [
+    (1024, 1024, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
+    (2048, 512, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
+    (1024, 1024, (W, W, W, W), lbm_sw.FP32, lbm_sw.KERNEL_VEC),
+    (1024, 1024, (P, P, P, P), lbm_sw.FP64, lbm_sw.KERNEL_VEC),
+    (512, 512, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_VEC),
+])
+def test_auto_kernel_choice(nx, ny, bc, precision, want):
+    with lbm_sw.Simulation(nx, ny, precision=precision, bc=bc, inflow=INFLOW, stream=torch_stream()) as sim:
+        assert sim.info().kernel == want
+
+
+def test_auto_temporal_counts_launches_and_steps():
+    """AUTO on a periodic 1024^2 FP32 grid: 6 steps per launch, the remainder one per launch."""
+    W0 = inputs.circular_dam_break_2d(1024, seed=inputs.stream_seed(3))
+    with lbm_sw.Simulation(1024, 1024, stream=torch_stream()) as sim:
+        sim.set_state(*W0)
+        before = sim.info().kernel_launches
+        sim.step(20)
+        info = sim.info()
+        assert info.steps_done == 20 and info.kernel_launches - before == 3 + 2

@@ -184,6 +184,20 @@ LBM_SW_API int lbm_sw_step(lbm_sw* h, int n);
  * supports BGK only.  Errors: LBM_SW_E_ARG. */
 LBM_SW_API int lbm_sw_set_relaxation(lbm_sw* h, const double* rates, int count);
 
+/* Obstacles inside a 2D domain (section 4, second test case: a forward-facing step in the
+ * channel).  solid[ny][nx] (x fastest, one byte per cell, nonzero = solid) is copied;
+ * on_device says whether it is a device pointer; the caller keeps ownership and may reuse it
+ * when the call returns.  A face between a fluid cell and a solid cell (inside the domain or
+ * across a periodic side) is a wall with the rule of a WALL side: the population that
+ * would arrive from the solid cell takes the value of the fluid cell's own reflected
+ * population, the momentum family normal to the face negated.  Solid cells hold no fluid:
+ * they are not collided or streamed and keep the populations they hold (also through
+ * lbm_sw_set_populations(PRE_COLLISION)); their moments still count in the diagnostics.
+ * With obstacles every step runs the one-thread-per-cell obstacle kernel, whatever the
+ * params' kernel.  solid == NULL removes the obstacles.  The adjoint does not support them.
+ * Errors: LBM_SW_E_ARG (1D handle), LBM_SW_E_NOMEM, LBM_SW_E_CUDA. */
+LBM_SW_API int lbm_sw_set_obstacle(lbm_sw* h, const unsigned char* solid, int on_device);
+
 /* Write the conserved moments (h = sum f, hu = sum gx, hv = sum gy; Eq.
  * 1-hyp-N-vconserv) of the current state as FP64 [ny][nx] arrays.  With host
  * arrays the call synchronises; with device arrays it is asynchronous on the stream.

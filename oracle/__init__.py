@@ -47,12 +47,14 @@ class OracleParams(ctypes.Structure):
         ("inflow", (ctypes.c_double * 3) * 4),
         ("mrt", ctypes.c_int),
         ("s_moments", ctypes.c_double * 13),
+        ("solid", ctypes.c_void_p),
     ]
 
 
 def params(nx, ny=1, *, g=1.0, lam=8.0, s=1.8, a=0.05, bc=(PERIODIC,) * 4,
-           inflow=None, s_moments=None) -> OracleParams:
-    """Build an ``OracleParams``; ``s_moments`` (13 or 5 rates) switches on MRT."""
+           inflow=None, s_moments=None, solid=None) -> OracleParams:
+    """Build an ``OracleParams``; ``s_moments`` (13 or 5 rates) switches on MRT; ``solid``
+    (2D, ``[ny][nx]``, nonzero = solid) places obstacles with mirror walls on their faces."""
     p = OracleParams()
     p.nx, p.ny = int(nx), int(ny)
     p.g, p.lam, p.s, p.a = float(g), float(lam), float(s), float(a)
@@ -69,6 +71,13 @@ def params(nx, ny=1, *, g=1.0, lam=8.0, s=1.8, a=0.05, bc=(PERIODIC,) * 4,
         p.mrt = 1
         for k, v in enumerate(s_moments):
             p.s_moments[k] = float(v)
+    p.solid = None
+    if solid is not None:
+        mask = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
+        if mask.shape != (int(ny), int(nx)):
+            raise ValueError(f"solid must have shape ({ny}, {nx})")
+        p._solid_keep = mask  # the struct holds a raw pointer: keep the array alive with it
+        p.solid = mask.ctypes.data
     return p
 
 

@@ -38,6 +38,12 @@
 //             reflected velocity, normal momentum family negated);
 //   OUTFLOW:  a copy of the boundary cell (zero gradient);
 //   INFLOW:   the equilibrium of a prescribed state W_in.
+// Obstacles (2D, optional): a mask of solid cells inside the domain.  A face between a
+// fluid cell and a solid cell is a wall with the same mirror rule: the population that
+// would arrive from the solid cell takes the value of the reflected population of the
+// fluid cell itself, normal momentum family negated (exactly what the WALL ghost gives
+// at a domain side).  Solid cells hold no fluid: they are neither collided nor streamed,
+// and keep the populations they hold.
 //
 // Templated on the scalar so that std::complex<double> gives complex-step
 // derivatives of a whole run (the scheme is analytic in its inputs).
@@ -71,6 +77,7 @@ struct oracle_params {
   double inflow[4][3];    // W_in = (h, h u, h v) per side for INFLOW
   int mrt;                // 0: BGK with s; 1: MRT with s_moments
   double s_moments[13];   // relaxation rate per moment (MRT only; conserved ones unused)
+  const unsigned char* solid;  // 2D: nx*ny flags, x fastest, nonzero = solid; NULL = none
 };
 }
 
@@ -326,6 +333,7 @@ void collide_2d(T* F, const P& pr) {
   const size_t plane = static_cast<size_t>(pr.nx) * pr.ny;
 #pragma omp parallel for schedule(static)
   for (long c = 0; c < static_cast<long>(plane); ++c) {
+    if (pr.solid && pr.solid[c]) continue;  // no fluid to relax
     T f[13];
     for (int j = 0; j < 13; ++j) f[j] = F[j * plane + c];
     collide_cell_2d(f, pr);
@@ -378,6 +386,34 @@ void stream_2d(const T* fs, T* f, const P& pr, std::vector<T>& G) {
     for (int p = 0; p < 13; ++p)
       for (int i = 0; i < nx; ++i)
         f[p * plane + static_cast<size_t>(j) * nx + i] = g(p, i - kEx2[p], j - kEy2[p]);
+
+  if (!pr.solid) return;
+  // Obstacles: solid cells keep their populations; a fluid cell whose source cell is
+  // solid takes the mirror image of its own population instead.
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const size_t c = static_cast<size_t>(j) * nx + i;
+      if (pr.solid[c]) {
+        for (int p = 0; p < 13; ++p) f[p * plane + c] = fs[p * plane + c];
+        continue;
+      }
+      for (int p = 1; p < 13; ++p) {
+        int si = i - kEx2[p], sj = j - kEy2[p];
+        // beyond a periodic side the source is the cell on the opposite side; beyond any
+        // other side the side's own rule above applies
+        if (si < 0 || si >= nx) {
+          if (pr.bc[si < 0 ? SIDE_XM : SIDE_XP] != BC_PERIODIC) continue;
+          si = (si + nx) % nx;
+        }
+        if (sj < 0 || sj >= ny) {
+          if (pr.bc[sj < 0 ? SIDE_YM : SIDE_YP] != BC_PERIODIC) continue;
+          sj = (sj + ny) % ny;
+        }
+        if (!pr.solid[static_cast<size_t>(sj) * nx + si]) continue;
+        f[p * plane + c] = kEx2[p] != 0 ? kSignX[p] * g(kMirrorX[p], i, j) : kSignY[p] * g(kMirrorY[p], i, j);
+      }
+    }
 }
 
 template <class T>

@@ -473,6 +473,10 @@ int lbm_sw_tape_create(lbm_sw* h, int steps, int interval, lbm_sw_tape** out) {
     h->err = "tape_create: the adjoint supports the BGK relaxation only (lbm_sw_set_relaxation(h, NULL, 0))";
     return LBM_SW_E_ARG;
   }
+  if (h->has_obstacles) {
+    h->err = "tape_create: the adjoint does not support obstacles (lbm_sw_set_obstacle(h, NULL, 0))";
+    return LBM_SW_E_ARG;
+  }
   if (steps < 1 || interval < 0 || interval > steps) {
     h->err = "tape_create: need steps >= 1 and 0 <= interval <= steps";
     return LBM_SW_E_ARG;
@@ -507,6 +511,8 @@ int lbm_sw_forward_record(lbm_sw* h, lbm_sw_tape* t) {
   if (!h || !t) return LBM_SW_E_ARG;
   if (t->owner != h) return tfail(t, LBM_SW_E_ARG, "forward_record: tape belongs to another handle");
   if (!h->has_state) return tfail(t, LBM_SW_E_STATE, "forward_record: the handle has no state");
+  if (h->mrt || h->has_obstacles)
+    return tfail(t, LBM_SW_E_ARG, "forward_record: the adjoint supports BGK without obstacles only");
   for (int k = 0; k < t->steps; ++k) {
     if (k % t->interval == 0) {
       double* dst = t->ckpt + static_cast<size_t>(k / t->interval) * t->state_elems;

@@ -50,6 +50,9 @@ lbm::ConstsD consts(const lbm_sw* h) { return lbm::handle_consts(h); }
 // takes single steps with the VEC kernel).
 cudaError_t launch_one_step(lbm_sw* h, int from, cudaStream_t st) {
   const int variant = h->kernel == LBM_SW_KERNEL_TEMPORAL ? LBM_SW_KERNEL_VEC : h->kernel;
+  if (h->has_obstacles)
+    return h->p.precision == LBM_SW_FP64 ? lbm::launch_step2d_obstacle<double>(args<double>(h, from), consts(h), h->solid, st)
+                                         : lbm::launch_step2d_obstacle<float>(args<float>(h, from), consts(h), h->solid, st);
   if (h->p.precision == LBM_SW_FP64) {
     auto a = args<double>(h, from);
     return h->p.dim == 1 ? lbm::launch_step1d<double>(a, consts(h), st)
@@ -178,6 +181,7 @@ void lbm_sw_destroy(lbm_sw* h) {
   if (h->diag_partials) cudaFree(h->diag_partials);
   if (h->diag_out) cudaFree(h->diag_out);
   if (h->diag_host) cudaFreeHost(h->diag_host);
+  if (h->solid) cudaFree(h->solid);
   delete h;
 }
 
@@ -302,7 +306,8 @@ int lbm_sw_step(lbm_sw* h, int n) {
       return LBM_SW_OK;
     }
   }
-  if (h->p.dim == 2 && h->kernel == LBM_SW_KERNEL_TEMPORAL && h->p.precision == LBM_SW_FP32 && !h->mrt) {
+  if (h->p.dim == 2 && h->kernel == LBM_SW_KERNEL_TEMPORAL && h->p.precision == LBM_SW_FP32 && !h->mrt &&
+      !h->has_obstacles) {
     const int K = h->temporal_k;
     while (n >= K) {
       cudaError_t e = lbm::launch_step2d_temporal(args<float>(h, h->cur), consts(h), K, h->stream, h->sm_count);
@@ -442,10 +447,12 @@ int lbm_sw_set_populations(lbm_sw* h, const void* src, int on_device, int form) 
     cudaError_t e;
     if (h->p.precision == LBM_SW_FP64)
       e = h->p.dim == 1 ? lbm::launch_collide1d_dense<double>(args<double>(h, from), consts(h), static_cast<const double*>(dense), h->stream)
-                        : lbm::launch_collide2d_dense<double>(args<double>(h, from), consts(h), static_cast<const double*>(dense), h->stream);
+                        : lbm::launch_collide2d_dense<double>(args<double>(h, from), consts(h), static_cast<const double*>(dense),
+                                                              h->has_obstacles ? h->solid : nullptr, h->stream);
     else
       e = h->p.dim == 1 ? lbm::launch_collide1d_dense<float>(args<float>(h, from), consts(h), static_cast<const float*>(dense), h->stream)
-                        : lbm::launch_collide2d_dense<float>(args<float>(h, from), consts(h), static_cast<const float*>(dense), h->stream);
+                        : lbm::launch_collide2d_dense<float>(args<float>(h, from), consts(h), static_cast<const float*>(dense),
+                                                             h->has_obstacles ? h->solid : nullptr, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "collide kernel launch");
     h->launches += 1;
   }
@@ -482,6 +489,29 @@ int lbm_sw_set_relaxation(lbm_sw* h, const double* rates, int count) {
   return LBM_SW_OK;
 }
 
+int lbm_sw_set_obstacle(lbm_sw* h, const unsigned char* solid, int on_device) {
+  if (!h) return LBM_SW_E_ARG;
+  if (h->p.dim != 2) return fail(h, LBM_SW_E_ARG, "set_obstacle: obstacles are for 2D handles");
+  if (!solid) {
+    h->has_obstacles = false;
+  } else {
+    const size_t n = static_cast<size_t>(h->p.nx) * h->p.ny;
+    if (!h->solid) LBM_CUDA(h, cudaMalloc(&h->solid, n), "cudaMalloc (obstacle mask)");
+    LBM_CUDA(h, cudaMemcpyAsync(h->solid, solid, n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                h->stream), "obstacle mask copy");
+    // the caller may reuse its buffer when this returns
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "set_obstacle synchronize");
+    h->has_obstacles = true;
+  }
+  // the captured graphs hold the previous step kernel
+  for (int i = 0; i < 2; ++i)
+    if (h->graph[i]) {
+      cudaGraphExecDestroy(h->graph[i]);
+      h->graph[i] = nullptr;
+    }
+  return LBM_SW_OK;
+}
+
 int lbm_sw_synchronize(lbm_sw* h) {
   if (!h) return LBM_SW_E_ARG;
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
@@ -504,7 +534,7 @@ int lbm_sw_get_info(const lbm_sw* h, lbm_sw_info* out) {
   out->kernel_launches = h->launches;
   out->steps_per_launch = 1;
   if (out->kernel == LBM_SW_KERNEL_CLUSTER) out->steps_per_launch = 0;
-  if (h->kernel == LBM_SW_KERNEL_TEMPORAL && h->p.precision == LBM_SW_FP32 && !h->mrt)
+  if (h->kernel == LBM_SW_KERNEL_TEMPORAL && h->p.precision == LBM_SW_FP32 && !h->mrt && !h->has_obstacles)
     out->steps_per_launch = h->temporal_k;
   return LBM_SW_OK;
 }

@@ -38,7 +38,12 @@ template <class T>
 cudaError_t launch_init2d(const StepArgs<T>& a, const ConstsD& k, const double* h, const double* hu,
                           const double* hv, cudaStream_t st);
 template <class T>
-cudaError_t launch_collide2d_dense(const StepArgs<T>& a, const ConstsD& k, const T* dense, cudaStream_t st);
+cudaError_t launch_collide2d_dense(const StepArgs<T>& a, const ConstsD& k, const T* dense,
+                                  const unsigned char* solid, cudaStream_t st);
+// one step with obstacles (solid: [ny][nx] device mask, nonzero = solid)
+template <class T>
+cudaError_t launch_step2d_obstacle(const StepArgs<T>& a, const ConstsD& k, const unsigned char* solid,
+                                   cudaStream_t st);
 template <class T>
 cudaError_t launch_moments2d(const StepArgs<T>& a, double* h, double* hu, double* hv, cudaStream_t st);
 template <class T>
@@ -116,6 +121,8 @@ struct lbm_sw {
   int sm_count = 152;
   bool mrt = false;          // set by lbm_sw_set_relaxation
   double mrt_rates[10] = {};
+  unsigned char* solid = nullptr;  // obstacle mask [ny][nx] on the device (lbm_sw_set_obstacle)
+  bool has_obstacles = false;
   int graph_chunk = 64;
   bool has_state = false;
   long long steps_done = 0;

@@ -87,6 +87,51 @@ __global__ void __launch_bounds__(256) step2d_simple(const StepArgs<T> A, const 
 }
 
 // --------------------------------------------------------------------------
+// Obstacles: the SIMPLE step with a mask of solid cells ([ny][nx], nonzero = solid).  A
+// population whose source cell is solid (inside the domain, or across a periodic side) is
+// replaced by the mirror image of the cell's own population, the momentum family normal
+// to the face negated: the WALL rule of a domain side applied at the fluid-solid face.
+// Solid cells hold no fluid and keep their populations (copied to the new buffer).
+// --------------------------------------------------------------------------
+template <class T, bool MRT>
+__global__ void __launch_bounds__(256)
+    step2d_obstacle(const StepArgs<T> A, const Consts<T> K, const unsigned char* __restrict__ solid) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < A.ny; y += gridDim.y * blockDim.y) {
+    if (x >= A.nx) continue;
+    const long long cell = static_cast<long long>(y) * A.pitch + x;
+    if (solid[static_cast<long long>(y) * A.nx + x]) {
+#pragma unroll
+      for (int p = 0; p < 13; ++p) A.dst[p * A.plane + cell] = A.src[p * A.plane + cell];
+      continue;
+    }
+    T f[13];
+#pragma unroll
+    for (int p = 0; p < 13; ++p) {
+      int xs = x - ex_of(p), ys = y - ey_of(p);
+      const bool wrap_x = (xs < 0 || xs >= A.nx) && A.bc[xs < 0 ? LBM_SW_SIDE_XM : LBM_SW_SIDE_XP] == LBM_SW_BC_PERIODIC;
+      const bool wrap_y = (ys < 0 || ys >= A.ny) && A.bc[ys < 0 ? LBM_SW_SIDE_YM : LBM_SW_SIDE_YP] == LBM_SW_BC_PERIODIC;
+      if (wrap_x) xs = (xs + A.nx) % A.nx;
+      if (wrap_y) ys = (ys + A.ny) % A.ny;
+      const bool inside = xs >= 0 && xs < A.nx && ys >= 0 && ys < A.ny;
+      if (p > 0 && inside && solid[static_cast<long long>(ys) * A.nx + xs]) {
+        const bool xface = ex_of(p) != 0;
+        const int m = xface ? mirror_x(p) : mirror_y(p);
+        const bool normal = xface ? (p >= 5 && p <= 8) : (p >= 9);
+        const T v = A.src[m * A.plane + cell];
+        f[p] = normal ? -v : v;
+      } else {
+        f[p] = pull_one(A, p, x, y);
+      }
+    }
+    T h, qx, qy;
+    collide13_any<T, MRT>(f, K, h, qx, qy);
+#pragma unroll
+    for (int p = 0; p < 13; ++p) A.dst[p * A.plane + cell] = f[p];
+  }
+}
+
+// --------------------------------------------------------------------------
 // VEC variant (row body in step2d_vec.cuh): each thread owns V consecutive cells of one row (one 16-byte
 // vector per plane: 4 FP32 or 2 FP64 values), a warp owns 32 V cells of a row.
 // All 13 loads are aligned vectors: the y-moving families read whole vectors of
@@ -132,8 +177,11 @@ __global__ void init2d(const StepArgs<T> A, const Consts<T> K, const double* __r
   }
 }
 
+// Collide dense pre-collision populations into the pitched buffer; solid cells (when a
+// mask is given) are stored as they are.
 template <class T, bool MRT>
-__global__ void collide2d_dense(const StepArgs<T> A, const Consts<T> K, const T* __restrict__ dense) {
+__global__ void collide2d_dense(const StepArgs<T> A, const Consts<T> K, const T* __restrict__ dense,
+                                const unsigned char* __restrict__ solid) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const long long n = static_cast<long long>(A.nx) * A.ny;
   for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < A.ny; y += gridDim.y * blockDim.y) {
@@ -143,7 +191,7 @@ __global__ void collide2d_dense(const StepArgs<T> A, const Consts<T> K, const T*
 #pragma unroll
     for (int p = 0; p < 13; ++p) f[p] = dense[p * n + c];
     T h, qx, qy;
-    collide13_any<T, MRT>(f, K, h, qx, qy);
+    if (!(solid && solid[c])) collide13_any<T, MRT>(f, K, h, qx, qy);
 #pragma unroll
     for (int p = 0; p < 13; ++p) A.dst[p * A.plane + y * A.pitch + x] = f[p];
   }
@@ -245,6 +293,18 @@ cudaError_t launch_step2d(const StepArgs<T>& a, const ConstsD& kd, int variant, 
 }
 
 template <class T>
+cudaError_t launch_step2d_obstacle(const StepArgs<T>& a, const ConstsD& kd, const unsigned char* solid,
+                                   cudaStream_t st) {
+  const Consts<T> K = to_consts<T>(kd);
+  const dim3 block(32, 8);
+  if (kd.mrt)
+    step2d_obstacle<T, true><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, K, solid);
+  else
+    step2d_obstacle<T, false><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, K, solid);
+  return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t launch_step2d_store_w(const StepArgs<T>& a, const ConstsD& kd, T* w_out, cudaStream_t st) {
   const Consts<T> K = make_consts<T>(kd.g, kd.lambda, kd.s, kd.a);
   constexpr int BY = 4;
@@ -284,12 +344,13 @@ cudaError_t launch_init2d(const StepArgs<T>& a, const ConstsD& kd, const double*
 }
 
 template <class T>
-cudaError_t launch_collide2d_dense(const StepArgs<T>& a, const ConstsD& kd, const T* dense, cudaStream_t st) {
+cudaError_t launch_collide2d_dense(const StepArgs<T>& a, const ConstsD& kd, const T* dense,
+                                  const unsigned char* solid, cudaStream_t st) {
   const dim3 block(128, 2);
   if (kd.mrt)
-    collide2d_dense<T, true><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, to_consts<T>(kd), dense);
+    collide2d_dense<T, true><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, to_consts<T>(kd), dense, solid);
   else
-    collide2d_dense<T, false><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, to_consts<T>(kd), dense);
+    collide2d_dense<T, false><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, to_consts<T>(kd), dense, solid);
   return cudaGetLastError();
 }
 
@@ -316,7 +377,10 @@ cudaError_t launch_inflow_feq2d(T* out, const int bc[4], const double inflow[4][
   template cudaError_t launch_step2d<T>(const StepArgs<T>&, const ConstsD&, int, cudaStream_t);            \
   template cudaError_t launch_init2d<T>(const StepArgs<T>&, const ConstsD&, const double*, const double*,  \
                                         const double*, cudaStream_t);                                      \
-  template cudaError_t launch_collide2d_dense<T>(const StepArgs<T>&, const ConstsD&, const T*, cudaStream_t); \
+  template cudaError_t launch_collide2d_dense<T>(const StepArgs<T>&, const ConstsD&, const T*,              \
+                                                const unsigned char*, cudaStream_t);                        \
+  template cudaError_t launch_step2d_obstacle<T>(const StepArgs<T>&, const ConstsD&, const unsigned char*, \
+                                                 cudaStream_t);                                             \
   template cudaError_t launch_moments2d<T>(const StepArgs<T>&, double*, double*, double*, cudaStream_t);   \
   template cudaError_t launch_inflow_feq2d<T>(T*, const int[4], const double[4][3], const ConstsD&, cudaStream_t); \
   template cudaError_t launch_step2d_store_w<T>(const StepArgs<T>&, const ConstsD&, T*, cudaStream_t);       \

@@ -7,6 +7,10 @@
 * Section 4, first test case: the stationary reflection of an oblique shock by a wall,
   with the three states printed in the paper, on the 35 x 20, 70 x 40 and 140 x 80 meshes,
   run to a steady state and compared with the exact piecewise-constant solution.
+* Section 4, second test case: Emery's forward-facing step, a flow at Froude number 3 in a
+  channel of height 1 meeting a step of height 0.2 at x = 0.6, on the paper's meshes
+  120 x 40, 240 x 80 and 480 x 120 with lambda = 80, a = 0.05, s = 1.8, at t = 1/2 and 4
+  (the paper shows density maps only; no exact solution).
 
 Every lattice Boltzmann step runs in the CUDA library through lbm_sw; this module only
 sets up inputs, drives the runs and evaluates the exact solutions (which are not part of
@@ -170,6 +174,27 @@ def oblique_shock_reflection(nx: int = 140, ny: int = 80, lam: float = 8.0, a: f
             "l1_h": float(np.abs(h - he).mean()), "reflected_angle": reflected_shock_angle()}
 
 
+def emery_step(nx: int = 120, ny: int = 40, t_end: float = 0.5, lam: float = 80.0, a: float = 0.05,
+               s: float = 1.8, froude: float = 3.0, precision: int = lbm_sw.FP64, stream=None):
+    """Section 4 forward-facing step: channel [0, nx/ny] x [0, 1] (square cells of side
+    1/ny), inflow of (h, u, v) = (1, froude, 0) on x-, outflow on x+, walls on y-+ and on the
+    faces of the step (solid cells, inputs.emery_step); started filled with the inflow
+    state; t_end = steps dt, dt = 1/(ny lam)."""
+    solid, W0, win = inputs.emery_step(nx, ny, froude=froude)
+    steps = int(round(t_end * ny * lam))
+    with lbm_sw.Simulation(nx, ny, precision=precision, lam=lam, a=a, s=s,
+                           bc=(lbm_sw.INFLOW, lbm_sw.OUTFLOW, lbm_sw.WALL, lbm_sw.WALL),
+                           inflow=[win, None, None, None], stream=stream) as sim:
+        sim.set_obstacle(solid)
+        sim.set_state(*W0)
+        sim.step(steps)
+        h, hu, hv = sim.moments()
+    fluid = solid == 0
+    return {"x": (np.arange(nx) + 0.5) / ny, "y": (np.arange(ny) + 0.5) / ny, "h": h, "hu": hu, "hv": hv,
+            "solid": solid, "steps": steps, "t": steps / (ny * lam), "inflow": win,
+            "min_h": float(h[fluid].min()), "max_h": float(h[fluid].max())}
+
+
 # ----------------------------------------------------------------- output
 def _write_csv(path, header, rows):
     with open(path, "w", newline="") as fh:
@@ -193,6 +218,14 @@ def main():
         _write_csv(os.path.join(args.out, f"figure2_shock_reflection_{nx}x{ny}.csv"), ["x", "y", "h", "h_exact"], rows)
         print(f"shock reflection {nx}x{ny}: {e['steps']} steps, residual {e['residuals'][-1][1]:.2e}, "
               f"L1(h) = {e['l1_h']:.4e}")
+    for nx, ny in ((120, 40), (240, 80), (480, 120)):
+        for t_end in (0.5, 4.0):
+            e = emery_step(nx, ny, t_end)
+            rows = [(e["x"][i], e["y"][j], int(e["solid"][j, i]), e["h"][j, i]) for j in range(ny) for i in range(nx)]
+            _write_csv(os.path.join(args.out, f"figure{3 if t_end < 1 else 4}_emery_{nx}x{ny}_t{t_end:g}.csv"),
+                       ["x", "y", "solid", "h"], rows)
+            print(f"Emery step {nx}x{ny}, t = {e['t']:g} ({e['steps']} steps): h in [{e['min_h']:.4f}, "
+                  f"{e['max_h']:.4f}]")
 
 
 if __name__ == "__main__":

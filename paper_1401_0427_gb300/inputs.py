@@ -148,3 +148,26 @@ def random_states(n: int, seed: int, h=(0.5, 3.0), speed: float = 0.6):
     r = uniform(seed, 3 * n).reshape(3, n)
     hh = h[0] + (h[1] - h[0]) * r[0]
     return hh, hh * speed * (2 * r[1] - 1), hh * speed * (2 * r[2] - 1)
+
+
+def random_obstacles(ny: int, nx: int, seed: int, fraction: float = 0.15) -> np.ndarray:
+    """Solid-cell mask ``[ny][nx]`` (uint8, 1 = solid): each cell solid with probability
+    ``fraction``."""
+    return (uniform(seed, ny * nx).reshape(ny, nx) < fraction).astype(np.uint8)
+
+
+def emery_step(nx: int, ny: int, froude: float = 3.0, h0: float = 1.0, g: float = 1.0,
+               step_x: float = 0.6, step_h: float = 0.2):
+    """Forward-facing step in a channel of height 1 and length nx / ny (cells of side 1 / ny):
+    the step's front face stands at x = step_x and it fills [step_x, nx / ny] x [0, step_h]
+    (cells whose centre lies there are solid).  The channel starts filled with the inflow
+    state: depth h0, velocity froude sqrt(g h0) along x.
+
+    Returns (solid, (h, hu, hv), inflow_state)."""
+    xc = (np.arange(nx, dtype=np.float64) + 0.5) / ny
+    yc = (np.arange(ny, dtype=np.float64) + 0.5) / ny
+    X, Y = np.meshgrid(xc, yc)
+    solid = ((X > step_x) & (Y < step_h)).astype(np.uint8)
+    u = froude * math.sqrt(g * h0)
+    h = np.full((ny, nx), h0)
+    return solid, (h, h * u, np.zeros((ny, nx))), (h0, h0 * u, 0.0)

@@ -120,6 +120,7 @@ SIGNATURES = {
     "lbm_sw_set_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lbm_sw_step": (ctypes.c_int, [_H, ctypes.c_int]),
     "lbm_sw_set_relaxation": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "lbm_sw_set_obstacle": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
     "lbm_sw_get_moments": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lbm_sw_diagnostics": (ctypes.c_int, [_H, _DP]),
     "lbm_sw_get_populations": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
@@ -222,6 +223,11 @@ def lbm_sw_set_relaxation(h: int, rates=None) -> None:
         return
     arr = (ctypes.c_double * len(rates))(*[float(r) for r in rates])
     _check(load().lbm_sw_set_relaxation(h, arr, len(rates)), h, "lbm_sw_set_relaxation")
+
+
+def lbm_sw_set_obstacle(h: int, solid: int | None, on_device: bool) -> None:
+    """Solid-cell mask ([ny][nx] bytes, nonzero = solid) at address ``solid``, or None."""
+    _check(load().lbm_sw_set_obstacle(h, solid, int(on_device)), h, "lbm_sw_set_obstacle")
 
 
 def lbm_sw_get_moments(h: int, depth: int, hu: int, hv: int | None, on_device: bool) -> None:
@@ -453,6 +459,19 @@ class Simulation:
 
     def set_relaxation(self, rates=None):
         lbm_sw_set_relaxation(self.handle, rates)
+
+    def set_obstacle(self, solid=None):
+        """Solid cells: a [ny][nx] array (numpy, or a uint8 CUDA tensor), nonzero = solid;
+        None removes the obstacles."""
+        if solid is None:
+            lbm_sw_set_obstacle(self.handle, None, False)
+            return
+        dev = self._on_device(solid)
+        if not dev:
+            solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
+        if tuple(solid.shape) != (self.ny, self.nx):
+            raise ValueError(f"solid must have shape ({self.ny}, {self.nx})")
+        lbm_sw_set_obstacle(self.handle, _ptr(solid, dev), dev)
 
     def moments(self):
         h = np.empty((self.ny, self.nx))

@@ -28,8 +28,8 @@ def torch_stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-def oracle_params(nx, ny, dim, bc, inflow, a, lam=8.0, s=1.8):
-    return oracle.params(nx, ny, a=a, lam=lam, s=s, bc=bc, inflow=inflow)
+def oracle_params(nx, ny, dim, bc, inflow, a, lam=8.0, s=1.8, solid=None):
+    return oracle.params(nx, ny, a=a, lam=lam, s=s, bc=bc, inflow=inflow, solid=solid)
 
 
 def oracle_post(F0: np.ndarray, steps: int, p, dim: int) -> np.ndarray:
@@ -40,12 +40,14 @@ def oracle_post(F0: np.ndarray, steps: int, p, dim: int) -> np.ndarray:
 
 
 def gpu_post(F0: np.ndarray, steps: int, *, dim: int, precision: int, bc, inflow, a, kernel=lbm_sw.KERNEL_AUTO,
-             lam=8.0, s=1.8, graph_chunk=0, mrt_rates=None) -> np.ndarray:
+             lam=8.0, s=1.8, graph_chunk=0, mrt_rates=None, solid=None) -> np.ndarray:
     q, ny, nx = F0.shape
     with lbm_sw.Simulation(nx, ny, dim=dim, precision=precision, bc=bc, inflow=inflow, a=a, lam=lam, s=s,
                            kernel=kernel, stream=torch_stream(), graph_chunk=graph_chunk) as sim:
         if mrt_rates is not None:
             sim.set_relaxation(mrt_rates)
+        if solid is not None:
+            sim.set_obstacle(solid)
         sim.set_populations(F0, form=lbm_sw.PRE_COLLISION)
         sim.step(steps)
         return sim.populations().astype(np.float64)

@@ -5,8 +5,9 @@ inside radius 0.2 of the centre of the unit square, 1 outside, at rest, plus a s
 uniform perturbation of +-1e-3), D2Q5Q4Q4 with lambda = 8, s = 1.8, a = 0.05, g = 1,
 FP32 populations.  One bench step is one time step of the scheme over the whole grid
 (pull streaming, boundaries, moments, equilibria, relaxation), run by the library's
-default kernel for this workload: temporal blocking, 6 time steps per launch of one
-fused kernel (results bit-identical to one step per launch).  The two 872 MB population
+default kernel for this workload: temporal blocking, 4 time steps per launch of one
+fused kernel that updates two cells per thread with paired FP32 instructions (results
+bit-identical to one step per launch).  The two 872 MB population
 buffers exceed the 129 MB L2, so every launch streams the state from HBM and back.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -42,19 +43,26 @@ WORKLOAD = ("2D circular dam-break 4096x4096 periodic, D2Q5Q4Q4 (13 populations)
 JOB_STEPS = 1000  # steps of the workload as one job (the end-to-end unit)
 REF_SAMPLE = 512   # side of the periodic window the CPU oracle advances per reference step
 
-# Timed kernel by (variant, dtype); {k} is the steps per launch.
-KERNEL_NAMES = {(4, "f32"): "step2d_temporal_periodic<{k}, 192>", (2, "f32"): "step2d_vec<float>",
-                (2, "f64"): "step2d_vec<double>"}
+# One-step kernels by (variant, dtype).
+KERNEL_NAMES = {(2, "f32"): "step2d_vec<float>", (2, "f64"): "step2d_vec<double>"}
+
+
+def temporal_kernel_name(k: int) -> str:
+    """The periodic temporal kernel the library launches for an even-width grid."""
+    if k % 2:
+        return f"step2d_temporal_periodic<{k}, 192>"
+    return f"step2d_temporal_periodic_x2<{k}, 256, 2>" if k <= 4 else f"step2d_temporal_periodic_x2<{k}, 192, 1>"
+
 
 # DRAM traffic per launch of each timed kernel on the 4096^2 workload from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel name, valid only for the
 # kernel sources it was taken on.
 NCU_TRAFFIC = {
-    "step2d_temporal_periodic<6, 192>": {
-        "src_sha256": "9e98045b1638fab7d3cd7da022a09d69dc628d1db84baca1022f505399704682",
-        "sources": ("temporal.cu", "scheme.cuh"), "bytes_per_launch": 1733.67e6,
-        "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of the 5 launches of "
-                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 911.13 MB read + 822.53 MB "
+    "step2d_temporal_periodic_x2<4, 256, 2>": {
+        "src_sha256": "d83a395a8a08a24044b820d24ef91f90b31a412059a20c80c8bd7cb14126f151",
+        "sources": ("temporal.cu", "scheme.cuh"), "bytes_per_launch": 1730.49e6,
+        "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of the 6 launches of "
+                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 907.27 MB read + 823.22 MB "
                 "written per launch (mean)"},
 }
 
@@ -258,9 +266,7 @@ def run_ours(args, world, rank, local):
     sim.set_state(*W0)
     info = sim.info()
     unit = max(1, info.steps_per_launch)  # steps per launch of the step kernel
-    kname = KERNEL_NAMES[(info.kernel if unit > 1 else lbm_sw.KERNEL_VEC, dt_name)]
-    if unit > 1:
-        kname = kname.format(k=unit)
+    kname = temporal_kernel_name(unit) if unit > 1 else KERNEL_NAMES[(lbm_sw.KERNEL_VEC, dt_name)]
     # The timed region is exactly --steps time steps: full launches of `unit` steps, then
     # the remainder (one step per launch, bit-identical results).
     nfull, rem = divmod(args.steps, unit)
@@ -370,8 +376,8 @@ def variants(args, W0, stream, lbm_sw, torch):
         bpl = BYTES_PER_LUP["f64" if name == "fp64" else "f32"]
         spl = max(1, info.steps_per_launch)
         out[name] = {"MLUPS": N * N / (ms * 1e-3) / 1e6, "ms_per_step": ms, "steps_per_launch": spl,
-                     "kernel": KERNEL_NAMES[(info.kernel if spl > 1 else lbm_sw.KERNEL_VEC,
-                                             "f64" if name == "fp64" else "f32")].format(k=spl),
+                     "kernel": temporal_kernel_name(spl) if spl > 1
+                     else KERNEL_NAMES[(lbm_sw.KERNEL_VEC, "f64" if name == "fp64" else "f32")],
                      "HBM_GB_per_s": bpl * N * N / spl / (ms * 1e-3) / 1e9,
                      "frac_of_hbm_peak": bpl * N * N / spl / (ms * 1e-3) / 1e9 / peak}
     out["_l1"] = {"relative_l1_h": float(np.abs(hs["fp32"] - hs["fp64"]).sum() / np.abs(hs["fp64"]).sum()),

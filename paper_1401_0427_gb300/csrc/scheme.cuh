@@ -46,6 +46,7 @@ struct Consts {
   T c;       // 1 / (2 lambda)
   T half_g;  // g / 2
   T inv4g;   // 1 / (4 g)
+  T nz;      // -0, a value the compiler cannot see (products of the paired path, below)
   // Rates of the non-conserved moments for the MRT collision (Eq. 2-relaxation with
   // distinct s_l), in the order of the paper's moment bases:
   //   2D: J_x, J_y, eps, XX_rho | f_xx, f_xy, XX_u | f_yx, f_yy, XX_v   (r[0..9])
@@ -61,6 +62,7 @@ __host__ Consts<T> make_consts(double g, double lambda, double s, double a) {
   k.c = static_cast<T>(1.0 / (2.0 * lambda));
   k.half_g = static_cast<T>(g / 2.0);
   k.inv4g = static_cast<T>(1.0 / (4.0 * g));
+  k.nz = static_cast<T>(-0.0);
   for (int i = 0; i < 10; ++i) k.r[i] = k.s;
   return k;
 }
@@ -184,6 +186,83 @@ __device__ __forceinline__ void collide13_any(T f[13], const Consts<T>& k, T& h,
     collide13_mrt(f, k, h, qx, qy);
   else
     collide13(f, k, h, qx, qy);
+}
+
+// ---- Two FP32 cells at once (the paired FP32 instructions of sm_100 and later) ----
+// The same operations as collide13, in the same order, on (cell a, cell b) pairs, so each
+// lane rounds exactly like the scalar code and the results are equal bit for bit.  The code
+// generator contracts a paired multiply feeding a paired add into one fused multiply-add
+// even when both carry an explicit rounding mode, which would change the rounding (and
+// break the mirror symmetry of u u + v v).  So every paired product is formed as
+// fma(a, b, nz) with nz = -0 read from the kernel's constants: exactly the rounded product
+// a b (also for a zero product of either sign), in one instruction, and not a product
+// the code generator can merge into the add that follows.
+__device__ __forceinline__ unsigned long long pack2(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
+  return unpack2(r);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
+  return unpack2(r);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)), "l"(pack2(c)));
+  return unpack2(r);
+}
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ void collide13x2(float2 f[13], const Consts<float>& k) {
+  const float2 nz = dup2(k.nz);
+  auto mul2 = [&](float2 a, float2 b) { return fma2(a, b, nz); };  // the rounded product a b
+  const float2 h = add2(f[0], add2(add2(f[1], f[3]), add2(f[2], f[4])));
+  const float2 qx = add2(add2(f[5], f[7]), add2(f[6], f[8]));
+  const float2 qy = add2(add2(f[9], f[11]), add2(f[10], f[12]));
+  const float2 rh = make_float2(recip(h.x), recip(h.y));
+  const float2 u = mul2(qx, rh);
+  const float2 v = mul2(qy, rh);
+  const float2 uu = add2(mul2(u, u), mul2(v, v));
+  const float2 kap = fma2(make_float2(-uu.x, -uu.y), dup2(k.inv4g), mul2(dup2(0.5f), h));
+  const float2 f0 = mul2(dup2(k.a), kap);
+  const float2 r = mul2(sub2(h, f0), dup2(0.25f));
+  const float2 p = mul2(mul2(dup2(k.half_g), h), h);
+  const float2 c = dup2(k.c);
+  const float2 ax = mul2(qx, c);
+  const float2 ay = mul2(qy, c);
+  const float2 x4 = mul2(qx, dup2(0.25f));
+  const float2 y4 = mul2(qy, dup2(0.25f));
+  const float2 pxx = mul2(fma2(qx, u, p), c);
+  const float2 pyy = mul2(fma2(qy, v, p), c);
+  const float2 pxy = mul2(mul2(mul2(qx, qy), rh), c);
+  float2 e[13];
+  e[0] = f0;
+  e[1] = add2(r, ax);
+  e[2] = add2(r, ay);
+  e[3] = sub2(r, ax);
+  e[4] = sub2(r, ay);
+  e[5] = add2(x4, pxx);
+  e[6] = add2(x4, pxy);
+  e[7] = sub2(x4, pxx);
+  e[8] = sub2(x4, pxy);
+  e[9] = add2(y4, pxy);
+  e[10] = add2(y4, pyy);
+  e[11] = sub2(y4, pxy);
+  e[12] = sub2(y4, pyy);
+  const float2 s = dup2(k.s);
+#pragma unroll
+  for (int j = 0; j < 13; ++j) f[j] = fma2(s, sub2(e[j], f[j]), f[j]);
 }
 
 // ---- 1D: populations f0, f+, f-, g+, g- ----

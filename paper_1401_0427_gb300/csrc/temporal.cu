@@ -334,6 +334,142 @@ __global__ void __launch_bounds__(COLS, COLS == 192 ? 2 : (K <= 4 ? 5 : 3))
   });
 }
 
+// The periodic wavefront with two columns per thread (tile columns 2c and 2c + 1) and the
+// collision on FP32 pairs (collide13x2: the same rounded operations, so the same bits).
+// Rows of the shared-memory planes have COLS + 4 floats, tile column i at i + 2, so a
+// pair is 8-byte aligned and a read one column beyond either end of the tile stays inside
+// the row (the cells that read it lie outside the level's valid range and are never used).
+// Input pairs land by 8-byte cp.async, which needs even nx and K: then every strip starts
+// at an even column, has an even width, and no pair straddles the periodic seam.
+template <int K, int COLS, int PF>
+struct PairShape {
+  static constexpr int RS = COLS + 4;  // floats per plane row
+  // input ring per plane group: the row read now, the rows landed but not yet read by this
+  // group, and PF rows in flight
+  static constexpr int A0 = 1 + PF, B0 = 2 + PF, C0 = 3 + PF;
+  static constexpr int L0_FLOATS = RS * (3 * A0 + 7 * B0 + 3 * C0);
+  static constexpr int LV_FLOATS = RS * 2 * 6;
+  static constexpr size_t floats() { return static_cast<size_t>(L0_FLOATS) + (K - 1) * LV_FLOATS; }
+};
+
+template <int K, int COLS, int PF>
+__global__ void __launch_bounds__(COLS / 2, 2)
+    step2d_temporal_periodic_x2(const StepArgs<float> A, const Consts<float> Kc, const Partition P) {
+  using S = PairShape<K, COLS, PF>;
+  constexpr int RS = S::RS;
+  extern __shared__ __align__(16) float smem[];
+  const int c = threadIdx.x;  // pair index: tile columns 2c, 2c + 1
+  const int col = 2 * c;
+  const int nx = A.nx, ny = A.ny;
+
+  float* const l0a = smem;
+  float* const l0b = l0a + S::A0 * 3 * RS;
+  float* const l0c = l0b + S::B0 * 7 * RS;
+  auto xm = [&](int t, int slot) { return smem + S::L0_FLOATS + (t - 1) * S::LV_FLOATS + slot * 6 * RS; };
+  auto ld2 = [](const float* q) { return *reinterpret_cast<const float2*>(q); };
+  auto st2 = [](float* q, float2 v) { *reinterpret_cast<float2*>(q) = v; };
+
+  run_segment(P, ny, [&](int strip, int ys, int ye) {
+    const int gx_raw = strip * P.w - K + col;
+    const bool in_tile = col < P.w + 2 * K;
+    const int gx = ((gx_raw % nx) + nx) % nx;
+    const int iters = (ye - ys) + 2 * K;
+
+    float2 a_now[K][3], f0_now[K], c_now[K][3], f0_prev[K], c_prev1[K][3], c_prev2[K][3];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+      f0_now[t] = f0_prev[t] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = make_float2(0.f, 0.f);
+    }
+
+    auto issue_row = [&](int j) {
+      if (j < iters && in_tile) {
+        const int r = ys - K + j;
+        const int gr = ((r % ny) + ny) % ny;
+        const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
+        float* sa = l0a + (j % S::A0) * 3 * RS + col + 2;
+        float* sb = l0b + (j % S::B0) * 7 * RS + col + 2;
+        float* sc = l0c + (j % S::C0) * 3 * RS + col + 2;
+#pragma unroll
+        for (int p = 0; p < 13; ++p) {
+          float* d = plane_group(p) == 0 ? sa : (plane_group(p) == 1 ? sb : sc);
+          __pipeline_memcpy_async(d + plane_index(p) * RS, g + p * A.plane, 2 * sizeof(float));
+        }
+      }
+      __pipeline_commit();
+    };
+
+#pragma unroll
+    for (int q = 0; q < PF; ++q) issue_row(q);
+    for (int j = 0; j < iters; ++j) {
+      __pipeline_wait_prior(PF - 1);  // row j has landed (this thread's copies)
+      __syncthreads();                // ... and every thread's; iteration j - 1 is over everywhere
+      issue_row(j + PF);
+#pragma unroll
+      for (int t = 1; t <= K; ++t) {
+        const int R = ys - K + j - t;
+        const bool row_ok = R >= ys - K + t && R < ye + K - t;
+        if (row_ok && col + 1 >= t && col < P.w + 2 * K - t) {
+          float2 f[13];
+          if (t == 1) {
+            const float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;
+            const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 7 * RS + col + 2;
+            const float* rc = l0c + ((j + S::C0 - 2) % S::C0) * 3 * RS + col + 2;
+            f[0] = ld2(rb);
+#pragma unroll
+            for (int fam = 0; fam < 3; ++fam) {
+              const float* px = rb + (1 + 2 * fam) * RS;  // +x movers from columns 2c - 1, 2c
+              const float* mx = rb + (2 + 2 * fam) * RS;  // -x movers from columns 2c + 1, 2c + 2
+              f[1 + 4 * fam] = make_float2(px[-1], px[0]);
+              f[2 + 4 * fam] = ld2(rc + fam * RS);
+              f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
+              f[4 + 4 * fam] = ld2(ra + fam * RS);
+            }
+          } else {
+            const float* x = xm(t - 1, (j + 1) & 1) + col + 2;
+            f[0] = f0_prev[t - 1];
+#pragma unroll
+            for (int fam = 0; fam < 3; ++fam) {
+              const float* px = x + (2 * fam) * RS;
+              const float* mx = x + (2 * fam + 1) * RS;
+              f[1 + 4 * fam] = make_float2(px[-1], px[0]);
+              f[2 + 4 * fam] = c_prev2[t - 1][fam];
+              f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
+              f[4 + 4 * fam] = a_now[t - 1][fam];
+            }
+          }
+          collide13x2(f, Kc);
+          if (t < K) {
+            float* x = xm(t, j & 1) + col + 2;
+#pragma unroll
+            for (int fam = 0; fam < 3; ++fam) {
+              st2(x + (2 * fam) * RS, f[1 + 4 * fam]);
+              st2(x + (2 * fam + 1) * RS, f[3 + 4 * fam]);
+              a_now[t][fam] = f[4 + 4 * fam];
+              c_now[t][fam] = f[2 + 4 * fam];
+            }
+            f0_now[t] = f[0];
+          } else if (col >= K && col < K + P.w && gx_raw < nx) {
+            float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
+#pragma unroll
+            for (int p = 0; p < 13; ++p) st2(g + p * A.plane, f[p]);
+          }
+        }
+        if (t > 1) {
+          f0_prev[t - 1] = f0_now[t - 1];
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            c_prev2[t - 1][fam] = c_prev1[t - 1][fam];
+            c_prev1[t - 1][fam] = c_now[t - 1][fam];
+          }
+        }
+      }
+    }
+    __pipeline_wait_prior(0);
+  });
+}
+
 // Resident CTAs per SM of a kernel at its dynamic shared-memory size (asked once).
 inline int resident_ctas(const void* fn, int threads, size_t smem) {
   int r = 0;
@@ -344,16 +480,20 @@ inline int resident_ctas(const void* fn, int threads, size_t smem) {
 // Strips of equal width <= wmax, then row segments: about `waves` waves of the resident
 // CTAs (`slots` of them), rounded down to whole segments per strip, no segment shorter
 // than 2K rows (the wavefront's fill) unless the domain is.
-inline Partition partition(int nx, int ny, int wmax, int K, int slots, int waves) {
-  Partition P;
-  P.strips = (nx + wmax - 1) / wmax;
-  P.w = (nx + P.strips - 1) / P.strips;
+inline Partition partition_rows(Partition P, int ny, int K, int slots, int waves) {
   const int min_rows = std::min(2 * K, ny);
   int seg = std::max(1, (waves * slots) / P.strips);
   seg = std::min(seg, std::max(1, ny / min_rows));
   P.rows_per_cta = (ny + seg - 1) / seg;
   P.segments = (ny + P.rows_per_cta - 1) / P.rows_per_cta;
   return P;
+}
+
+inline Partition partition(int nx, int ny, int wmax, int K, int slots, int waves) {
+  Partition P;
+  P.strips = (nx + wmax - 1) / wmax;
+  P.w = (nx + P.strips - 1) / P.strips;
+  return partition_rows(P, ny, K, slots, waves);
 }
 
 // Launch one kernel of K steps.  Column counts: 192 for the periodic kernel (its shared
@@ -382,9 +522,37 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
   return cudaGetLastError();
 }
 
+// The paired periodic kernel: COLS tile columns, COLS / 2 threads, w even.
+template <int K, int COLS, int PF>
+cudaError_t launch_k_pairs(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t st, int sm_count) {
+  const size_t smem = PairShape<K, COLS, PF>::floats() * sizeof(float);
+  const void* fn = reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  static int resident = 0;
+  if (resident == 0) resident = resident_ctas(fn, COLS / 2, smem);
+  Partition P = partition(a.nx, a.ny, COLS - 2 * K, K, resident * std::max(sm_count, 1), 1);
+  P.w += P.w & 1;  // even strip width (<= COLS - 2K since that is even)
+  P.strips = (a.nx + P.w - 1) / P.w;
+  const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
+  const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
+  step2d_temporal_periodic_x2<K, COLS, PF><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q);
+  return cudaGetLastError();
+}
+
 template <int K>
 cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t st, int sm_count) {
   const bool per = a.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC && a.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
+  // paired kernel (even nx and K): 256 columns and two rows of prefetch up to K = 4; above,
+  // 192 columns and one row of prefetch keep two CTAs per SM within the shared memory
+  if constexpr (K % 2 == 0) {
+    if (per && a.nx % 2 == 0) {
+      if constexpr (K <= 4)
+        return launch_k_pairs<K, 256, 2>(a, kd, st, sm_count);
+      else
+        return launch_k_pairs<K, 192, 1>(a, kd, st, sm_count);
+    }
+  }
   return per ? launch_k<K, true>(a, kd, st, sm_count) : launch_k<K, false>(a, kd, st, sm_count);
 }
 

@@ -225,7 +225,8 @@ LBM_SW_API int lbm_sw_set_populations(lbm_sw* h, const void* src, int on_device,
  * the same scheme parameters and boundary kinds, advanced together: one kernel launch per
  * time step walks a list of tiles (rows x 32 vectors) covering every instance, either one CTA
  * per tile or a persistent grid of a few CTAs per SM striding through the list,
- * and long runs replay a CUDA graph of graph_chunk steps.  Each instance evolves exactly as
+ * and long runs replay a CUDA graph of graph_chunk steps; FP32 batches with every side
+ * periodic fuse temporal_steps steps per launch instead (temporal blocking).  Each instance evolves exactly as
  * it would in its own lbm_sw handle (same device arithmetic, bit for bit).  Tile shape and
  * schedule come from lbm_sw_batch_autotune (or the params).  All instances share two device
  * buffers (double buffering); instance i stores its planes like a single handle does
@@ -244,7 +245,10 @@ typedef struct lbm_sw_batch_params {
   int tile_rows;          /* rows per CTA tile: 1, 2, 4 or 8; 0 = default (4) */
   int ctas_per_sm;        /* persistent CTAs per SM, 1 .. 32; 0 = one CTA per tile (default) */
   int graph_chunk;        /* steps per captured CUDA graph; 0 = default (50), < 0 = off */
-  int reserved[5];        /* must be zero */
+  int temporal_steps;     /* steps fused per launch (temporal blocking, FP32 with every side
+                             periodic): 2 .. 8; 1 = one step per launch; 0 = default (6 where
+                             allowed, else 1; lbm_sw_batch_autotune may change it) */
+  int reserved[4];        /* must be zero */
 } lbm_sw_batch_params;
 
 typedef struct lbm_sw_batch_tuning {
@@ -254,6 +258,7 @@ typedef struct lbm_sw_batch_tuning {
   double ms_per_step;     /* time per step of the chosen configuration (0 if not timed) */
   long long tiles;        /* tiles in the work list */
   long long cells;        /* cells over all instances */
+  int temporal_steps;     /* steps fused per launch (1: one step per launch) */
 } lbm_sw_batch_tuning;
 
 /* Defaults as for lbm_sw_params_init (count = 0, nx = ny = NULL must be set). */
@@ -271,7 +276,10 @@ LBM_SW_API void lbm_sw_batch_destroy(lbm_sw_batch* b);
 LBM_SW_API int lbm_sw_batch_set_state(lbm_sw_batch* b, int instance, const double* depth, const double* hu,
                                       const double* hv, int on_device);
 
-/* Advance every instance n >= 0 steps: one tile-list kernel launch per step.  Errors:
+/* Advance every instance n >= 0 steps: with temporal_steps = K >= 2, one launch of a
+ * work list of wavefronts (instance, column strip, row segment; the units balanced over one
+ * wave of resident CTAs) per K steps, the rest of n one tile-list launch per step; else
+ * one tile-list launch per step.  Results equal one step per launch bit for bit.  Errors:
  * LBM_SW_E_ARG, LBM_SW_E_STATE (an instance has no state), LBM_SW_E_CUDA. */
 LBM_SW_API int lbm_sw_batch_step(lbm_sw_batch* b, int n);
 
@@ -286,10 +294,11 @@ LBM_SW_API int lbm_sw_batch_get_populations(lbm_sw_batch* b, int instance, void*
 LBM_SW_API int lbm_sw_batch_diagnostics(lbm_sw_batch* b, int instance, double out[4]);
 
 /* Time trial_steps launches (>= 1) of every candidate tile shape (1, 2, 4, 8 rows) and
- * schedule (one CTA per tile, or 2, 4, 8 persistent CTAs per SM), keep the fastest, and
- * report it.  The
- * trials read the current state and write the spare buffer, so the state does not change.
- * Needs every instance's state.  Synchronises. */
+ * schedule (one CTA per tile, or 2, 4, 8 persistent CTAs per SM) of the one-step kernel and,
+ * when the params left temporal_steps at 0 and the batch allows it, of the temporal kernel
+ * at K = 4, 6 and 8 steps per launch (per step: launch time / K); keep the fastest per
+ * step, and report it.  The trials read the current state and write the spare buffer, so
+ * the state does not change.  Needs every instance's state.  Synchronises. */
 LBM_SW_API int lbm_sw_batch_autotune(lbm_sw_batch* b, int trial_steps, lbm_sw_batch_tuning* out);
 
 /* The tile shape and schedule in use. */

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -102,6 +103,10 @@ struct lbm_sw_batch {
   int candidates = 0;
   double tuned_ms = 0.0;
   int graph_chunk = 50;
+  bool temporal_allowed = false;  // FP32 and every side periodic
+  bool temporal_auto = false;     // temporal_steps left to the library (autotune may choose)
+  int temporal_k = 0;             // steps per temporal launch; 0 = one step per launch
+  lbm::BatchWaves waves[9];       // work lists by K (built on first use)
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   std::string err;
@@ -182,6 +187,25 @@ cudaError_t launch_batch(const lbm_sw_batch* b, int from, int rows, int ctas, cu
                                        : launch_batch_t<float>(b, from, rows, ctas, st);
 }
 
+int ensure_waves(lbm_sw_batch* b, int k) {
+  if (b->waves[k].grid > 0) return LBM_SW_OK;
+  std::vector<long long> off(b->p.count), pitch(b->p.count), plane(b->p.count);
+  for (int i = 0; i < b->p.count; ++i) {
+    off[i] = b->inst[i].offset;
+    pitch[i] = b->inst[i].pitch;
+    plane[i] = b->inst[i].plane;
+  }
+  BATCH_CUDA(b, lbm::batch_waves_build(b->p.count, b->nx.data(), b->ny.data(), off.data(), pitch.data(), plane.data(),
+                                       k, b->sm_count, &b->waves[k]),
+             "temporal work list");
+  return LBM_SW_OK;
+}
+
+cudaError_t launch_temporal(const lbm_sw_batch* b, int from, int k, cudaStream_t st) {
+  return lbm::launch_batch_temporal(b->waves[k], k, static_cast<const float*>(b->buf[from]),
+                                    static_cast<float*>(b->buf[1 - from]), bconsts(b), st);
+}
+
 void drop_graphs(lbm_sw_batch* b) {
   for (int i = 0; i < 2; ++i)
     if (b->graph[i]) {
@@ -251,7 +275,15 @@ int validate_batch(const lbm_sw_batch_params* p, lbm_sw_batch* b) {
   if (p->tile_rows != 0 && p->tile_rows != 1 && p->tile_rows != 2 && p->tile_rows != 4 && p->tile_rows != 8)
     return bfail(b, LBM_SW_E_ARG, "tile_rows must be 0, 1, 2, 4 or 8");
   if (p->ctas_per_sm < 0 || p->ctas_per_sm > 32) return bfail(b, LBM_SW_E_ARG, "ctas_per_sm must be in [0, 32]");
-  for (int r = 0; r < 5; ++r)
+  if (p->temporal_steps < 0 || p->temporal_steps > 8)
+    return bfail(b, LBM_SW_E_ARG, "temporal_steps must be in [0, 8] (got %d)", p->temporal_steps);
+  if (p->temporal_steps >= 2) {
+    bool per = true;
+    for (int s = 0; s < 4; ++s) per = per && p->bc[s] == LBM_SW_BC_PERIODIC;
+    if (p->precision != LBM_SW_FP32 || !per)
+      return bfail(b, LBM_SW_E_ARG, "temporal_steps >= 2 needs FP32 and every side periodic");
+  }
+  for (int r = 0; r < 4; ++r)
     if (p->reserved[r] != 0) return bfail(b, LBM_SW_E_ARG, "reserved fields must be zero");
   return LBM_SW_OK;
 }
@@ -291,6 +323,7 @@ void lbm_sw_batch_destroy(lbm_sw_batch* b) {
   if (b->diag_partials) cudaFree(b->diag_partials);
   if (b->diag_out) cudaFree(b->diag_out);
   if (b->diag_host) cudaFreeHost(b->diag_host);
+  for (int k = 0; k < 9; ++k) lbm::batch_waves_free(&b->waves[k]);
   delete b;
 }
 
@@ -317,6 +350,10 @@ int lbm_sw_batch_create(const lbm_sw_batch_params* p, lbm_sw_batch** out) {
   b->tile_rows = p->tile_rows ? p->tile_rows : 4;
   b->ctas_per_sm = p->ctas_per_sm;  // 0: one CTA per tile
   b->graph_chunk = p->graph_chunk == 0 ? 50 : (p->graph_chunk < 0 ? 0 : p->graph_chunk + (p->graph_chunk & 1));
+  b->temporal_allowed = p->precision == LBM_SW_FP32;
+  for (int s = 0; s < 4; ++s) b->temporal_allowed = b->temporal_allowed && p->bc[s] == LBM_SW_BC_PERIODIC;
+  b->temporal_auto = p->temporal_steps == 0 && b->temporal_allowed;
+  b->temporal_k = p->temporal_steps >= 2 ? p->temporal_steps : (b->temporal_auto ? 6 : 0);
   b->has_state.assign(p->count, 0);
   const int V = p->precision == LBM_SW_FP64 ? 2 : 4;
 
@@ -429,8 +466,17 @@ int lbm_sw_batch_step(lbm_sw_batch* b, int n) {
   if (n < 0) return bfail(b, LBM_SW_E_ARG, "step: n must be >= 0 (got %d)", n);
   if (b->states_set != b->p.count)
     return bfail(b, LBM_SW_E_STATE, "step: %d of %d instances have no state", b->p.count - b->states_set, b->p.count);
+  if (b->temporal_k >= 2 && n >= b->temporal_k) {
+    int rc = ensure_waves(b, b->temporal_k);
+    if (rc) return rc;
+  }
   while (n > 0) {
-    if (b->graph_chunk > 0 && n >= b->graph_chunk) {
+    if (b->temporal_k >= 2 && n >= b->temporal_k) {
+      cudaError_t e = launch_temporal(b, b->cur, b->temporal_k, b->stream);
+      if (e != cudaSuccess) return bcuda(b, e, "batch temporal launch");
+      b->cur ^= 1;
+      n -= b->temporal_k;
+    } else if (b->graph_chunk > 0 && n >= b->graph_chunk) {
       if (!b->graph[b->cur]) {
         int rc = build_graph(b, b->cur);
         if (rc) return rc;
@@ -520,6 +566,7 @@ int lbm_sw_batch_get_tuning(const lbm_sw_batch* b, lbm_sw_batch_tuning* out) {
   out->ms_per_step = b->tuned_ms;
   out->tiles = b->tiles[rows_index(b->tile_rows)];
   out->cells = b->cells;
+  out->temporal_steps = b->temporal_k >= 2 ? b->temporal_k : 1;
   return LBM_SW_OK;
 }
 
@@ -557,12 +604,41 @@ int lbm_sw_batch_autotune(lbm_sw_batch* b, int trial_steps, lbm_sw_batch_tuning*
       }
     }
   }
+  // temporal blocking: K steps per launch, compared per step
+  int best_k = b->temporal_auto ? 0 : b->temporal_k;
+  if (rc == LBM_SW_OK && b->temporal_auto) {
+    const int ks[3] = {4, 6, 8};
+    for (int q = 0; q < 3 && rc == LBM_SW_OK; ++q) {
+      const int k = ks[q];
+      rc = ensure_waves(b, k);
+      if (rc != LBM_SW_OK) break;
+      const int launches = std::max(1, (trial_steps + k - 1) / k);
+      cudaError_t e = launch_temporal(b, b->cur, k, b->stream);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+      for (int r = 0; r < launches && e == cudaSuccess; ++r) e = launch_temporal(b, b->cur, k, b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        rc = bcuda(b, e, "autotune temporal trial");
+        break;
+      }
+      ++tried;
+      const double per = ms / (static_cast<double>(launches) * k);
+      if (per < best) {
+        best = per;
+        best_k = k;
+      }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != LBM_SW_OK) return rc;
   if (best_rows != b->tile_rows || best_ctas != b->ctas_per_sm) drop_graphs(b);
   b->tile_rows = best_rows;
   b->ctas_per_sm = best_ctas;
+  b->temporal_k = best_k;
   b->candidates = tried;
   b->tuned_ms = best;
   if (out) lbm_sw_batch_get_tuning(b, out);

@@ -59,7 +59,34 @@ cudaError_t launch_moments2d_planes(const StepArgs<T>& a, T* w_out, cudaStream_t
 template <class Tin, class Tout>
 cudaError_t launch_convert(const Tin* in, Tout* out, long long n, cudaStream_t st);
 
-// k fused steps per launch (temporal.cu; FP32, BGK; k in 2 .. 6): src -> dst.
+// Batched temporal blocking (temporal.cu): one wavefront unit covers rows [ys, ye) of the
+// output columns [x0, x0 + w) of one instance (clipped at nx) of a batch whose sides are
+// all periodic; a work list holds the units of every instance, grouped by CTA.
+struct WaveUnit {
+  long long offset;  // element offset of the instance's first plane in each buffer
+  long long plane;   // elements per plane
+  int pitch;         // elements per row
+  int nx, ny;
+  int x0, w;
+  int ys, ye;
+  int pad;
+};
+struct BatchWaves {
+  WaveUnit* units = nullptr;  // device
+  int* first = nullptr;       // device, grid + 1 entries: CTA b runs units [first[b], first[b + 1])
+  int count = 0;
+  int grid = 0;
+};
+// Build the work list of k-step wavefronts for the given instances (host arrays of count
+// entries) on the current device; free with batch_waves_free.
+cudaError_t batch_waves_build(int count, const int* nx, const int* ny, const long long* offset, const long long* pitch,
+                              const long long* plane, int k, int sm_count, BatchWaves* out);
+void batch_waves_free(BatchWaves* w);
+// k fused steps of every instance: src -> dst (the batch's two buffers).
+cudaError_t launch_batch_temporal(const BatchWaves& w, int k, const float* src, float* dst, const ConstsD& kd,
+                                  cudaStream_t st);
+
+// k fused steps per launch (temporal.cu; FP32, BGK; k in 2 .. 8): src -> dst.
 bool temporal_steps_supported(int k);
 cudaError_t launch_step2d_temporal(const StepArgs<float>& a, const ConstsD& kd, int k, cudaStream_t st,
                                    int sm_count);

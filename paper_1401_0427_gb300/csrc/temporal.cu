@@ -16,6 +16,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
+#include <queue>
+#include <utility>
+#include <vector>
 
 #include "internal.h"
 #include "scheme.cuh"
@@ -214,11 +218,12 @@ __global__ void __launch_bounds__(COLS, 1)
 // reads level t's x movers from the previous iteration's row and its other planes from
 // registers, so the only barrier per iteration is the one after the input row lands; the
 // next input row is issued after it, when every thread has finished the previous iteration.
+// One wavefront of the periodic scheme over output columns [x0, x0 + w) and rows [ys, ye)
+// of the grid A (every side periodic), K levels per input row.
 template <int K, int COLS>
-__global__ void __launch_bounds__(COLS, COLS == 192 ? 2 : (K <= 4 ? 5 : 3))
-    step2d_temporal_periodic(const StepArgs<float> A, const Consts<float> Kc, const Partition P) {
+__device__ __forceinline__ void periodic_wave(const StepArgs<float>& A, const Consts<float>& Kc, float* smem, int x0,
+                                              int w, int ys, int ye) {
   using S = PeriodicShape<K, COLS>;
-  extern __shared__ __align__(16) float smem[];
   const int c = threadIdx.x;
   const int nx = A.nx, ny = A.ny;
 
@@ -229,109 +234,138 @@ __global__ void __launch_bounds__(COLS, COLS == 192 ? 2 : (K <= 4 ? 5 : 3))
   // level t >= 1: x movers [2][6][COLS], planes 1, 3, 5, 7, 9, 11 in that order
   auto xm = [&](int t, int slot) { return smem + S::L0_FLOATS + (t - 1) * S::LV_FLOATS + slot * 6 * COLS; };
 
-  run_segment(P, ny, [&](int strip, int ys, int ye) {
-    const int gx_raw = strip * P.w - K + c;
-    const bool in_tile = c < P.w + 2 * K;
-    const int gx = ((gx_raw % nx) + nx) % nx;
-    const int iters = (ye - ys) + 2 * K;
+  const int gx_raw = x0 - K + c;
+  const bool in_tile = c < w + 2 * K;
+  const int gx = ((gx_raw % nx) + nx) % nx;
+  const int iters = (ye - ys) + 2 * K;
 
-    // Level t (1 .. K - 1) as the input of level t + 1, in the column's registers: the -y
-    // movers, f0 and +y movers of the row computed in this iteration (*_now), f0 of the
-    // previous row, the +y movers of the previous two rows.  Where a level was not
-    // computed (halo columns and rows outside its range) they hold stale values that the
-    // next level, whose range is one smaller on each side, never reads.
-    float a_now[K][3], f0_now[K], c_now[K][3], f0_prev[K], c_prev1[K][3], c_prev2[K][3];
+  // Level t (1 .. K - 1) as the input of level t + 1, in the column's registers: the -y
+  // movers, f0 and +y movers of the row computed in this iteration (*_now), f0 of the
+  // previous row, the +y movers of the previous two rows.  Where a level was not
+  // computed (halo columns and rows outside its range) they hold stale values that the
+  // next level, whose range is one smaller on each side, never reads.
+  float a_now[K][3], f0_now[K], c_now[K][3], f0_prev[K], c_prev1[K][3], c_prev2[K][3];
 #pragma unroll
-    for (int t = 0; t < K; ++t) {
-      f0_now[t] = f0_prev[t] = 0.0f;
+  for (int t = 0; t < K; ++t) {
+    f0_now[t] = f0_prev[t] = 0.0f;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = 0.0f;
-    }
+    for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = 0.0f;
+  }
 
-    auto issue_row = [&](int j) {
-      if (j < iters && in_tile) {
-        const int r = ys - K + j;
-        const int gr = ((r % ny) + ny) % ny;
-        const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
-        float* sa = l0a + (j % S::A0) * 3 * COLS + c;
-        float* sb = l0b + (j % S::B0) * 7 * COLS + c;
-        float* sc = l0c + (j % S::C0) * 3 * COLS + c;
+  auto issue_row = [&](int j) {
+    if (j < iters && in_tile) {
+      const int r = ys - K + j;
+      const int gr = ((r % ny) + ny) % ny;
+      const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
+      float* sa = l0a + (j % S::A0) * 3 * COLS + c;
+      float* sb = l0b + (j % S::B0) * 7 * COLS + c;
+      float* sc = l0c + (j % S::C0) * 3 * COLS + c;
 #pragma unroll
-        for (int p = 0; p < 13; ++p) {
-          float* d = plane_group(p) == 0 ? sa : (plane_group(p) == 1 ? sb : sc);
-          __pipeline_memcpy_async(d + plane_index(p) * COLS, g + p * A.plane, sizeof(float));
-        }
+      for (int p = 0; p < 13; ++p) {
+        float* d = plane_group(p) == 0 ? sa : (plane_group(p) == 1 ? sb : sc);
+        __pipeline_memcpy_async(d + plane_index(p) * COLS, g + p * A.plane, sizeof(float));
       }
-      __pipeline_commit();
-    };
+    }
+    __pipeline_commit();
+  };
 
-    issue_row(0);
-    issue_row(1);
-    for (int j = 0; j < iters; ++j) {
-      __pipeline_wait_prior(1);  // row j has landed (this thread's copies; row j + 1 may be in flight)
-      __syncthreads();           // ... and every thread's; iteration j - 1 is over everywhere
-      issue_row(j + 2);
+  issue_row(0);
+  issue_row(1);
+  for (int j = 0; j < iters; ++j) {
+    __pipeline_wait_prior(1);  // row j has landed (this thread's copies; row j + 1 may be in flight)
+    __syncthreads();           // ... and every thread's; iteration j - 1 is over everywhere
+    issue_row(j + 2);
 #pragma unroll
-      for (int t = 1; t <= K; ++t) {
-        const int R = ys - K + j - t;  // row of level t computed now
-        const bool row_ok = R >= ys - K + t && R < ye + K - t;
-        if (row_ok && c >= t && c < P.w + 2 * K - t) {
-          float f[13];
-          if (t == 1) {
-            // level 0: row R + 1 landed now (iteration j), R at j - 1, R - 1 at j - 2
-            const float* ra = l0a + (j % S::A0) * 3 * COLS + c;
-            const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 7 * COLS + c;
-            const float* rc = l0c + ((j + S::C0 - 2) % S::C0) * 3 * COLS + c;
-            f[0] = rb[0];
-#pragma unroll
-            for (int fam = 0; fam < 3; ++fam) {
-              f[1 + 4 * fam] = rb[(1 + 2 * fam) * COLS - 1];
-              f[2 + 4 * fam] = rc[fam * COLS];
-              f[3 + 4 * fam] = rb[(2 + 2 * fam) * COLS + 1];
-              f[4 + 4 * fam] = ra[fam * COLS];
-            }
-          } else {
-            const float* x = xm(t - 1, (j + 1) & 1) + c;  // level t - 1, row R (previous iteration)
-            f[0] = f0_prev[t - 1];
-#pragma unroll
-            for (int fam = 0; fam < 3; ++fam) {
-              f[1 + 4 * fam] = x[(2 * fam) * COLS - 1];
-              f[2 + 4 * fam] = c_prev2[t - 1][fam];
-              f[3 + 4 * fam] = x[(2 * fam + 1) * COLS + 1];
-              f[4 + 4 * fam] = a_now[t - 1][fam];
-            }
-          }
-          float h, qx, qy;
-          collide13(f, Kc, h, qx, qy);
-          if (t < K) {
-            float* x = xm(t, j & 1) + c;
-#pragma unroll
-            for (int fam = 0; fam < 3; ++fam) {
-              x[(2 * fam) * COLS] = f[1 + 4 * fam];
-              x[(2 * fam + 1) * COLS] = f[3 + 4 * fam];
-              a_now[t][fam] = f[4 + 4 * fam];
-              c_now[t][fam] = f[2 + 4 * fam];
-            }
-            f0_now[t] = f[0];
-          } else if (c >= K && c < K + P.w && gx_raw < nx) {
-            float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
-#pragma unroll
-            for (int p = 0; p < 13; ++p) g[p * A.plane] = f[p];
-          }
-        }
-        if (t > 1) {
-          // level t - 1 is consumed for this iteration: age its rows
-          f0_prev[t - 1] = f0_now[t - 1];
+    for (int t = 1; t <= K; ++t) {
+      const int R = ys - K + j - t;  // row of level t computed now
+      const bool row_ok = R >= ys - K + t && R < ye + K - t;
+      if (row_ok && c >= t && c < w + 2 * K - t) {
+        float f[13];
+        if (t == 1) {
+          // level 0: row R + 1 landed now (iteration j), R at j - 1, R - 1 at j - 2
+          const float* ra = l0a + (j % S::A0) * 3 * COLS + c;
+          const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 7 * COLS + c;
+          const float* rc = l0c + ((j + S::C0 - 2) % S::C0) * 3 * COLS + c;
+          f[0] = rb[0];
 #pragma unroll
           for (int fam = 0; fam < 3; ++fam) {
-            c_prev2[t - 1][fam] = c_prev1[t - 1][fam];
-            c_prev1[t - 1][fam] = c_now[t - 1][fam];
+            f[1 + 4 * fam] = rb[(1 + 2 * fam) * COLS - 1];
+            f[2 + 4 * fam] = rc[fam * COLS];
+            f[3 + 4 * fam] = rb[(2 + 2 * fam) * COLS + 1];
+            f[4 + 4 * fam] = ra[fam * COLS];
           }
+        } else {
+          const float* x = xm(t - 1, (j + 1) & 1) + c;  // level t - 1, row R (previous iteration)
+          f[0] = f0_prev[t - 1];
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            f[1 + 4 * fam] = x[(2 * fam) * COLS - 1];
+            f[2 + 4 * fam] = c_prev2[t - 1][fam];
+            f[3 + 4 * fam] = x[(2 * fam + 1) * COLS + 1];
+            f[4 + 4 * fam] = a_now[t - 1][fam];
+          }
+        }
+        float h, qx, qy;
+        collide13(f, Kc, h, qx, qy);
+        if (t < K) {
+          float* x = xm(t, j & 1) + c;
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            x[(2 * fam) * COLS] = f[1 + 4 * fam];
+            x[(2 * fam + 1) * COLS] = f[3 + 4 * fam];
+            a_now[t][fam] = f[4 + 4 * fam];
+            c_now[t][fam] = f[2 + 4 * fam];
+          }
+          f0_now[t] = f[0];
+        } else if (c >= K && c < K + w && gx_raw < nx) {
+          float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
+#pragma unroll
+          for (int p = 0; p < 13; ++p) g[p * A.plane] = f[p];
+        }
+      }
+      if (t > 1) {
+        // level t - 1 is consumed for this iteration: age its rows
+        f0_prev[t - 1] = f0_now[t - 1];
+#pragma unroll
+        for (int fam = 0; fam < 3; ++fam) {
+          c_prev2[t - 1][fam] = c_prev1[t - 1][fam];
+          c_prev1[t - 1][fam] = c_now[t - 1][fam];
         }
       }
     }
-    __pipeline_wait_prior(0);
-  });
+  }
+  __pipeline_wait_prior(0);
+}
+
+template <int K, int COLS>
+__global__ void __launch_bounds__(COLS, COLS == 192 ? 2 : (K <= 4 ? 5 : 3))
+    step2d_temporal_periodic(const StepArgs<float> A, const Consts<float> Kc, const Partition P) {
+  extern __shared__ __align__(16) float smem[];
+  run_segment(P, A.ny, [&](int strip, int ys, int ye) { periodic_wave<K, COLS>(A, Kc, smem, strip * P.w, P.w, ys, ye); });
+}
+
+// Batched instances: a list of wavefront units (instance, strip, row segment); CTA b runs
+// units [first[b], first[b + 1]) one after the other, on a grid of one wave of resident
+// CTAs (the host balances the units over the CTAs).
+template <int K, int COLS>
+__global__ void __launch_bounds__(COLS, COLS == 192 ? 2 : (K <= 4 ? 5 : 3))
+    batch_temporal_periodic(const WaveUnit* __restrict__ units, const int* __restrict__ first,
+                            const float* __restrict__ src, float* __restrict__ dst, const Consts<float> Kc) {
+  extern __shared__ __align__(16) float smem[];
+  for (int u = first[blockIdx.x]; u < first[blockIdx.x + 1]; ++u) {
+    const WaveUnit U = units[u];
+    StepArgs<float> A;
+    A.src = src + U.offset;
+    A.dst = dst + U.offset;
+    A.inflow_feq = nullptr;
+    A.nx = U.nx;
+    A.ny = U.ny;
+    A.pitch = U.pitch;
+    A.plane = U.plane;
+    for (int s = 0; s < 4; ++s) A.bc[s] = LBM_SW_BC_PERIODIC;
+    periodic_wave<K, COLS>(A, Kc, smem, U.x0, U.w, U.ys, U.ye);
+    __syncthreads();  // the next unit reuses the rings
+  }
 }
 
 // The periodic wavefront with two columns per thread (tile columns 2c and 2c + 1) and the
@@ -571,6 +605,145 @@ cudaError_t launch_step2d_temporal(const StepArgs<float>& a, const ConstsD& kd, 
     case 8: return launch_k<8>(a, kd, st, sm_count);
     default: return launch_k<4>(a, kd, st, sm_count);
   }
+}
+
+// ---------------------------------------------------------------- batched instances
+namespace {
+
+template <int K>
+size_t batch_smem() {
+  return PeriodicShape<K, 192>::floats() * sizeof(float);
+}
+
+template <int K>
+const void* batch_fn() {
+  return reinterpret_cast<const void*>(batch_temporal_periodic<K, 192>);
+}
+
+template <int K>
+cudaError_t batch_prepare(int* resident) {
+  const size_t smem = batch_smem<K>();
+  cudaError_t e = cudaFuncSetAttribute(batch_fn<K>(), cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  *resident = resident_ctas(batch_fn<K>(), 192, smem);
+  return cudaSuccess;
+}
+
+cudaError_t batch_prepare_k(int k, int* resident) {
+  switch (k) {
+    case 2: return batch_prepare<2>(resident);
+    case 3: return batch_prepare<3>(resident);
+    case 5: return batch_prepare<5>(resident);
+    case 6: return batch_prepare<6>(resident);
+    case 7: return batch_prepare<7>(resident);
+    case 8: return batch_prepare<8>(resident);
+    default: return batch_prepare<4>(resident);
+  }
+}
+
+template <int K>
+void batch_launch(const BatchWaves& w, const float* src, float* dst, const Consts<float>& c, cudaStream_t st) {
+  batch_temporal_periodic<K, 192><<<w.grid, 192, batch_smem<K>(), st>>>(w.units, w.first, src, dst, c);
+}
+
+}  // namespace
+
+cudaError_t batch_waves_build(int count, const int* nx, const int* ny, const long long* offset, const long long* pitch,
+                              const long long* plane, int k, int sm_count, BatchWaves* out) {
+  batch_waves_free(out);
+  int resident = 1;
+  cudaError_t e = batch_prepare_k(k, &resident);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, resident * std::max(sm_count, 1));
+  const int wmax = 192 - 2 * k;
+  // row segments of about a sixth of a CTA's share of the strip rows, no shorter than 4k
+  long long strip_rows = 0;
+  for (int i = 0; i < count; ++i) strip_rows += static_cast<long long>((nx[i] + wmax - 1) / wmax) * ny[i];
+  const long long target = std::max<long long>(4LL * k, (strip_rows + 6LL * grid - 1) / (6LL * grid));
+  std::vector<WaveUnit> units;
+  std::vector<long long> cost;
+  for (int i = 0; i < count; ++i) {
+    const int strips = (nx[i] + wmax - 1) / wmax;
+    const int w = (nx[i] + strips - 1) / strips;
+    const int segs = static_cast<int>(std::max<long long>(1, (ny[i] + target - 1) / target));
+    const int rows = (ny[i] + segs - 1) / segs;
+    for (int sgi = 0; sgi < segs; ++sgi)
+      for (int st = 0; st < strips; ++st) {
+        WaveUnit u;
+        u.offset = offset[i];
+        u.plane = plane[i];
+        u.pitch = static_cast<int>(pitch[i]);
+        u.nx = nx[i];
+        u.ny = ny[i];
+        u.x0 = st * w;
+        u.w = w;
+        u.ys = sgi * rows;
+        u.ye = std::min(ny[i], u.ys + rows);
+        u.pad = 0;
+        if (u.ys >= u.ye) continue;
+        units.push_back(u);
+        cost.push_back(static_cast<long long>(u.ye - u.ys + 2 * k) * (std::min(w, nx[i] - u.x0) + 2 * k));
+      }
+  }
+  // longest-processing-time-first onto the least loaded CTA
+  std::vector<int> order(units.size());
+  for (size_t u = 0; u < order.size(); ++u) order[u] = static_cast<int>(u);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  using Load = std::pair<long long, int>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (int b = 0; b < grid; ++b) heap.push({0, b});
+  std::vector<std::vector<int>> per(grid);
+  for (int u : order) {
+    Load l = heap.top();
+    heap.pop();
+    per[l.second].push_back(u);
+    heap.push({l.first + cost[u], l.second});
+  }
+  std::vector<WaveUnit> sorted;
+  std::vector<int> first(grid + 1, 0);
+  sorted.reserve(units.size());
+  for (int b = 0; b < grid; ++b) {
+    first[b] = static_cast<int>(sorted.size());
+    for (int u : per[b]) sorted.push_back(units[u]);
+  }
+  first[grid] = static_cast<int>(sorted.size());
+  e = cudaMalloc(&out->units, std::max<size_t>(1, sorted.size()) * sizeof(WaveUnit));
+  if (e == cudaSuccess) e = cudaMalloc(&out->first, first.size() * sizeof(int));
+  if (e == cudaSuccess && !sorted.empty())
+    e = cudaMemcpy(out->units, sorted.data(), sorted.size() * sizeof(WaveUnit), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(out->first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    batch_waves_free(out);
+    return e;
+  }
+  out->count = static_cast<int>(sorted.size());
+  out->grid = grid;
+  return cudaSuccess;
+}
+
+void batch_waves_free(BatchWaves* w) {
+  if (w->units) cudaFree(w->units);
+  if (w->first) cudaFree(w->first);
+  *w = BatchWaves();
+}
+
+cudaError_t launch_batch_temporal(const BatchWaves& w, int k, const float* src, float* dst, const ConstsD& kd,
+                                  cudaStream_t st) {
+  if (w.grid < 1) return cudaErrorInvalidValue;
+  int resident = 1;
+  cudaError_t e = batch_prepare_k(k, &resident);  // the shared-memory attribute, on this device
+  if (e != cudaSuccess) return e;
+  const Consts<float> c = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
+  switch (k) {
+    case 2: batch_launch<2>(w, src, dst, c, st); break;
+    case 3: batch_launch<3>(w, src, dst, c, st); break;
+    case 5: batch_launch<5>(w, src, dst, c, st); break;
+    case 6: batch_launch<6>(w, src, dst, c, st); break;
+    case 7: batch_launch<7>(w, src, dst, c, st); break;
+    case 8: batch_launch<8>(w, src, dst, c, st); break;
+    default: batch_launch<4>(w, src, dst, c, st);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace lbm

@@ -82,7 +82,8 @@ class lbm_sw_batch_params(ctypes.Structure):
         ("tile_rows", ctypes.c_int),
         ("ctas_per_sm", ctypes.c_int),
         ("graph_chunk", ctypes.c_int),
-        ("reserved", ctypes.c_int * 5),
+        ("temporal_steps", ctypes.c_int),
+        ("reserved", ctypes.c_int * 4),
     ]
 
 
@@ -94,6 +95,7 @@ class lbm_sw_batch_tuning(ctypes.Structure):
         ("ms_per_step", ctypes.c_double),
         ("tiles", ctypes.c_longlong),
         ("cells", ctypes.c_longlong),
+        ("temporal_steps", ctypes.c_int),
     ]
 
 
@@ -514,7 +516,7 @@ class Batch:
 
     def __init__(self, sizes, *, precision: int = FP32, g: float = 1.0, lam: float = 8.0, s: float = 1.8,
                  a: float = 0.05, bc=(PERIODIC,) * 4, inflow=None, stream: int | None = None, tile_rows: int = 0,
-                 ctas_per_sm: int = 0, graph_chunk: int = 0):
+                 ctas_per_sm: int = 0, graph_chunk: int = 0, temporal_steps: int = 0):
         self.sizes = [(int(nx), int(ny)) for nx, ny in sizes]
         self._nx = (ctypes.c_int * len(self.sizes))(*[nx for nx, _ in self.sizes])
         self._ny = (ctypes.c_int * len(self.sizes))(*[ny for _, ny in self.sizes])
@@ -530,6 +532,7 @@ class Batch:
                         p.inflow[k][c] = float(v)
         p.stream = stream
         p.tile_rows, p.ctas_per_sm, p.graph_chunk = int(tile_rows), int(ctas_per_sm), int(graph_chunk)
+        p.temporal_steps = int(temporal_steps)
         self.params = p
         self.handle = lbm_sw_batch_create(p)
         self.dtype = np.float64 if precision == FP64 else np.float32

@@ -64,10 +64,14 @@ def test_struct_layout_matches_c(tmp_path):
         ' printf("%zu %zu %zu %zu %zu\\n", sizeof(lbm_sw_info), offsetof(lbm_sw_info, pitch),\n'
         "   offsetof(lbm_sw_info, bytes_per_update), offsetof(lbm_sw_info, kernel_launches),\n"
         "   offsetof(lbm_sw_info, steps_per_launch));\n"
+        ' printf("%zu %zu %zu %zu %zu\\n", sizeof(lbm_sw_batch_params), offsetof(lbm_sw_batch_params, stream),\n'
+        "   offsetof(lbm_sw_batch_params, temporal_steps), sizeof(lbm_sw_batch_tuning),\n"
+        "   offsetof(lbm_sw_batch_tuning, temporal_steps));\n"
         " return 0; }\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
-    c_params, c_info = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    c_params, c_info, c_batch = subprocess.run([str(exe)], capture_output=True, text=True,
+                                               check=True).stdout.split("\n")[:3]
     P, I = lbm_sw.lbm_sw_params, lbm_sw.lbm_sw_info
     py_params = [ctypes.sizeof(P), P.g.offset, P.bc.offset, P.inflow.offset, P.stream.offset, P.kernel.offset,
                  P.reserved.offset]
@@ -75,6 +79,9 @@ def test_struct_layout_matches_c(tmp_path):
                I.steps_per_launch.offset]
     assert [int(v) for v in c_params.split()] == py_params
     assert [int(v) for v in c_info.split()] == py_info
+    B, BT = lbm_sw.lbm_sw_batch_params, lbm_sw.lbm_sw_batch_tuning
+    py_batch = [ctypes.sizeof(B), B.stream.offset, B.temporal_steps.offset, ctypes.sizeof(BT), BT.temporal_steps.offset]
+    assert [int(v) for v in c_batch.split()] == py_batch
 
 
 def test_params_defaults(lib):

@@ -78,7 +78,9 @@ def test_autotune_keeps_the_state_and_picks_a_candidate():
         batch.step(3)
         before = [batch.populations(i) for i in range(len(SIZES))]
         t = batch.autotune(3)
-        assert t.candidates == 16 and t.tile_rows in (1, 2, 4, 8) and t.ctas_per_sm in (0, 2, 4, 8)
+        # 16 one-step shapes and schedules, then temporal blocking at K = 4, 6, 8
+        assert t.candidates == 16 + 3 and t.tile_rows in (1, 2, 4, 8) and t.ctas_per_sm in (0, 2, 4, 8)
+        assert t.temporal_steps in (1, 4, 6, 8)
         assert t.ms_per_step > 0 and t.cells == sum(nx * ny for nx, ny in SIZES)
         for i in range(len(SIZES)):
             assert np.array_equal(batch.populations(i), before[i])
@@ -124,3 +126,49 @@ def test_benchmark_instance_table_full_size():
         for i in range(0, 256, 37):
             d = batch.diagnostics(i)
             assert d[4] == lbm_sw.OK
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 6, 7, 8])
+def test_batch_temporal_equals_one_step_per_launch(k):
+    """Temporal blocking over the batch's work list (instance, strip, row segment) against one
+    tile-list launch per step: the same arithmetic, so the same bits, for odd and even sizes,
+    instances narrower than a strip and wider than several."""
+    sizes = [(1, 1), (3, 2), (7, 5), (64, 64), (130, 9), (257, 33), (100, 200), (513, 3), (400, 37), (181, 181)]
+    states = _states(sizes, seed=1300 + k)
+    out = []
+    for temporal in (1, k):
+        with lbm_sw.Batch(sizes, stream=torch_stream(), temporal_steps=temporal) as batch:
+            for i, W0 in enumerate(states):
+                batch.set_state(i, *W0)
+            batch.step(2 * k + 3)
+            assert batch.tuning().temporal_steps == temporal
+            out.append([batch.populations(i) for i in range(len(sizes))])
+    for i in range(len(sizes)):
+        assert np.array_equal(out[0][i], out[1][i]), (k, sizes[i])
+
+
+def test_batch_temporal_on_the_benchmark_table_and_autotune():
+    table = inputs.batched_instances(256)[:48]
+    sizes = [(n, n) for n, _, _ in table]
+    states = [inputs.circular_dam_break_2d(n, seed=None, h_in=hin, radius=r) for n, hin, r in table]
+    out = []
+    for temporal in (1, 0):
+        with lbm_sw.Batch(sizes, stream=torch_stream(), temporal_steps=temporal) as batch:
+            for i, W0 in enumerate(states):
+                batch.set_state(i, *W0)
+            if temporal == 0:
+                t = batch.autotune(2)
+                assert t.candidates == 16 + 3 and t.temporal_steps in (1, 4, 6, 8)
+            batch.step(30)
+            out.append([batch.populations(i) for i in (0, 7, 19, 47)])
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
+def test_batch_temporal_needs_fp32_and_periodic_sides():
+    with pytest.raises(lbm_sw.LbmSwError):
+        lbm_sw.Batch([(32, 32)], bc=(W, W, P, P), stream=torch_stream(), temporal_steps=4)
+    with pytest.raises(lbm_sw.LbmSwError):
+        lbm_sw.Batch([(32, 32)], precision=lbm_sw.FP64, stream=torch_stream(), temporal_steps=4)
+    with lbm_sw.Batch([(32, 32)], bc=(W, W, P, P), stream=torch_stream()) as batch:
+        assert batch.tuning().temporal_steps == 1  # the default falls back to one step per launch

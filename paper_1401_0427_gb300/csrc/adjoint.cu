@@ -19,6 +19,7 @@
 // for FP32 states, so the replay repeats the forward run bit for bit).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -87,32 +88,6 @@ __device__ __forceinline__ T reverse_pull(const AdjArgs<T>& A, int q, int x, int
   if (!(xb >= 0 && xb < A.nx && yb >= 0 && yb < A.ny) && A.bc[side_of(-ex, -ey)] == LBM_SW_BC_OUTFLOW)
     v += A.phi_in[q * P + y * A.pitch + x];
   return v;
-}
-
-// z = D(W)^T psi: vector-Jacobian product of the equilibria (closed forms of section 3
-// in W = (h, qx, qy); kappa = h/2 - (qx^2 + qy^2)/(4 g h^2), c = 1/(2 lambda)).
-template <class T>
-__device__ __forceinline__ void equilibrium_vjp(T h, T qx, T qy, const T psi[13], const Consts<T>& K, T& zh,
-                                                T& zx, T& zy) {
-  const T rh = T(1) / h;
-  const T u = qx * rh, v = qy * rh;
-  const T gh = T(2) * K.half_g * h;
-  const T inv2gh = T(2) * K.inv4g * rh;
-  const T kh = T(0.5) + (u * u + v * v) * inv2gh;  // dkappa/dh
-  const T kx = -u * inv2gh;                        // dkappa/dqx
-  const T ky = -v * inv2gh;                        // dkappa/dqy
-  const T Sf = (psi[1] + psi[3]) + (psi[2] + psi[4]);
-  const T Af = psi[0] - T(0.25) * Sf;
-  const T Df13 = psi[1] - psi[3], Df24 = psi[2] - psi[4];
-  const T Sx = (psi[5] + psi[7]) + (psi[6] + psi[8]);
-  const T Dx13 = psi[5] - psi[7], Dx24 = psi[6] - psi[8];
-  const T Sy = (psi[9] + psi[11]) + (psi[10] + psi[12]);
-  const T Dy13 = psi[9] - psi[11], Dy24 = psi[10] - psi[12];
-  const T X = Dx24 + Dy13;
-  const T c = K.c;
-  zh = K.a * kh * Af + T(0.25) * Sf + c * (Dx13 * (gh - u * u) - X * u * v + Dy24 * (gh - v * v));
-  zx = K.a * kx * Af + c * Df13 + T(0.25) * Sx + c * (T(2) * Dx13 * u + X * v);
-  zy = K.a * ky * Af + c * Df24 + T(0.25) * Sy + c * (X * u + T(2) * Dy24 * v);
 }
 
 template <class T>
@@ -355,7 +330,8 @@ struct lbm_sw_tape {
   bool recorded = false;
   size_t state_elems = 0;  // 13 * plane
   double* ckpt = nullptr;  // checkpoints * 13 * plane doubles
-  void* wstore = nullptr;  // interval * 3 * plane of T
+  void* wstore = nullptr;  // wslots * 3 * plane of T
+  int wslots = 0;           // interval, plus room for the last fused replay launch to run past it
   void* phi[2] = {nullptr, nullptr};
   void* rep[2] = {nullptr, nullptr};
   double* grad_staging = nullptr;  // 3 * nx * ny doubles (host transfers)
@@ -411,11 +387,36 @@ int run_adjoint(lbm_sw* h, lbm_sw_tape* t, const double* gh, const double* gu, c
                                                  static_cast<T*>(t->rep[0]), static_cast<long long>(t->state_elems), st)),
               "checkpoint restore");
     TAPE_CUDA(t, lbm::launch_moments2d_planes<T>(replay_args<T>(h, t, 0), W, st), "replay moments");
-    for (int j = 1; j < k1 - k0; ++j)
-      TAPE_CUDA(t, lbm::launch_step2d_store_w<T>(replay_args<T>(h, t, (j - 1) & 1), kd, W + 3 * P * j, st),
-                "replay step");
-    // adjoint steps n = k1 .. k0 + 1
+    int from = 0, j = 1;
+    if constexpr (sizeof(T) == 4) {
+      // FP32: K steps per launch where the fused kernel can store every level's moments
+      const int k = h->temporal_k;
+      const auto a0 = replay_args<T>(h, t, 0);
+      // (the last launch may run past the segment into the spare moment slots)
+      if (h->kernel == LBM_SW_KERNEL_TEMPORAL && k > 1 && j + k <= t->wslots && lbm::temporal_store_w_supported(a0, k))
+        for (; j < k1 - k0 && j + k <= t->wslots; j += k, from ^= 1)
+          TAPE_CUDA(t, lbm::launch_step2d_temporal_store_w(replay_args<T>(h, t, from), kd, k, W + 3 * P * j, 3 * P, st,
+                                                           h->sm_count),
+                    "replay launch");
+    }
+    for (; j < k1 - k0; ++j, from ^= 1)
+      TAPE_CUDA(t, lbm::launch_step2d_store_w<T>(replay_args<T>(h, t, from), kd, W + 3 * P * j, st), "replay step");
+    // adjoint steps n = k1 .. k0 + 1 (FP32 periodic: k reverse steps per launch while the
+    // segment's stored moments cover them)
     for (int n = k1; n > k0; --n) {
+      if constexpr (sizeof(T) == 4) {
+        const int k = h->temporal_k;
+        lbm::StepArgs<float> a = lbm::handle_args<float>(h, 0);
+        a.src = static_cast<const float*>(t->phi[cur]);
+        a.dst = static_cast<float*>(t->phi[1 - cur]);
+        if (h->kernel == LBM_SW_KERNEL_TEMPORAL && k > 1 && n - k0 >= k && lbm::adjoint_temporal_supported(a, k)) {
+          TAPE_CUDA(t, lbm::launch_adjoint_temporal(a, W + 3 * P * (n - 1 - k0), 3 * P, kd, k, st, h->sm_count),
+                    "adjoint launch");
+          cur ^= 1;
+          n -= k - 1;  // with the loop's decrement: n -= k
+          continue;
+        }
+      }
       lbm::AdjArgs<T> A;
       A.phi_in = static_cast<const T*>(t->phi[cur]);
       A.phi_out = static_cast<T*>(t->phi[1 - cur]);
@@ -486,18 +487,25 @@ int lbm_sw_tape_create(lbm_sw* h, int steps, int interval, lbm_sw_tape** out) {
   t->owner = h;
   t->steps = steps;
   t->interval = interval ? interval : static_cast<int>(std::ceil(std::sqrt(static_cast<double>(steps))));
+  if (!interval && h->kernel == LBM_SW_KERNEL_TEMPORAL && h->p.precision == LBM_SW_FP32 && h->temporal_k > 1) {
+    // a whole number of fused launches per interval
+    const int k = h->temporal_k;
+    t->interval = std::min(steps, (t->interval + k - 1) / k * k);
+  }
   t->checkpoints = (steps + t->interval - 1) / t->interval;
+  // a replay that fuses k steps per launch may run up to k - 1 steps past its segment
+  t->wslots = t->interval + (h->kernel == LBM_SW_KERNEL_TEMPORAL && h->p.precision == LBM_SW_FP32 ? h->temporal_k : 0);
   t->state_elems = static_cast<size_t>(13) * h->plane;
   const size_t n = static_cast<size_t>(h->p.nx) * h->p.ny;
   bool ok = cudaMalloc(&t->ckpt, sizeof(double) * t->state_elems * t->checkpoints) == cudaSuccess &&
-            cudaMalloc(&t->wstore, h->elem * 3 * h->plane * t->interval) == cudaSuccess &&
+            cudaMalloc(&t->wstore, h->elem * 3 * h->plane * t->wslots) == cudaSuccess &&
             cudaMalloc(&t->grad_staging, sizeof(double) * 3 * n) == cudaSuccess;
   for (int i = 0; i < 2 && ok; ++i)
     ok = cudaMalloc(&t->phi[i], h->elem * t->state_elems) == cudaSuccess &&
          cudaMemsetAsync(t->phi[i], 0, h->elem * t->state_elems, h->stream) == cudaSuccess &&
          cudaMalloc(&t->rep[i], h->elem * t->state_elems) == cudaSuccess &&
          cudaMemsetAsync(t->rep[i], 0, h->elem * t->state_elems, h->stream) == cudaSuccess;
-  if (ok) ok = cudaMemsetAsync(t->wstore, 0, h->elem * 3 * h->plane * t->interval, h->stream) == cudaSuccess;
+  if (ok) ok = cudaMemsetAsync(t->wstore, 0, h->elem * 3 * h->plane * t->wslots, h->stream) == cudaSuccess;
   if (!ok) {
     h->err = std::string("tape_create: device allocation failed: ") + cudaGetErrorString(cudaGetLastError());
     lbm_sw_tape_destroy(t);
@@ -513,17 +521,19 @@ int lbm_sw_forward_record(lbm_sw* h, lbm_sw_tape* t) {
   if (!h->has_state) return tfail(t, LBM_SW_E_STATE, "forward_record: the handle has no state");
   if (h->mrt || h->has_obstacles)
     return tfail(t, LBM_SW_E_ARG, "forward_record: the adjoint supports BGK without obstacles only");
-  for (int k = 0; k < t->steps; ++k) {
-    if (k % t->interval == 0) {
-      double* dst = t->ckpt + static_cast<size_t>(k / t->interval) * t->state_elems;
-      cudaError_t e = h->p.precision == LBM_SW_FP64
-                          ? lbm::launch_convert<double, double>(static_cast<const double*>(h->buf[h->cur]), dst,
-                                                                static_cast<long long>(t->state_elems), h->stream)
-                          : lbm::launch_convert<float, double>(static_cast<const float*>(h->buf[h->cur]), dst,
-                                                               static_cast<long long>(t->state_elems), h->stream);
-      TAPE_CUDA(t, e, "checkpoint store");
-    }
-    const int rc = lbm_sw_step(h, 1);
+  // one lbm_sw_step call per checkpoint interval, so long intervals take the handle's
+  // temporal blocking (bit-identical to single steps)
+  for (int seg = 0; seg < t->checkpoints; ++seg) {
+    const int k0 = seg * t->interval;
+    double* dst = t->ckpt + static_cast<size_t>(seg) * t->state_elems;
+    cudaError_t e = h->p.precision == LBM_SW_FP64
+                        ? lbm::launch_convert<double, double>(static_cast<const double*>(h->buf[h->cur]), dst,
+                                                              static_cast<long long>(t->state_elems), h->stream)
+                        : lbm::launch_convert<float, double>(static_cast<const float*>(h->buf[h->cur]), dst,
+                                                             static_cast<long long>(t->state_elems), h->stream);
+    TAPE_CUDA(t, e, "checkpoint store");
+    const int len = std::min(t->interval, t->steps - k0);
+    const int rc = lbm_sw_step(h, len);
     if (rc != LBM_SW_OK) return tfail(t, rc, "forward_record: %s", h->err.c_str());
   }
   t->recorded = true;
@@ -572,7 +582,7 @@ int lbm_sw_tape_get_info(const lbm_sw_tape* t, lbm_sw_tape_info* out) {
   out->checkpoints = t->checkpoints;
   out->recorded = t->recorded ? 1 : 0;
   out->checkpoint_bytes = sizeof(double) * t->state_elems * t->checkpoints;
-  out->replay_bytes = t->owner->elem * (3 * t->owner->plane * t->interval + 4 * t->state_elems);
+  out->replay_bytes = t->owner->elem * (3 * t->owner->plane * t->wslots + 4 * t->state_elems);
   return LBM_SW_OK;
 }
 

@@ -59,6 +59,13 @@ cudaError_t launch_moments2d_planes(const StepArgs<T>& a, T* w_out, cudaStream_t
 template <class Tin, class Tout>
 cudaError_t launch_convert(const Tin* in, Tout* out, long long n, cudaStream_t st);
 
+// K reverse steps of the discrete adjoint per launch (temporal.cu; FP32, every side periodic,
+// k in {2, 4, 6, 8}): Phi^{n0} in a.src -> Phi^{n0 - k} in a.dst; reverse step t reads the
+// moments W^{n0 - t} at w0 - (t - 1) * wslot.
+bool adjoint_temporal_supported(const StepArgs<float>& a, int k);
+cudaError_t launch_adjoint_temporal(const StepArgs<float>& a, const float* w0, long long wslot, const ConstsD& kd,
+                                    int k, cudaStream_t st, int sm_count);
+
 // Batched temporal blocking (temporal.cu): one wavefront unit covers rows [ys, ye) of the
 // output columns [x0, x0 + w) of one instance (clipped at nx) of a batch whose sides are
 // all periodic; a work list holds the units of every instance, grouped by CTA.
@@ -88,6 +95,11 @@ cudaError_t launch_batch_temporal(const BatchWaves& w, int k, const float* src, 
 
 // k fused steps per launch (temporal.cu; FP32, BGK; k in 2 .. 8): src -> dst.
 bool temporal_steps_supported(int k);
+// k fused steps that also write the moments of every level t = 1 .. k, for every cell, to
+// the three planes at wout + (t - 1) * wslot (every side periodic, even nx, even k).
+bool temporal_store_w_supported(const StepArgs<float>& a, int k);
+cudaError_t launch_step2d_temporal_store_w(const StepArgs<float>& a, const ConstsD& kd, int k, float* wout,
+                                           long long wslot, cudaStream_t st, int sm_count);
 cudaError_t launch_step2d_temporal(const StepArgs<float>& a, const ConstsD& kd, int k, cudaStream_t st,
                                    int sm_count);
 

@@ -188,6 +188,32 @@ __device__ __forceinline__ void collide13_any(T f[13], const Consts<T>& k, T& h,
     collide13(f, k, h, qx, qy);
 }
 
+// z = D(W)^T psi: vector-Jacobian product of the equilibria (closed forms of section 3
+// in W = (h, qx, qy); kappa = h/2 - (qx^2 + qy^2)/(4 g h^2), c = 1/(2 lambda)).
+template <class T>
+__device__ __forceinline__ void equilibrium_vjp(T h, T qx, T qy, const T psi[13], const Consts<T>& K, T& zh,
+                                                T& zx, T& zy) {
+  const T rh = T(1) / h;
+  const T u = qx * rh, v = qy * rh;
+  const T gh = T(2) * K.half_g * h;
+  const T inv2gh = T(2) * K.inv4g * rh;
+  const T kh = T(0.5) + (u * u + v * v) * inv2gh;  // dkappa/dh
+  const T kx = -u * inv2gh;                        // dkappa/dqx
+  const T ky = -v * inv2gh;                        // dkappa/dqy
+  const T Sf = (psi[1] + psi[3]) + (psi[2] + psi[4]);
+  const T Af = psi[0] - T(0.25) * Sf;
+  const T Df13 = psi[1] - psi[3], Df24 = psi[2] - psi[4];
+  const T Sx = (psi[5] + psi[7]) + (psi[6] + psi[8]);
+  const T Dx13 = psi[5] - psi[7], Dx24 = psi[6] - psi[8];
+  const T Sy = (psi[9] + psi[11]) + (psi[10] + psi[12]);
+  const T Dy13 = psi[9] - psi[11], Dy24 = psi[10] - psi[12];
+  const T X = Dx24 + Dy13;
+  const T c = K.c;
+  zh = K.a * kh * Af + T(0.25) * Sf + c * (Dx13 * (gh - u * u) - X * u * v + Dy24 * (gh - v * v));
+  zx = K.a * kx * Af + c * Df13 + T(0.25) * Sx + c * (T(2) * Dx13 * u + X * v);
+  zy = K.a * ky * Af + c * Df24 + T(0.25) * Sy + c * (X * u + T(2) * Dy24 * v);
+}
+
 // ---- Two FP32 cells at once (the paired FP32 instructions of sm_100 and later) ----
 // The same operations as collide13, in the same order, on (cell a, cell b) pairs, so each
 // lane rounds exactly like the scalar code and the results are equal bit for bit.  The code
@@ -224,12 +250,13 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
-__device__ __forceinline__ void collide13x2(float2 f[13], const Consts<float>& k) {
+// (h, qx, qy) receive the conserved moments of the pulled populations (as collide13's).
+__device__ __forceinline__ void collide13x2(float2 f[13], const Consts<float>& k, float2& h, float2& qx, float2& qy) {
   const float2 nz = dup2(k.nz);
   auto mul2 = [&](float2 a, float2 b) { return fma2(a, b, nz); };  // the rounded product a b
-  const float2 h = add2(f[0], add2(add2(f[1], f[3]), add2(f[2], f[4])));
-  const float2 qx = add2(add2(f[5], f[7]), add2(f[6], f[8]));
-  const float2 qy = add2(add2(f[9], f[11]), add2(f[10], f[12]));
+  h = add2(f[0], add2(add2(f[1], f[3]), add2(f[2], f[4])));
+  qx = add2(add2(f[5], f[7]), add2(f[6], f[8]));
+  qy = add2(add2(f[9], f[11]), add2(f[10], f[12]));
   const float2 rh = make_float2(recip(h.x), recip(h.y));
   const float2 u = mul2(qx, rh);
   const float2 v = mul2(qy, rh);
@@ -263,6 +290,11 @@ __device__ __forceinline__ void collide13x2(float2 f[13], const Consts<float>& k
   const float2 s = dup2(k.s);
 #pragma unroll
   for (int j = 0; j < 13; ++j) f[j] = fma2(s, sub2(e[j], f[j]), f[j]);
+}
+
+__device__ __forceinline__ void collide13x2(float2 f[13], const Consts<float>& k) {
+  float2 h, qx, qy;
+  collide13x2(f, k, h, qx, qy);
 }
 
 // ---- 1D: populations f0, f+, f-, g+, g- ----

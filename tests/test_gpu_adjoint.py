@@ -44,9 +44,10 @@ def _oracle_directional(W0, dW, steps, p, h_obs):
     return L.imag / eps
 
 
-def _gpu_gradient(W0, steps, h_obs, *, precision, bc=(P,) * 4, interval=0):
+def _gpu_gradient(W0, steps, h_obs, *, precision, bc=(P,) * 4, interval=0, kernel=lbm_sw.KERNEL_AUTO):
     ny, nx = W0[0].shape
-    with lbm_sw.Simulation(nx, ny, precision=precision, bc=bc, inflow=INFLOW, stream=torch_stream()) as sim:
+    with lbm_sw.Simulation(nx, ny, precision=precision, bc=bc, inflow=INFLOW, stream=torch_stream(),
+                           kernel=kernel) as sim:
         sim.set_state(*W0)
         with lbm_sw.Tape(sim, steps, interval) as tape:
             tape.record()
@@ -141,7 +142,10 @@ def test_inverse_problem_workload_1024():
     h_obs = _oracle_hT((h_true, z, z), steps, p)
     (g64, _, _), _, _ = _gpu_gradient((h_guess, z, z), steps, h_obs, precision=lbm_sw.FP64)
     (g32, _, _), _, info = _gpu_gradient((h_guess, z, z), steps, h_obs, precision=lbm_sw.FP32)
-    assert info.checkpoints == 14 and info.checkpoint_bytes == 14 * 13 * 1024 * 1024 * 8
+    # the FP32 handle fuses 4 steps per launch: the default interval ceil(sqrt(200)) = 15 is
+    # rounded up to 16, so 13 checkpoints
+    assert info.interval == 16 and info.checkpoints == 13
+    assert info.checkpoint_bytes == 13 * 13 * 1024 * 1024 * 8
     assert np.linalg.norm(g32 - g64) <= 2e-3 * np.linalg.norm(g64)
     d = inputs.uniform(77, n * n, -1, 1).reshape(n, n)
     want = _oracle_directional((h_guess, z, z), (d, z, z), steps, p, h_obs)
@@ -199,3 +203,25 @@ def test_vector_adjoint_equals_scalar_adjoint(nx, ny, bc, precision):
     tol = 1e-13 if precision == lbm_sw.FP64 else 1e-5
     for ga, gb in zip(a, b):
         assert np.abs(ga - gb).max() <= tol * max(np.abs(ga).max(), 1e-30)
+
+
+def test_fused_launches_give_the_same_fp32_gradient():
+    """1024 x 1024 periodic FP32: the default handle fuses 4 steps per launch in the forward
+    run, in the segment replays (whose kernel also stores every level's moments) and in the
+    adjoint steps (a reverse wavefront of the same shape); a handle held to one step per launch
+    gives the same gradient, with intervals of 16 (fused launches only) and 15 (fused launches
+    and single steps).  The forward run and the replays are bit-identical; the two adjoint
+    kernels evaluate the same plain-arithmetic expressions, whose contraction into fused
+    multiply-adds the compiler may choose per kernel, so they agree to FP32 rounding."""
+    n, steps = 1024, 48
+    h_true, h_guess = _workload(n)
+    z = np.zeros((n, n))
+    p = oracle.params(n, n, a=0.05)
+    h_obs = _oracle_hT((h_true, z, z), steps, p)
+    for interval in (16, 15):
+        fused, hT_f, _ = _gpu_gradient((h_guess, z, z), steps, h_obs, precision=lbm_sw.FP32, interval=interval)
+        single, hT_s, _ = _gpu_gradient((h_guess, z, z), steps, h_obs, precision=lbm_sw.FP32, interval=interval,
+                                        kernel=lbm_sw.KERNEL_VEC)
+        assert np.array_equal(hT_f, hT_s)
+        for a, b in zip(fused, single):
+            assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max(), interval

@@ -206,6 +206,62 @@ def cpu_oracle_mlups(W0, target_seconds: float = 15.0, max_steps: int = 120):
                       f"({dt:.1f} s, OpenMP over rows)"}
 
 
+def _time_oracle(fn, min_seconds: float = 0.5):
+    """Run fn() until min_seconds have passed; return (calls, seconds)."""
+    calls, t0 = 0, time.perf_counter()
+    while True:
+        fn()
+        calls += 1
+        dt = time.perf_counter() - t0
+        if dt >= min_seconds:
+            return calls, dt
+
+
+def cpu_oracle_configs():
+    """The FP64 oracle on the other workloads, each on a bounded sample, on one core and on
+    every core (MLUPS = cells x steps / s of oracle time)."""
+    import oracle
+    from paper_1401_0427_gb300 import inputs
+
+    out = {}
+    all_cores = oracle.set_threads(0)
+    cases = []
+    # 1D shock tube: the whole 1000-cell, 500-step run
+    p1 = oracle.params(1000, a=0.15, lam=LAM, s=S_RATE, bc=(oracle.WALL, oracle.WALL))
+    h, q = inputs.dam_break_1d(1000)
+    F1 = oracle.equilibrium_1d(h, q, p1)
+    cases.append(("shock_tube_1d_1000", 1000 * 500, lambda: oracle.run_1d(F1, 500, p1),
+                  "the whole run: 1000 cells x 500 steps"))
+    # 2D shock reflection 512^2: 20 of its 2000 steps
+    n = 512
+    uL = inputs.shock_speed_state(2.0, 1.0)
+    p2 = oracle.params(n, n, lam=LAM, s=S_RATE, a=A_REST, bc=(oracle.INFLOW, oracle.WALL, oracle.PERIODIC, oracle.PERIODIC),
+                       inflow=[(2.0, 2.0 * uL, 0.0)] * 4)
+    F2 = oracle.equilibrium_2d(*inputs.planar_shock_2d(n, n), p2)
+    cases.append(("shock_reflection_512", n * n * 20, lambda: oracle.run_2d(F2, 20, p2),
+                  "20 of the 2000 steps on the full 512x512 grid"))
+    # batched ensemble: 8 of the 256 instances (every 32nd), 10 steps
+    table = inputs.batched_instances(256)[::32]
+    bstates = []
+    for k, hin, r in table:
+        pb = oracle.params(k, k, lam=LAM, s=S_RATE, a=A_REST)
+        bstates.append((pb, oracle.equilibrium_2d(*inputs.circular_dam_break_2d(k, seed=None, h_in=hin, radius=r), pb)))
+    bcells = sum(k * k for k, _, _ in table)
+    cases.append(("batched_256", bcells * 10, lambda: [oracle.run_2d(F, 10, pb) for pb, F in bstates],
+                  f"every 32nd of the 256 instances ({bcells} cells), 10 steps each"))
+    for name, lups, fn, sample in cases:
+        entry = {"sample": sample, "unit": UNIT, "kind": "oracle"}
+        for label, threads in (("one_core", 1), ("all_cores", 0)):
+            cores = oracle.set_threads(threads)
+            calls, dt = _time_oracle(fn)
+            entry[label] = {"MLUPS": lups * calls / dt / 1e6, "cores": cores}
+        out[name] = entry
+    oracle.set_threads(all_cores)
+    out["adjoint_1024"] = {"sample": "none: the oracle has no adjoint; its complex-step derivative gives one "
+                                     "directional derivative per run, not a gradient"}
+    return out
+
+
 def run_reference(args, world, rank):
     """The oracle on the host cores: each bench step advances a 512x512 periodic window
     of the workload's initial field by one step (a bounded sample of the workload)."""
@@ -338,6 +394,16 @@ def run_ours(args, world, rank, local):
         result["e2e"] = end_to_end(W0, stream, lbm_sw, torch)
     if rank == 0 and not args.quick and not args.skip_cpu:
         result["cpu_baseline"] = cpu_oracle_mlups(W0)
+        import oracle
+
+        threads = oracle.set_threads(1)
+        p512 = oracle.params(512, 512, lam=LAM, s=S_RATE, a=A_REST)
+        F1 = oracle.equilibrium_2d(*(np.ascontiguousarray(x[:512, :512]) for x in W0), p512)
+        calls, dt = _time_oracle(lambda: oracle.run_2d(F1, 2, p512), 2.0)
+        result["cpu_baseline"]["one_core"] = {"MLUPS": 512 * 512 * 2 * calls / dt / 1e6, "cores": threads,
+                                              "sample": "a 512x512 periodic corner of the workload, 2 steps a call"}
+        oracle.set_threads(0)
+        result["cpu_baseline_configs"] = cpu_oracle_configs()
     if rank == 0:
         print(json.dumps(result))
     if world > 1:

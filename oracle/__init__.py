@@ -132,7 +132,10 @@ def lib() -> ctypes.CDLL:
 
 
 def set_threads(n: int = 0) -> int:
-    """Set the OpenMP thread count (n <= 0 keeps it); returns the count in use."""
+    """Set the OpenMP thread count (n <= 0: every core this process may run on); returns the
+    count in use."""
+    if n <= 0:
+        n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     return lib().oracle_set_threads(int(n))
 
 

@@ -162,26 +162,33 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(world, value: float) -> float:
+def _all_reduce(world, value: float, op: str) -> float:
+    """value reduced over the ranks (op "max" or "sum"); on the process group's device (CUDA
+    for NCCL, host memory for gloo)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def max_over_ranks(world, value: float) -> float:
+    return _all_reduce(world, value, "max")
 
 
 def sum_over_ranks(world, value: float) -> float:
-    if world == 1:
-        return value
-    import torch
-    import torch.distributed as dist
+    return _all_reduce(world, value, "sum")
 
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+
+def job_throughput(world, units: float, ms: float) -> tuple[float, float]:
+    """Whole-job throughput of replicas: the units of every rank over the slowest rank's time.
+    Returns (value in units per microsecond, max time in ms)."""
+    slowest = max_over_ranks(world, ms)
+    return sum_over_ranks(world, units) / (slowest * 1e-3) / 1e6, slowest
 
 
 # ----------------------------------------------------------------- CPU oracle
@@ -356,9 +363,8 @@ def run_ours(args, world, rank, local):
     total_ms = events[0].elapsed_time(events[-1])
     per_launch = [events[i].elapsed_time(events[i + 1]) for i in range(nfull)]
     launches = sim.info().kernel_launches - launches0 - warm_launches
-    total_ms = max_over_ranks(world, total_ms)
+    value, total_ms = job_throughput(world, cells * args.steps, total_ms)
     diag = sim.diagnostics()
-    value = sum_over_ranks(world, cells * args.steps) / (total_ms * 1e-3) / 1e6
 
     avg_launch_s = float(np.mean(per_launch)) * 1e-3
     peak, peak_kind = measured_peaks()

@@ -126,7 +126,7 @@ typedef struct lbm_sw_params {
   void* stream;        /* cudaStream_t borrowed from the caller (NULL = legacy default) */
   int kernel;          /* LBM_SW_KERNEL_*: AUTO, SIMPLE, VEC or TEMPORAL (2D), CLUSTER (1D) */
   int graph_chunk;     /* steps per captured CUDA graph in lbm_sw_step; 0 = default, < 0 = off */
-  int temporal_steps;  /* steps fused per launch by the TEMPORAL kernel: 2 .. 8; 0 = default (4) */
+  int temporal_steps;  /* steps fused per launch by the TEMPORAL kernel: 2 .. 8; 0 = default (6) */
   int reserved[5];     /* must be zero */
 } lbm_sw_params;
 

@@ -214,7 +214,7 @@ int lbm_sw_create(const lbm_sw_params* p, lbm_sw** out) {
   } else {
     h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? LBM_SW_KERNEL_CLUSTER : p->kernel;
   }
-  h->temporal_k = p->temporal_steps ? p->temporal_steps : 4;
+  h->temporal_k = p->temporal_steps ? p->temporal_steps : 6;
   h->graph_chunk = p->graph_chunk == 0 ? 64 : (p->graph_chunk < 0 ? 0 : p->graph_chunk + (p->graph_chunk & 1));
 
   auto bail = [&](int code) {

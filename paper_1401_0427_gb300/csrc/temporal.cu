@@ -375,25 +375,39 @@ __global__ void __launch_bounds__(COLS, COLS == 192 ? 2 : (K <= 4 ? 5 : 3))
 // the row (the cells that read it lie outside the level's valid range and are never used).
 // Input pairs land by 8-byte cp.async, which needs even nx and K: then every strip starts
 // at an even column, has an even width, and no pair straddles the periodic seam.
-template <int K, int COLS, int PF>
+template <int K, int COLS, int PF, bool L0R = false>
 struct PairShape {
   static constexpr int RS = COLS + 4;  // floats per plane row
-  // input ring per plane group: the row read now, the rows landed but not yet read by this
-  // group, and PF rows in flight
-  static constexpr int A0 = 1 + PF, B0 = 2 + PF, C0 = 3 + PF;
-  static constexpr int L0_FLOATS = RS * (3 * A0 + 7 * B0 + 3 * C0);
+  // Input ring per plane group: the row read now, the rows landed but not yet read by this
+  // group, and PF rows in flight.  Groups: the -y movers (read in the landing iteration),
+  // f0 and the x movers (one iteration later), the +y movers (two later).  With L0R, f0 and
+  // the +y movers go to registers when their row lands, so only the x movers wait in
+  // shared memory: groups -y movers [1 + PF][3], x movers [2 + PF][6], f0 and +y movers
+  // [1 + PF][4].
+  static constexpr int A0 = 1 + PF, B0 = 2 + PF, C0 = L0R ? 1 + PF : 3 + PF;
+  static constexpr int BP = L0R ? 6 : 7, CP = L0R ? 4 : 3;  // planes per row of groups B, C
+  static constexpr int L0_FLOATS = RS * (3 * A0 + BP * B0 + CP * C0);
   static constexpr int LV_FLOATS = RS * 2 * 6;
   static constexpr size_t floats() { return static_cast<size_t>(L0_FLOATS) + (K - 1) * LV_FLOATS; }
 };
 
+// Input plane p -> (group, index) in the L0R layout: 0 = {4, 8, 12}, 1 = x movers
+// {1, 3, 5, 7, 9, 11}, 2 = {0, 2, 6, 10}.
+__host__ __device__ constexpr int reg_group(int p) {
+  return (p == 4 || p == 8 || p == 12) ? 0 : ((p == 0 || p == 2 || p == 6 || p == 10) ? 2 : 1);
+}
+__host__ __device__ constexpr int reg_index(int p) {
+  return reg_group(p) == 0 ? (p - 4) / 4 : (reg_group(p) == 1 ? (p - 1) / 2 : (p == 0 ? 0 : (p - 2) / 4 + 1));
+}
+
 // With STORE_W, the moments (h, hu, hv) of every time level t = 1 .. K are also written, for
 // the launch's output cells, to the three planes at wout + (t - 1) * wslot (the replay of the
 // discrete adjoint keeps the moments of every step).
-template <int K, int COLS, int PF, bool STORE_W = false>
+template <int K, int COLS, int PF, bool STORE_W = false, bool L0R = false>
 __global__ void __launch_bounds__(COLS / 2, 2)
     step2d_temporal_periodic_x2(const StepArgs<float> A, const Consts<float> Kc, const Partition P,
                                 float* __restrict__ wout = nullptr, long long wslot = 0) {
-  using S = PairShape<K, COLS, PF>;
+  using S = PairShape<K, COLS, PF, L0R>;
   constexpr int RS = S::RS;
   extern __shared__ __align__(16) float smem[];
   const int c = threadIdx.x;  // pair index: tile columns 2c, 2c + 1
@@ -402,10 +416,12 @@ __global__ void __launch_bounds__(COLS / 2, 2)
 
   float* const l0a = smem;
   float* const l0b = l0a + S::A0 * 3 * RS;
-  float* const l0c = l0b + S::B0 * 7 * RS;
+  float* const l0c = l0b + S::B0 * S::BP * RS;
   auto xm = [&](int t, int slot) { return smem + S::L0_FLOATS + (t - 1) * S::LV_FLOATS + slot * 6 * RS; };
   auto ld2 = [](const float* q) { return *reinterpret_cast<const float2*>(q); };
   auto st2 = [](float* q, float2 v) { *reinterpret_cast<float2*>(q) = v; };
+  auto grp = [](int p) { return L0R ? reg_group(p) : plane_group(p); };
+  auto idx = [](int p) { return L0R ? reg_index(p) : plane_index(p); };
 
   run_segment(P, ny, [&](int strip, int ys, int ye) {
     const int gx_raw = strip * P.w - K + col;
@@ -427,12 +443,12 @@ __global__ void __launch_bounds__(COLS / 2, 2)
         const int gr = ((r % ny) + ny) % ny;
         const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
         float* sa = l0a + (j % S::A0) * 3 * RS + col + 2;
-        float* sb = l0b + (j % S::B0) * 7 * RS + col + 2;
-        float* sc = l0c + (j % S::C0) * 3 * RS + col + 2;
+        float* sb = l0b + (j % S::B0) * S::BP * RS + col + 2;
+        float* sc = l0c + (j % S::C0) * S::CP * RS + col + 2;
 #pragma unroll
         for (int p = 0; p < 13; ++p) {
-          float* d = plane_group(p) == 0 ? sa : (plane_group(p) == 1 ? sb : sc);
-          __pipeline_memcpy_async(d + plane_index(p) * RS, g + p * A.plane, 2 * sizeof(float));
+          float* d = grp(p) == 0 ? sa : (grp(p) == 1 ? sb : sc);
+          __pipeline_memcpy_async(d + idx(p) * RS, g + p * A.plane, 2 * sizeof(float));
         }
       }
       __pipeline_commit();
@@ -443,6 +459,14 @@ __global__ void __launch_bounds__(COLS / 2, 2)
     for (int j = 0; j < iters; ++j) {
       __pipeline_wait_prior(PF - 1);  // row j has landed (this thread's copies)
       __syncthreads();                // ... and every thread's; iteration j - 1 is over everywhere
+      if (L0R) {
+        // f0 and the +y movers of the row just landed, into registers (read by level 1 one
+        // and two iterations later)
+        const float* rf = l0c + (j % S::C0) * S::CP * RS + col + 2;
+        f0_now[0] = ld2(rf);
+#pragma unroll
+        for (int fam = 0; fam < 3; ++fam) c_now[0][fam] = ld2(rf + (1 + fam) * RS);
+      }
       issue_row(j + PF);
 #pragma unroll
       for (int t = 1; t <= K; ++t) {
@@ -450,7 +474,20 @@ __global__ void __launch_bounds__(COLS / 2, 2)
         const bool row_ok = R >= ys - K + t && R < ye + K - t;
         if (row_ok && col + 1 >= t && col < P.w + 2 * K - t) {
           float2 f[13];
-          if (t == 1) {
+          if (t == 1 && L0R) {
+            const float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;                 // row R + 1
+            const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 6 * RS + col + 2;  // row R
+            f[0] = f0_prev[0];
+#pragma unroll
+            for (int fam = 0; fam < 3; ++fam) {
+              const float* px = rb + (2 * fam) * RS;      // +x movers from columns 2c - 1, 2c
+              const float* mx = rb + (2 * fam + 1) * RS;  // -x movers from columns 2c + 1, 2c + 2
+              f[1 + 4 * fam] = make_float2(px[-1], px[0]);
+              f[2 + 4 * fam] = c_prev2[0][fam];
+              f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
+              f[4 + 4 * fam] = ld2(ra + fam * RS);
+            }
+          } else if (t == 1) {
             const float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;
             const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 7 * RS + col + 2;
             const float* rc = l0c + ((j + S::C0 - 2) % S::C0) * 3 * RS + col + 2;
@@ -501,7 +538,7 @@ __global__ void __launch_bounds__(COLS / 2, 2)
             for (int p = 0; p < 13; ++p) st2(g + p * A.plane, f[p]);
           }
         }
-        if (t > 1) {
+        if (t > 1 || L0R) {
           f0_prev[t - 1] = f0_now[t - 1];
 #pragma unroll
           for (int fam = 0; fam < 3; ++fam) {
@@ -568,10 +605,10 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
 }
 
 // The paired periodic kernel: COLS tile columns, COLS / 2 threads, w even.
-template <int K, int COLS, int PF>
+template <int K, int COLS, int PF, bool L0R = false>
 cudaError_t launch_k_pairs(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t st, int sm_count) {
-  const size_t smem = PairShape<K, COLS, PF>::floats() * sizeof(float);
-  const void* fn = reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF>);
+  const size_t smem = PairShape<K, COLS, PF, L0R>::floats() * sizeof(float);
+  const void* fn = reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF, false, L0R>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   static int resident = 0;
@@ -581,7 +618,7 @@ cudaError_t launch_k_pairs(const StepArgs<float>& a, const ConstsD& kd, cudaStre
   P.strips = (a.nx + P.w - 1) / P.w;
   const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
   const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
-  step2d_temporal_periodic_x2<K, COLS, PF><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q);
+  step2d_temporal_periodic_x2<K, COLS, PF, false, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q);
   return cudaGetLastError();
 }
 
@@ -607,12 +644,16 @@ cudaError_t launch_k_pairs_w(const StepArgs<float>& a, const ConstsD& kd, float*
 template <int K>
 cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t st, int sm_count) {
   const bool per = a.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC && a.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
-  // paired kernel (even nx and K): 256 columns and two rows of prefetch up to K = 4; above,
-  // 192 columns and one row of prefetch keep two CTAs per SM within the shared memory
+  // paired kernel (even nx and K), the measured best at each K: 256 columns and two rows of
+  // prefetch up to K = 4; at K = 6, 256 columns, one row of prefetch and the input row's f0
+  // and +y movers in registers (two CTAs per SM); at K = 8, 192 columns and one row of
+  // prefetch
   if constexpr (K % 2 == 0) {
     if (per && a.nx % 2 == 0) {
       if constexpr (K <= 4)
         return launch_k_pairs<K, 256, 2>(a, kd, st, sm_count);
+      else if constexpr (K == 6)
+        return launch_k_pairs<K, 256, 1, true>(a, kd, st, sm_count);
       else
         return launch_k_pairs<K, 192, 1>(a, kd, st, sm_count);
     }

@@ -142,10 +142,10 @@ def test_inverse_problem_workload_1024():
     h_obs = _oracle_hT((h_true, z, z), steps, p)
     (g64, _, _), _, _ = _gpu_gradient((h_guess, z, z), steps, h_obs, precision=lbm_sw.FP64)
     (g32, _, _), _, info = _gpu_gradient((h_guess, z, z), steps, h_obs, precision=lbm_sw.FP32)
-    # the FP32 handle fuses 4 steps per launch: the default interval ceil(sqrt(200)) = 15 is
-    # rounded up to 16, so 13 checkpoints
-    assert info.interval == 16 and info.checkpoints == 13
-    assert info.checkpoint_bytes == 13 * 13 * 1024 * 1024 * 8
+    # the FP32 handle fuses 6 steps per launch forward and 4 in the replay: the default
+    # interval ceil(sqrt(200)) = 15 is rounded up to 24, so 9 checkpoints
+    assert info.interval == 24 and info.checkpoints == 9
+    assert info.checkpoint_bytes == 9 * 13 * 1024 * 1024 * 8
     assert np.linalg.norm(g32 - g64) <= 2e-3 * np.linalg.norm(g64)
     d = inputs.uniform(77, n * n, -1, 1).reshape(n, n)
     want = _oracle_directional((h_guess, z, z), (d, z, z), steps, p, h_obs)

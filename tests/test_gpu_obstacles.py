@@ -58,14 +58,14 @@ def test_graph_replay_removal_and_temporal_default():
     out = []
     for graph_chunk in (-1, 16):
         with lbm_sw.Simulation(n, n, stream=torch_stream(), graph_chunk=graph_chunk) as sim:
-            assert sim.info().kernel == lbm_sw.KERNEL_TEMPORAL and sim.info().steps_per_launch == 4
+            assert sim.info().kernel == lbm_sw.KERNEL_TEMPORAL and sim.info().steps_per_launch == 6
             sim.set_state(*W0)
             sim.set_obstacle(solid)
             assert sim.info().steps_per_launch == 1
             sim.step(40)
             out.append(sim.populations())
             sim.set_obstacle(None)
-            assert sim.info().steps_per_launch == 4
+            assert sim.info().steps_per_launch == 6
             sim.step(12)
             out.append(sim.populations())
     assert np.array_equal(out[0], out[2]) and np.array_equal(out[1], out[3])

@@ -3,8 +3,8 @@ one-step-per-launch kernel: every cell update is the same pull + collide, so the
 must be equal bit for bit, on ragged grids (a strip holds up to 128 - 2K output columns
 with walls, inflow or outflow, and 192 - 2K or 256 - 2K on all-periodic domains, where even
 widths and even K take the kernel that updates two columns per thread with paired FP32
-instructions), with every boundary kind, for step counts that leave a remainder, and on
-the 4096^2 dam-break."""
+instructions, at K = 6 with the input row's non-shifting planes in registers), with every
+boundary kind, for step counts that leave a remainder, and on the 4096^2 dam-break."""
 
 import numpy as np
 import pytest
@@ -66,14 +66,14 @@ def test_auto_kernel_choice(nx, ny, bc, precision, want):
 
 
 def test_auto_temporal_counts_launches_and_steps():
-    """AUTO on a periodic 1024^2 FP32 grid: 4 steps per launch, the remainder one per launch."""
+    """AUTO on a periodic 1024^2 FP32 grid: 6 steps per launch, the remainder one per launch."""
     W0 = inputs.circular_dam_break_2d(1024, seed=inputs.stream_seed(3))
     with lbm_sw.Simulation(1024, 1024, stream=torch_stream()) as sim:
         sim.set_state(*W0)
         before = sim.info().kernel_launches
         sim.step(22)
         info = sim.info()
-        assert info.steps_done == 22 and info.steps_per_launch == 4 and info.kernel_launches - before == 5 + 2
+        assert info.steps_done == 22 and info.steps_per_launch == 6 and info.kernel_launches - before == 3 + 4
 
 
 @pytest.mark.parametrize("nx,ny", [(2, 3), (4, 4), (10, 7), (244, 5), (246, 9), (488, 20), (490, 33), (1024, 130)])

@@ -79,10 +79,16 @@ struct WaveUnit {
   int pad;
 };
 struct BatchWaves {
+  // units of odd-width instances (one column per thread) and, for even K, of even-width
+  // instances (two columns per thread); each list balanced over its own wave of CTAs
   WaveUnit* units = nullptr;  // device
   int* first = nullptr;       // device, grid + 1 entries: CTA b runs units [first[b], first[b + 1])
   int count = 0;
   int grid = 0;
+  WaveUnit* punits = nullptr;
+  int* pfirst = nullptr;
+  int pcount = 0;
+  int pgrid = 0;
 };
 // Build the work list of k-step wavefronts for the given instances (host arrays of count
 // entries) on the current device; free with batch_waves_free.

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <functional>
 #include <queue>
 #include <utility>
@@ -403,13 +405,11 @@ __host__ __device__ constexpr int reg_index(int p) {
 // With STORE_W, the moments (h, hu, hv) of every time level t = 1 .. K are also written, for
 // the launch's output cells, to the three planes at wout + (t - 1) * wslot (the replay of the
 // discrete adjoint keeps the moments of every step).
-template <int K, int COLS, int PF, bool STORE_W = false, bool L0R = false>
-__global__ void __launch_bounds__(COLS / 2, 2)
-    step2d_temporal_periodic_x2(const StepArgs<float> A, const Consts<float> Kc, const Partition P,
-                                float* __restrict__ wout = nullptr, long long wslot = 0) {
+template <int K, int COLS, int PF, bool STORE_W, bool L0R>
+__device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts<float>& Kc, float* smem, int x0, int w,
+                                          int ys, int ye, float* __restrict__ wout, long long wslot) {
   using S = PairShape<K, COLS, PF, L0R>;
   constexpr int RS = S::RS;
-  extern __shared__ __align__(16) float smem[];
   const int c = threadIdx.x;  // pair index: tile columns 2c, 2c + 1
   const int col = 2 * c;
   const int nx = A.nx, ny = A.ny;
@@ -423,140 +423,184 @@ __global__ void __launch_bounds__(COLS / 2, 2)
   auto grp = [](int p) { return L0R ? reg_group(p) : plane_group(p); };
   auto idx = [](int p) { return L0R ? reg_index(p) : plane_index(p); };
 
-  run_segment(P, ny, [&](int strip, int ys, int ye) {
-    const int gx_raw = strip * P.w - K + col;
-    const bool in_tile = col < P.w + 2 * K;
-    const int gx = ((gx_raw % nx) + nx) % nx;
-    const int iters = (ye - ys) + 2 * K;
+  const int gx_raw = x0 - K + col;
+  const bool in_tile = col < w + 2 * K;
+  const int gx = ((gx_raw % nx) + nx) % nx;
+  const int iters = (ye - ys) + 2 * K;
 
-    float2 a_now[K][3], f0_now[K], c_now[K][3], f0_prev[K], c_prev1[K][3], c_prev2[K][3];
+  float2 a_now[K][3], f0_now[K], c_now[K][3], f0_prev[K], c_prev1[K][3], c_prev2[K][3];
 #pragma unroll
-    for (int t = 0; t < K; ++t) {
-      f0_now[t] = f0_prev[t] = make_float2(0.f, 0.f);
+  for (int t = 0; t < K; ++t) {
+    f0_now[t] = f0_prev[t] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = make_float2(0.f, 0.f);
+  }
+
+  auto issue_row = [&](int j) {
+    if (j < iters && in_tile) {
+      const int r = ys - K + j;
+      const int gr = ((r % ny) + ny) % ny;
+      const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
+      float* sa = l0a + (j % S::A0) * 3 * RS + col + 2;
+      float* sb = l0b + (j % S::B0) * S::BP * RS + col + 2;
+      float* sc = l0c + (j % S::C0) * S::CP * RS + col + 2;
+#pragma unroll
+      for (int p = 0; p < 13; ++p) {
+        float* d = grp(p) == 0 ? sa : (grp(p) == 1 ? sb : sc);
+        __pipeline_memcpy_async(d + idx(p) * RS, g + p * A.plane, 2 * sizeof(float));
+      }
     }
-
-    auto issue_row = [&](int j) {
-      if (j < iters && in_tile) {
-        const int r = ys - K + j;
-        const int gr = ((r % ny) + ny) % ny;
-        const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
-        float* sa = l0a + (j % S::A0) * 3 * RS + col + 2;
-        float* sb = l0b + (j % S::B0) * S::BP * RS + col + 2;
-        float* sc = l0c + (j % S::C0) * S::CP * RS + col + 2;
-#pragma unroll
-        for (int p = 0; p < 13; ++p) {
-          float* d = grp(p) == 0 ? sa : (grp(p) == 1 ? sb : sc);
-          __pipeline_memcpy_async(d + idx(p) * RS, g + p * A.plane, 2 * sizeof(float));
-        }
-      }
-      __pipeline_commit();
-    };
+    __pipeline_commit();
+  };
 
 #pragma unroll
-    for (int q = 0; q < PF; ++q) issue_row(q);
-    for (int j = 0; j < iters; ++j) {
-      __pipeline_wait_prior(PF - 1);  // row j has landed (this thread's copies)
-      __syncthreads();                // ... and every thread's; iteration j - 1 is over everywhere
-      if (L0R) {
-        // f0 and the +y movers of the row just landed, into registers (read by level 1 one
-        // and two iterations later)
-        const float* rf = l0c + (j % S::C0) * S::CP * RS + col + 2;
-        f0_now[0] = ld2(rf);
+  for (int q = 0; q < PF; ++q) issue_row(q);
+  for (int j = 0; j < iters; ++j) {
+    __pipeline_wait_prior(PF - 1);  // row j has landed (this thread's copies)
+    __syncthreads();                // ... and every thread's; iteration j - 1 is over everywhere
+    if (L0R) {
+      // f0 and the +y movers of the row just landed, into registers (read by level 1 one
+      // and two iterations later)
+      const float* rf = l0c + (j % S::C0) * S::CP * RS + col + 2;
+      f0_now[0] = ld2(rf);
 #pragma unroll
-        for (int fam = 0; fam < 3; ++fam) c_now[0][fam] = ld2(rf + (1 + fam) * RS);
-      }
-      issue_row(j + PF);
+      for (int fam = 0; fam < 3; ++fam) c_now[0][fam] = ld2(rf + (1 + fam) * RS);
+    }
+    issue_row(j + PF);
 #pragma unroll
-      for (int t = 1; t <= K; ++t) {
-        const int R = ys - K + j - t;
-        const bool row_ok = R >= ys - K + t && R < ye + K - t;
-        if (row_ok && col + 1 >= t && col < P.w + 2 * K - t) {
-          float2 f[13];
-          if (t == 1 && L0R) {
-            const float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;                 // row R + 1
-            const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 6 * RS + col + 2;  // row R
-            f[0] = f0_prev[0];
-#pragma unroll
-            for (int fam = 0; fam < 3; ++fam) {
-              const float* px = rb + (2 * fam) * RS;      // +x movers from columns 2c - 1, 2c
-              const float* mx = rb + (2 * fam + 1) * RS;  // -x movers from columns 2c + 1, 2c + 2
-              f[1 + 4 * fam] = make_float2(px[-1], px[0]);
-              f[2 + 4 * fam] = c_prev2[0][fam];
-              f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
-              f[4 + 4 * fam] = ld2(ra + fam * RS);
-            }
-          } else if (t == 1) {
-            const float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;
-            const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 7 * RS + col + 2;
-            const float* rc = l0c + ((j + S::C0 - 2) % S::C0) * 3 * RS + col + 2;
-            f[0] = ld2(rb);
-#pragma unroll
-            for (int fam = 0; fam < 3; ++fam) {
-              const float* px = rb + (1 + 2 * fam) * RS;  // +x movers from columns 2c - 1, 2c
-              const float* mx = rb + (2 + 2 * fam) * RS;  // -x movers from columns 2c + 1, 2c + 2
-              f[1 + 4 * fam] = make_float2(px[-1], px[0]);
-              f[2 + 4 * fam] = ld2(rc + fam * RS);
-              f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
-              f[4 + 4 * fam] = ld2(ra + fam * RS);
-            }
-          } else {
-            const float* x = xm(t - 1, (j + 1) & 1) + col + 2;
-            f[0] = f0_prev[t - 1];
-#pragma unroll
-            for (int fam = 0; fam < 3; ++fam) {
-              const float* px = x + (2 * fam) * RS;
-              const float* mx = x + (2 * fam + 1) * RS;
-              f[1 + 4 * fam] = make_float2(px[-1], px[0]);
-              f[2 + 4 * fam] = c_prev2[t - 1][fam];
-              f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
-              f[4 + 4 * fam] = a_now[t - 1][fam];
-            }
-          }
-          float2 wh, wx, wy;
-          collide13x2(f, Kc, wh, wx, wy);
-          if (STORE_W && R >= ys && R < ye && col >= K && col < K + P.w && gx_raw < nx) {
-            float* wp = wout + (t - 1) * wslot + static_cast<long long>(R) * A.pitch + gx_raw;
-            st2(wp, wh);
-            st2(wp + A.plane, wx);
-            st2(wp + 2 * A.plane, wy);
-          }
-          if (t < K) {
-            float* x = xm(t, j & 1) + col + 2;
-#pragma unroll
-            for (int fam = 0; fam < 3; ++fam) {
-              st2(x + (2 * fam) * RS, f[1 + 4 * fam]);
-              st2(x + (2 * fam + 1) * RS, f[3 + 4 * fam]);
-              a_now[t][fam] = f[4 + 4 * fam];
-              c_now[t][fam] = f[2 + 4 * fam];
-            }
-            f0_now[t] = f[0];
-          } else if (col >= K && col < K + P.w && gx_raw < nx) {
-            float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
-#pragma unroll
-            for (int p = 0; p < 13; ++p) st2(g + p * A.plane, f[p]);
-          }
-        }
-        if (t > 1 || L0R) {
-          f0_prev[t - 1] = f0_now[t - 1];
+    for (int t = 1; t <= K; ++t) {
+      const int R = ys - K + j - t;
+      const bool row_ok = R >= ys - K + t && R < ye + K - t;
+      if (row_ok && col + 1 >= t && col < w + 2 * K - t) {
+        float2 f[13];
+        if (t == 1 && L0R) {
+          const float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;                 // row R + 1
+          const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 6 * RS + col + 2;  // row R
+          f[0] = f0_prev[0];
 #pragma unroll
           for (int fam = 0; fam < 3; ++fam) {
-            c_prev2[t - 1][fam] = c_prev1[t - 1][fam];
-            c_prev1[t - 1][fam] = c_now[t - 1][fam];
+            const float* px = rb + (2 * fam) * RS;      // +x movers from columns 2c - 1, 2c
+            const float* mx = rb + (2 * fam + 1) * RS;  // -x movers from columns 2c + 1, 2c + 2
+            f[1 + 4 * fam] = make_float2(px[-1], px[0]);
+            f[2 + 4 * fam] = c_prev2[0][fam];
+            f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
+            f[4 + 4 * fam] = ld2(ra + fam * RS);
           }
+        } else if (t == 1) {
+          const float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;
+          const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 7 * RS + col + 2;
+          const float* rc = l0c + ((j + S::C0 - 2) % S::C0) * 3 * RS + col + 2;
+          f[0] = ld2(rb);
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            const float* px = rb + (1 + 2 * fam) * RS;  // +x movers from columns 2c - 1, 2c
+            const float* mx = rb + (2 + 2 * fam) * RS;  // -x movers from columns 2c + 1, 2c + 2
+            f[1 + 4 * fam] = make_float2(px[-1], px[0]);
+            f[2 + 4 * fam] = ld2(rc + fam * RS);
+            f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
+            f[4 + 4 * fam] = ld2(ra + fam * RS);
+          }
+        } else {
+          const float* x = xm(t - 1, (j + 1) & 1) + col + 2;
+          f[0] = f0_prev[t - 1];
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            const float* px = x + (2 * fam) * RS;
+            const float* mx = x + (2 * fam + 1) * RS;
+            f[1 + 4 * fam] = make_float2(px[-1], px[0]);
+            f[2 + 4 * fam] = c_prev2[t - 1][fam];
+            f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
+            f[4 + 4 * fam] = a_now[t - 1][fam];
+          }
+        }
+        float2 wh, wx, wy;
+        collide13x2(f, Kc, wh, wx, wy);
+        if (STORE_W && R >= ys && R < ye && col >= K && col < K + w && gx_raw < nx) {
+          float* wp = wout + (t - 1) * wslot + static_cast<long long>(R) * A.pitch + gx_raw;
+          st2(wp, wh);
+          st2(wp + A.plane, wx);
+          st2(wp + 2 * A.plane, wy);
+        }
+        if (t < K) {
+          float* x = xm(t, j & 1) + col + 2;
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            st2(x + (2 * fam) * RS, f[1 + 4 * fam]);
+            st2(x + (2 * fam + 1) * RS, f[3 + 4 * fam]);
+            a_now[t][fam] = f[4 + 4 * fam];
+            c_now[t][fam] = f[2 + 4 * fam];
+          }
+          f0_now[t] = f[0];
+        } else if (col >= K && col < K + w && gx_raw < nx) {
+          float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
+#pragma unroll
+          for (int p = 0; p < 13; ++p) st2(g + p * A.plane, f[p]);
+        }
+      }
+      if (t > 1 || L0R) {
+        f0_prev[t - 1] = f0_now[t - 1];
+#pragma unroll
+        for (int fam = 0; fam < 3; ++fam) {
+          c_prev2[t - 1][fam] = c_prev1[t - 1][fam];
+          c_prev1[t - 1][fam] = c_now[t - 1][fam];
         }
       }
     }
-    __pipeline_wait_prior(0);
+  }
+  __pipeline_wait_prior(0);
+}
+
+template <int K, int COLS, int PF, bool STORE_W = false, bool L0R = false>
+__global__ void __launch_bounds__(COLS / 2, 2)
+    step2d_temporal_periodic_x2(const StepArgs<float> A, const Consts<float> Kc, const Partition P,
+                                float* __restrict__ wout = nullptr, long long wslot = 0) {
+  extern __shared__ __align__(16) float smem[];
+  run_segment(P, A.ny, [&](int strip, int ys, int ye) {
+    pair_wave<K, COLS, PF, STORE_W, L0R>(A, Kc, smem, strip * P.w, P.w, ys, ye, wout, wslot);
   });
 }
 
-// Resident CTAs per SM of a kernel at its dynamic shared-memory size (asked once).
+// The same for even-width instances with the paired wavefront (two columns per thread).
+template <int K, int COLS, int PF, bool L0R>
+__global__ void __launch_bounds__(COLS / 2, 2)
+    batch_temporal_pairs(const WaveUnit* __restrict__ units, const int* __restrict__ first,
+                         const float* __restrict__ src, float* __restrict__ dst, const Consts<float> Kc) {
+  extern __shared__ __align__(16) float smem[];
+  for (int u = first[blockIdx.x]; u < first[blockIdx.x + 1]; ++u) {
+    const WaveUnit U = units[u];
+    StepArgs<float> A;
+    A.src = src + U.offset;
+    A.dst = dst + U.offset;
+    A.inflow_feq = nullptr;
+    A.nx = U.nx;
+    A.ny = U.ny;
+    A.pitch = U.pitch;
+    A.plane = U.plane;
+    for (int s = 0; s < 4; ++s) A.bc[s] = LBM_SW_BC_PERIODIC;
+    pair_wave<K, COLS, PF, false, L0R>(A, Kc, smem, U.x0, U.w, U.ys, U.ye, nullptr, 0);
+    __syncthreads();  // the next unit reuses the rings
+  }
+}
+
+// Resident CTAs per SM of a kernel at its dynamic shared-memory size.
 inline int resident_ctas(const void* fn, int threads, size_t smem) {
   int r = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fn, threads, smem) != cudaSuccess) return 1;
   return std::max(r, 1);
+}
+
+// The same, asked once per kernel and device.
+inline int cached_resident(const void* fn, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return resident_ctas(fn, threads, smem);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({dev, fn});
+  if (it != cache.end()) return it->second;
+  const int v = resident_ctas(fn, threads, smem);
+  cache[{dev, fn}] = v;
+  return v;
 }
 
 // Strips of equal width <= wmax, then row segments: about `waves` waves of the resident
@@ -591,8 +635,7 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
     fn = reinterpret_cast<const void*>(step2d_temporal<K, COLS>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  static int resident = 0;  // the same on every GPU of one model
-  if (resident == 0) resident = resident_ctas(fn, COLS, smem);
+  const int resident = cached_resident(fn, COLS, smem);
   // one wave of the resident CTAs for the periodic kernel, two for the other
   const Partition P = partition(a.nx, a.ny, COLS - 2 * K, K, resident * std::max(sm_count, 1), PER ? 1 : 2);
   const int grid = P.strips * P.segments;
@@ -611,8 +654,7 @@ cudaError_t launch_k_pairs(const StepArgs<float>& a, const ConstsD& kd, cudaStre
   const void* fn = reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF, false, L0R>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  static int resident = 0;
-  if (resident == 0) resident = resident_ctas(fn, COLS / 2, smem);
+  const int resident = cached_resident(fn, COLS / 2, smem);
   Partition P = partition(a.nx, a.ny, COLS - 2 * K, K, resident * std::max(sm_count, 1), 1);
   P.w += P.w & 1;  // even strip width (<= COLS - 2K since that is even)
   P.strips = (a.nx + P.w - 1) / P.w;
@@ -630,8 +672,7 @@ cudaError_t launch_k_pairs_w(const StepArgs<float>& a, const ConstsD& kd, float*
   const void* fn = reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF, true>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  static int resident = 0;
-  if (resident == 0) resident = resident_ctas(fn, COLS / 2, smem);
+  const int resident = cached_resident(fn, COLS / 2, smem);
   Partition P = partition(a.nx, a.ny, COLS - 2 * K, K, resident * std::max(sm_count, 1), 1);
   P.w += P.w & 1;
   P.strips = (a.nx + P.w - 1) / P.w;
@@ -857,8 +898,7 @@ cudaError_t launch_adjoint_k(const StepArgs<float>& a, const float* w0, long lon
   const void* fn = reinterpret_cast<const void*>(adjoint_temporal_periodic<K, COLS>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  static int resident = 0;
-  if (resident == 0) resident = resident_ctas(fn, COLS, smem);
+  const int resident = cached_resident(fn, COLS, smem);
   const Partition P = partition(a.nx, a.ny, COLS - 2 * K, K, resident * std::max(sm_count, 1), 1);
   const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
   adjoint_temporal_periodic<K, COLS><<<P.strips * P.segments, COLS, smem, st>>>(a, w0, wslot, K_, P);
@@ -887,61 +927,95 @@ cudaError_t launch_adjoint_temporal(const StepArgs<float>& a, const float* w0, l
 // ---------------------------------------------------------------- batched instances
 namespace {
 
+// Configuration of the paired batch kernel at K (0 columns: no paired kernel for odd K).
+struct PairCfg {
+  int cols, pf;
+  bool l0r;
+};
+constexpr PairCfg pair_cfg(int k) {
+  return k % 2 ? PairCfg{0, 0, false} : (k <= 4 ? PairCfg{256, 2, false} : (k == 6 ? PairCfg{256, 1, true} : PairCfg{192, 1, false}));
+}
+
 template <int K>
 size_t batch_smem() {
   return PeriodicShape<K, 192>::floats() * sizeof(float);
 }
 
 template <int K>
-const void* batch_fn() {
-  return reinterpret_cast<const void*>(batch_temporal_periodic<K, 192>);
+size_t batch_pair_smem() {
+  constexpr PairCfg c = pair_cfg(K);
+  if constexpr (c.cols == 0)
+    return 0;
+  else
+    return PairShape<K, c.cols, c.pf, c.l0r>::floats() * sizeof(float);
 }
 
 template <int K>
-cudaError_t batch_prepare(int* resident) {
-  const size_t smem = batch_smem<K>();
-  cudaError_t e = cudaFuncSetAttribute(batch_fn<K>(), cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+const void* batch_pair_fn() {
+  constexpr PairCfg c = pair_cfg(K);
+  if constexpr (c.cols == 0)
+    return nullptr;
+  else
+    return reinterpret_cast<const void*>(batch_temporal_pairs<K, c.cols, c.pf, c.l0r>);
+}
+
+// Shared-memory attributes of both kernels on this device; resident CTAs per SM of each
+// (0 for the paired kernel at odd K).
+template <int K>
+cudaError_t batch_prepare(int* resident, int* resident_pairs) {
+  const void* fn = reinterpret_cast<const void*>(batch_temporal_periodic<K, 192>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(batch_smem<K>()));
   if (e != cudaSuccess) return e;
-  *resident = resident_ctas(batch_fn<K>(), 192, smem);
+  *resident = cached_resident(fn, 192, batch_smem<K>());
+  *resident_pairs = 0;
+  if (const void* pf = batch_pair_fn<K>()) {
+    e = cudaFuncSetAttribute(pf, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(batch_pair_smem<K>()));
+    if (e != cudaSuccess) return e;
+    *resident_pairs = cached_resident(pf, pair_cfg(K).cols / 2, batch_pair_smem<K>());
+  }
   return cudaSuccess;
 }
 
-cudaError_t batch_prepare_k(int k, int* resident) {
+cudaError_t batch_prepare_k(int k, int* resident, int* resident_pairs) {
   switch (k) {
-    case 2: return batch_prepare<2>(resident);
-    case 3: return batch_prepare<3>(resident);
-    case 5: return batch_prepare<5>(resident);
-    case 6: return batch_prepare<6>(resident);
-    case 7: return batch_prepare<7>(resident);
-    case 8: return batch_prepare<8>(resident);
-    default: return batch_prepare<4>(resident);
+    case 2: return batch_prepare<2>(resident, resident_pairs);
+    case 3: return batch_prepare<3>(resident, resident_pairs);
+    case 5: return batch_prepare<5>(resident, resident_pairs);
+    case 6: return batch_prepare<6>(resident, resident_pairs);
+    case 7: return batch_prepare<7>(resident, resident_pairs);
+    case 8: return batch_prepare<8>(resident, resident_pairs);
+    default: return batch_prepare<4>(resident, resident_pairs);
   }
 }
 
 template <int K>
 void batch_launch(const BatchWaves& w, const float* src, float* dst, const Consts<float>& c, cudaStream_t st) {
-  batch_temporal_periodic<K, 192><<<w.grid, 192, batch_smem<K>(), st>>>(w.units, w.first, src, dst, c);
+  if (w.count > 0) batch_temporal_periodic<K, 192><<<w.grid, 192, batch_smem<K>(), st>>>(w.units, w.first, src, dst, c);
+  constexpr PairCfg pc = pair_cfg(K);
+  if constexpr (pc.cols > 0)
+    if (w.pcount > 0)
+      batch_temporal_pairs<K, pc.cols, pc.pf, pc.l0r>
+          <<<w.pgrid, pc.cols / 2, batch_pair_smem<K>(), st>>>(w.punits, w.pfirst, src, dst, c);
 }
 
-}  // namespace
-
-cudaError_t batch_waves_build(int count, const int* nx, const int* ny, const long long* offset, const long long* pitch,
-                              const long long* plane, int k, int sm_count, BatchWaves* out) {
-  batch_waves_free(out);
-  int resident = 1;
-  cudaError_t e = batch_prepare_k(k, &resident);
-  if (e != cudaSuccess) return e;
-  const int grid = std::max(1, resident * std::max(sm_count, 1));
-  const int wmax = 192 - 2 * k;
+// Units of the given instances at strip width <= wmax (even widths when `even`), balanced
+// longest-first over `grid` CTAs; uploads them and the per-CTA ranges.
+cudaError_t build_list(const std::vector<int>& ids, const int* nx, const int* ny, const long long* offset,
+                       const long long* pitch, const long long* plane, int k, int wmax, bool even, int grid,
+                       WaveUnit** d_units, int** d_first, int* count) {
   // row segments of about a sixth of a CTA's share of the strip rows, no shorter than 4k
   long long strip_rows = 0;
-  for (int i = 0; i < count; ++i) strip_rows += static_cast<long long>((nx[i] + wmax - 1) / wmax) * ny[i];
+  for (int i : ids) strip_rows += static_cast<long long>((nx[i] + wmax - 1) / wmax) * ny[i];
   const long long target = std::max<long long>(4LL * k, (strip_rows + 6LL * grid - 1) / (6LL * grid));
   std::vector<WaveUnit> units;
   std::vector<long long> cost;
-  for (int i = 0; i < count; ++i) {
-    const int strips = (nx[i] + wmax - 1) / wmax;
-    const int w = (nx[i] + strips - 1) / strips;
+  for (int i : ids) {
+    int strips = (nx[i] + wmax - 1) / wmax;
+    int w = (nx[i] + strips - 1) / strips;
+    if (even) {
+      w += w & 1;  // <= wmax, which is even
+      strips = (nx[i] + w - 1) / w;
+    }
     const int segs = static_cast<int>(std::max<long long>(1, (ny[i] + target - 1) / target));
     const int rows = (ny[i] + segs - 1) / segs;
     for (int sgi = 0; sgi < segs; ++sgi)
@@ -984,31 +1058,51 @@ cudaError_t batch_waves_build(int count, const int* nx, const int* ny, const lon
     for (int u : per[b]) sorted.push_back(units[u]);
   }
   first[grid] = static_cast<int>(sorted.size());
-  e = cudaMalloc(&out->units, std::max<size_t>(1, sorted.size()) * sizeof(WaveUnit));
-  if (e == cudaSuccess) e = cudaMalloc(&out->first, first.size() * sizeof(int));
+  cudaError_t e = cudaMalloc(d_units, std::max<size_t>(1, sorted.size()) * sizeof(WaveUnit));
+  if (e == cudaSuccess) e = cudaMalloc(d_first, first.size() * sizeof(int));
   if (e == cudaSuccess && !sorted.empty())
-    e = cudaMemcpy(out->units, sorted.data(), sorted.size() * sizeof(WaveUnit), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(out->first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    batch_waves_free(out);
-    return e;
+    e = cudaMemcpy(*d_units, sorted.data(), sorted.size() * sizeof(WaveUnit), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(*d_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice);
+  *count = static_cast<int>(sorted.size());
+  return e;
+}
+
+}  // namespace
+
+cudaError_t batch_waves_build(int count, const int* nx, const int* ny, const long long* offset, const long long* pitch,
+                              const long long* plane, int k, int sm_count, BatchWaves* out) {
+  batch_waves_free(out);
+  int resident = 1, resident_pairs = 0;
+  cudaError_t e = batch_prepare_k(k, &resident, &resident_pairs);
+  if (e != cudaSuccess) return e;
+  const PairCfg pc = pair_cfg(k);
+  std::vector<int> odd, even;
+  for (int i = 0; i < count; ++i) (pc.cols > 0 && nx[i] % 2 == 0 ? even : odd).push_back(i);
+  out->grid = std::max(1, resident * std::max(sm_count, 1));
+  e = build_list(odd, nx, ny, offset, pitch, plane, k, 192 - 2 * k, false, out->grid, &out->units, &out->first,
+                 &out->count);
+  if (e == cudaSuccess && !even.empty()) {
+    out->pgrid = std::max(1, resident_pairs * std::max(sm_count, 1));
+    e = build_list(even, nx, ny, offset, pitch, plane, k, pc.cols - 2 * k, true, out->pgrid, &out->punits,
+                   &out->pfirst, &out->pcount);
   }
-  out->count = static_cast<int>(sorted.size());
-  out->grid = grid;
-  return cudaSuccess;
+  if (e != cudaSuccess) batch_waves_free(out);
+  return e;
 }
 
 void batch_waves_free(BatchWaves* w) {
   if (w->units) cudaFree(w->units);
   if (w->first) cudaFree(w->first);
+  if (w->punits) cudaFree(w->punits);
+  if (w->pfirst) cudaFree(w->pfirst);
   *w = BatchWaves();
 }
 
 cudaError_t launch_batch_temporal(const BatchWaves& w, int k, const float* src, float* dst, const ConstsD& kd,
                                   cudaStream_t st) {
   if (w.grid < 1) return cudaErrorInvalidValue;
-  int resident = 1;
-  cudaError_t e = batch_prepare_k(k, &resident);  // the shared-memory attribute, on this device
+  int resident = 1, resident_pairs = 0;
+  cudaError_t e = batch_prepare_k(k, &resident, &resident_pairs);  // the shared-memory attributes, on this device
   if (e != cudaSuccess) return e;
   const Consts<float> c = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
   switch (k) {

@@ -61,10 +61,10 @@ def temporal_kernel_name(k: int) -> str:
 # kernel sources it was taken on.
 NCU_TRAFFIC = {
     "step2d_temporal_periodic_x2<6, 256, 1, 0, 1>": {
-        "src_sha256": "cc0b5d66b382742ac0c96217efe1310db9745dab54b4c81220fa83add43db38a",
-        "sources": ("temporal.cu", "scheme.cuh"), "bytes_per_launch": 1745.65e6,
+        "src_sha256": "13e440f3312594d4188cace7fd2ac49f8dfb5e6d94fa35b2d55c6c5652cd51ae",
+        "sources": ("temporal.cu", "scheme.cuh"), "bytes_per_launch": 1745.69e6,
         "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of the 5 launches of "
-                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.78 MB read + 823.87 MB "
+                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.88 MB read + 823.81 MB "
                 "written per launch (mean)"},
 }
 

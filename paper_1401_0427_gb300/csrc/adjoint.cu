@@ -359,13 +359,15 @@ int tfail(lbm_sw_tape* t, int code, const char* fmt, ...) {
                    cudaGetErrorString(e_));                                                   \
   } while (0)
 
-// Steps per fused launch of the replay and of the adjoint steps: the handle's temporal K,
-// at most 4 (the reverse wavefront keeps every level's moments in shared memory as well,
-// which at K = 6 would leave one CTA per SM); 0 when the handle does not fuse steps.
-int tape_k(const lbm_sw* h) {
+// Steps per fused launch of the segment replays (the handle's K: its kernel also stores the
+// moments of every level) and of the adjoint steps (at most 4: the reverse wavefront keeps
+// every level's moments in shared memory as well, which at K = 6 would leave one CTA per SM);
+// 0 when the handle does not fuse steps.
+int replay_k(const lbm_sw* h) {
   if (h->kernel != LBM_SW_KERNEL_TEMPORAL || h->p.precision != LBM_SW_FP32 || h->temporal_k < 2) return 0;
-  return std::min(h->temporal_k, 4);
+  return h->temporal_k;
 }
+int adjoint_k(const lbm_sw* h) { return std::min(replay_k(h), 4); }
 
 template <class T>
 lbm::StepArgs<T> replay_args(const lbm_sw* h, const lbm_sw_tape* t, int from) {
@@ -399,7 +401,7 @@ int run_adjoint(lbm_sw* h, lbm_sw_tape* t, const double* gh, const double* gu, c
     int from = 0, j = 1;
     if constexpr (sizeof(T) == 4) {
       // FP32: K steps per launch where the fused kernel can store every level's moments
-      const int k = tape_k(h);
+      const int k = replay_k(h);
       const auto a0 = replay_args<T>(h, t, 0);
       // (the last launch may run past the segment into the spare moment slots)
       if (k > 1 && j + k <= t->wslots && lbm::temporal_store_w_supported(a0, k))
@@ -414,7 +416,7 @@ int run_adjoint(lbm_sw* h, lbm_sw_tape* t, const double* gh, const double* gu, c
     // segment's stored moments cover them)
     for (int n = k1; n > k0; --n) {
       if constexpr (sizeof(T) == 4) {
-        const int k = tape_k(h);
+        const int k = adjoint_k(h);
         lbm::StepArgs<float> a = lbm::handle_args<float>(h, 0);
         a.src = static_cast<const float*>(t->phi[cur]);
         a.dst = static_cast<float*>(t->phi[1 - cur]);
@@ -496,16 +498,17 @@ int lbm_sw_tape_create(lbm_sw* h, int steps, int interval, lbm_sw_tape** out) {
   t->owner = h;
   t->steps = steps;
   t->interval = interval ? interval : static_cast<int>(std::ceil(std::sqrt(static_cast<double>(steps))));
-  if (!interval && tape_k(h) > 1) {
-    // a whole number of fused launches per interval: of the forward run (the handle's K)
-    // and of the replay (tape_k) where that at most doubles the interval, else of the replay
-    const int k = tape_k(h), both = std::lcm(k, h->temporal_k), iv = t->interval;
+  if (!interval && replay_k(h) > 1) {
+    // a whole number of fused launches per interval: of the forward run and replay (the
+    // handle's K) and of the adjoint steps where that at most doubles the interval, else of
+    // the forward run and replay
+    const int k = replay_k(h), both = std::lcm(k, adjoint_k(h)), iv = t->interval;
     const int round_both = (iv + both - 1) / both * both;
     t->interval = std::min(steps, round_both <= 2 * iv ? round_both : (iv + k - 1) / k * k);
   }
   t->checkpoints = (steps + t->interval - 1) / t->interval;
   // a replay that fuses k steps per launch may run up to k - 1 steps past its segment
-  t->wslots = t->interval + tape_k(h);
+  t->wslots = t->interval + replay_k(h);
   t->state_elems = static_cast<size_t>(13) * h->plane;
   const size_t n = static_cast<size_t>(h->p.nx) * h->p.ny;
   bool ok = cudaMalloc(&t->ckpt, sizeof(double) * t->state_elems * t->checkpoints) == cudaSuccess &&

@@ -667,9 +667,11 @@ cudaError_t launch_k_pairs(const StepArgs<float>& a, const ConstsD& kd, cudaStre
 template <int K>
 cudaError_t launch_k_pairs_w(const StepArgs<float>& a, const ConstsD& kd, float* wout, long long wslot,
                              cudaStream_t st, int sm_count) {
-  constexpr int COLS = K <= 4 ? 256 : 192, PF = K <= 4 ? 2 : 1;
-  const size_t smem = PairShape<K, COLS, PF>::floats() * sizeof(float);
-  const void* fn = reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF, true>);
+  // the configuration of the forward kernel at each K
+  constexpr int COLS = K <= 6 ? 256 : 192, PF = K <= 4 ? 2 : 1;
+  constexpr bool L0R = K == 6;
+  const size_t smem = PairShape<K, COLS, PF, L0R>::floats() * sizeof(float);
+  const void* fn = reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF, true, L0R>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int resident = cached_resident(fn, COLS / 2, smem);
@@ -678,7 +680,8 @@ cudaError_t launch_k_pairs_w(const StepArgs<float>& a, const ConstsD& kd, float*
   P.strips = (a.nx + P.w - 1) / P.w;
   const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
   const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
-  step2d_temporal_periodic_x2<K, COLS, PF, true><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q, wout, wslot);
+  step2d_temporal_periodic_x2<K, COLS, PF, true, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q, wout,
+                                                                                                  wslot);
   return cudaGetLastError();
 }
 

@@ -8,6 +8,7 @@ statically.  Outputs stay in the source tree (``csrc/_build``, git-ignored).
 from __future__ import annotations
 
 import concurrent.futures
+import fcntl
 import os
 import shutil
 import subprocess
@@ -48,11 +49,24 @@ def _stale(target: str, deps: list[str]) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Build (if needed) and return the path of liblbm_sw.so."""
+    """Build (if needed) and return the path of liblbm_sw.so.  Processes that build at the
+    same time (one per rank of a multi-GPU run) take turns on a lock file; the ones that
+    wait find the library up to date."""
     os.makedirs(BUILD, exist_ok=True)
     srcs, hdrs = sources(), headers()
     if not force and not ptxas_info and not _stale(LIB, srcs + hdrs + [__file__]):
         return LIB
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and not ptxas_info and not _stale(LIB, srcs + hdrs + [__file__]):
+                return LIB
+            return _compile_and_link(srcs, verbose, ptxas_info)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _compile_and_link(srcs: list[str], verbose: bool, ptxas_info: bool) -> str:
     exe = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 

@@ -658,6 +658,17 @@ def profile_case(args, local):
                 g = torch.full((n, n), 1e-3, dtype=torch.float64, device="cuda")
                 t = _timed(stream, torch, lambda: tape.adjoint(g))
         out["cells"] = n * n
+    elif args.case == "reflection":
+        n = 512
+        uL = inputs.shock_speed_state(2.0, 1.0)
+        prec = lbm_sw.FP64 if args.precision == "fp64" else lbm_sw.FP32
+        with lbm_sw.Simulation(n, n, precision=prec, lam=LAM, s=S_RATE, a=A_REST,
+                               bc=(lbm_sw.INFLOW, lbm_sw.WALL, lbm_sw.PERIODIC, lbm_sw.PERIODIC),
+                               inflow=[(2.0, 2.0 * uL, 0.0)] * 4, stream=stream.cuda_stream, graph_chunk=-1) as sim:
+            sim.set_state(*inputs.planar_shock_2d(n, n))
+            sim.step(args.warmup)
+            t = _timed(stream, torch, lambda: sim.step(args.steps))
+        out["cells"] = n * n
     elif args.case == "shock_tube":
         h, q = inputs.dam_break_1d(1000)
         with lbm_sw.Simulation(1000, 1, dim=1, precision=lbm_sw.FP64, lam=LAM, s=S_RATE, a=0.15,
@@ -694,7 +705,7 @@ def main():
     ap.add_argument("--temporal-steps", type=int, default=0,
                     help="steps per launch of the temporal kernel (0: the library default, 6 here; for "
                          "--case batched: 0 or 1 = one step per launch)")
-    ap.add_argument("--case", choices=["step", "batched", "adjoint", "shock_tube", "diag"], default="step",
+    ap.add_argument("--case", choices=["step", "batched", "adjoint", "reflection", "shock_tube", "diag"], default="step",
                     help="kernel to run for profiling (only 'step' prints the benchmark line)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
                     help="population precision of the timed loop (fp32 is the workload)")

@@ -458,6 +458,7 @@ def variants(args, W0, stream, lbm_sw, torch):
                   "steps": JOB_STEPS, "against": "FP64 run of the same workload (equal to the FP64 oracle "
                                                  "within 1e-12 in the parity tests)"}
     out["fp32_temporal_k"] = temporal_sweep(W0, stream, lbm_sw, torch)
+    out["fp32_closed_basin"] = bounded_variant(W0, stream, lbm_sw, torch)
     out["batched_256"] = batched_variant(stream, lbm_sw, torch)
     out["shock_reflection_512"] = shock_reflection_variant(stream, lbm_sw, torch)
     out["shock_tube_1d_1000"] = shock_tube_variant(stream, lbm_sw, torch)
@@ -487,6 +488,25 @@ def temporal_sweep(W0, stream, lbm_sw, torch, steps: int = 840):
             t = _timed(stream, torch, lambda: sim.step(n))
         out[str(k)] = {"MLUPS": N * N * n / t / 1e6,
                        "HBM_GB_per_s": BYTES_PER_LUP["f32"] * N * N * (n // k) / t / 1e9}
+    return out
+
+
+def bounded_variant(W0, stream, lbm_sw, torch, steps: int = 240):
+    """The same dam-break with boundaries: walls on every side (a closed basin), and a channel
+    (inflow at x-, outflow at x+, walls at y-+), FP32, the library's kernel choice (the
+    two-column temporal kernel, whose edge lanes apply the side rules) against one step per
+    launch."""
+    W, O, I = lbm_sw.WALL, lbm_sw.OUTFLOW, lbm_sw.INFLOW
+    out = {}
+    for name, bc in (("walls", (W, W, W, W)), ("channel", (I, O, W, W))):
+        for kname, kernel in (("auto", lbm_sw.KERNEL_AUTO), ("one_step", lbm_sw.KERNEL_VEC)):
+            with lbm_sw.Simulation(N, N, precision=lbm_sw.FP32, lam=LAM, s=S_RATE, a=A_REST, bc=bc,
+                                   inflow=[(1.0, 0.2, 0.0)] * 4, stream=stream.cuda_stream, kernel=kernel) as sim:
+                sim.set_state(*W0)
+                sim.step(12)
+                spl = max(1, sim.info().steps_per_launch)
+                t = _timed(stream, torch, lambda: sim.step(steps))
+            out[f"{name}_{kname}"] = {"MLUPS": N * N * steps / t / 1e6, "steps_per_launch": spl}
     return out
 
 

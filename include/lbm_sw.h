@@ -101,7 +101,8 @@ typedef struct lbm_sw lbm_sw;
 
 /* step kernel variants */
 #define LBM_SW_KERNEL_AUTO 0    /* library choice: TEMPORAL for 2D FP32 grids of >= 2^20 cells with
-                                   every side periodic, else VEC in 2D; CLUSTER in 1D */
+                                   every side periodic, or with an even nx and an even
+                                   temporal_steps, else VEC in 2D; CLUSTER in 1D */
 #define LBM_SW_KERNEL_SIMPLE 1  /* one launch per step, one thread per cell, scalar loads */
 #define LBM_SW_KERNEL_VEC 2     /* 2D: 16-byte vectors along x (4 FP32 or 2 FP64 cells per thread),
                                    x-neighbours exchanged with warp shuffles */

@@ -206,9 +206,11 @@ int lbm_sw_create(const lbm_sw_params* p, lbm_sw** out) {
   h->plane = round_up(h->pitch * p->ny, 64);  // 256-byte aligned planes in FP32 and FP64
   const bool all_periodic = p->bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC && p->bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
   if (p->dim == 2) {
-    // AUTO: temporal blocking where it was measured faster (FP32, all sides periodic, at
-    // least 2^20 cells), otherwise one vectorised step per launch
-    const bool temporal = p->precision == LBM_SW_FP32 && all_periodic &&
+    // AUTO: temporal blocking where it was measured faster (FP32, at least 2^20 cells, all
+    // sides periodic or the two-column kernel: even nx and K), otherwise one vectorised step
+    // per launch
+    const int k = p->temporal_steps ? p->temporal_steps : 6;
+    const bool temporal = p->precision == LBM_SW_FP32 && (all_periodic || (p->nx % 2 == 0 && k % 2 == 0)) &&
                           static_cast<long long>(p->nx) * p->ny >= (1LL << 20);
     h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? (temporal ? LBM_SW_KERNEL_TEMPORAL : LBM_SW_KERNEL_VEC) : p->kernel;
   } else {

@@ -405,7 +405,17 @@ __host__ __device__ constexpr int reg_index(int p) {
 // With STORE_W, the moments (h, hu, hv) of every time level t = 1 .. K are also written, for
 // the launch's output cells, to the three planes at wout + (t - 1) * wslot (the replay of the
 // discrete adjoint keeps the moments of every step).
-template <int K, int COLS, int PF, bool STORE_W, bool L0R>
+//
+// PER: every side periodic.  Otherwise the sides that are not periodic apply their rule
+// (WALL, OUTFLOW, INFLOW) without a branch in the pull.  x sides: the edge lane reads its
+// pulled x mover from another place in the same row -- its own opposite mover (WALL, times
+// -1 for the hu family, an exact product), its own mover (OUTFLOW), or the column outside
+// the domain, which holds the inflow equilibrium from the start (INFLOW).  y sides: when a
+// level computes the first row, or reaches the row past the last, the value the rule gives
+// is put in the register the next level pulls from (for level 0, in the input ring).  Tile
+// columns and rows outside the domain are neither loaded nor computed; nx is even, so a pair
+// never straddles the domain's edge.
+template <int K, int COLS, int PF, bool STORE_W, bool L0R, bool PER = true>
 __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts<float>& Kc, float* smem, int x0, int w,
                                           int ys, int ye, float* __restrict__ wout, long long wslot) {
   using S = PairShape<K, COLS, PF, L0R>;
@@ -424,8 +434,12 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
   auto idx = [](int p) { return L0R ? reg_index(p) : plane_index(p); };
 
   const int gx_raw = x0 - K + col;
-  const bool in_tile = col < w + 2 * K;
-  const int gx = ((gx_raw % nx) + nx) % nx;
+  const bool px = PER || A.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC;
+  const bool py = PER || A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
+  const bool col_live = col < w + 2 * K && (px || (gx_raw >= 0 && gx_raw < nx));
+  const int gx = px ? ((gx_raw % nx) + nx) % nx : gx_raw;
+  const bool at_xm = !px && gx_raw == 0;           // lane .x is the domain's first column
+  const bool at_xp = !px && gx_raw + 1 == nx - 1;  // lane .y is its last
   const int iters = (ye - ys) + 2 * K;
 
   float2 a_now[K][3], f0_now[K], c_now[K][3], f0_prev[K], c_prev1[K][3], c_prev2[K][3];
@@ -436,10 +450,74 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
     for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = make_float2(0.f, 0.f);
   }
 
+  // x sides: offsets of the edge lane's pulled x movers from the +x (-x) plane pointer at
+  // this pair (normally -1 and 2), and the sign of the hu family's
+  int o_p1 = -1, o_p3 = 2;
+  float2 sgn1 = make_float2(1.f, 1.f);
+  if (!PER) {
+    const int bm = A.bc[LBM_SW_SIDE_XM], bp = A.bc[LBM_SW_SIDE_XP];
+    if (at_xm && bm != LBM_SW_BC_INFLOW) {
+      o_p1 = bm == LBM_SW_BC_WALL ? RS : 0;  // own -x mover / own +x mover
+      if (bm == LBM_SW_BC_WALL) sgn1.x = -1.f;
+    }
+    if (at_xp && bp != LBM_SW_BC_INFLOW) {
+      o_p3 = bp == LBM_SW_BC_WALL ? 1 - RS : 1;  // own +x mover / own -x mover
+      if (bp == LBM_SW_BC_WALL) sgn1.y = -1.f;
+    }
+    // INFLOW: the column outside the domain of every x-mover row holds the inflow
+    // equilibrium (nothing else writes there)
+    const bool in_m = at_xm && bm == LBM_SW_BC_INFLOW, in_p = at_xp && bp == LBM_SW_BC_INFLOW;
+    if (in_m || in_p) {
+      for (int fam = 0; fam < 3; ++fam) {
+        const float vm = A.inflow_feq[LBM_SW_SIDE_XM * 13 + 1 + 4 * fam];
+        const float vp = A.inflow_feq[LBM_SW_SIDE_XP * 13 + 3 + 4 * fam];
+        for (int q = 0; q < S::B0; ++q) {
+          float* rb = l0b + q * S::BP * RS + col + 2;
+          if (in_m) rb[idx(1 + 4 * fam) * RS - 1] = vm;
+          if (in_p) rb[idx(3 + 4 * fam) * RS + 2] = vp;
+        }
+        for (int t = 1; t < K; ++t)
+          for (int q = 0; q < 2; ++q) {
+            float* x = xm(t, q) + col + 2;
+            if (in_m) x[(2 * fam) * RS - 1] = vm;
+            if (in_p) x[(2 * fam + 1) * RS + 2] = vp;
+          }
+      }
+    }
+  }
+  // the pulled x movers of family fam from the +x / -x planes at this pair
+  auto pull_x = [&](int fam, const float* px, const float* mx, float2* f) {
+    if constexpr (PER) {
+      f[1 + 4 * fam] = make_float2(px[-1], px[0]);
+      f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
+    } else {
+      f[1 + 4 * fam] = make_float2(px[o_p1], px[0]);
+      f[3 + 4 * fam] = make_float2(mx[1], mx[o_p3]);
+      if (fam == 1) {
+        f[5].x *= sgn1.x;
+        f[7].y *= sgn1.y;
+      }
+    }
+  };
+  // y sides: from the edge row's own -y (p4) and +y (p2) movers, the +y movers of row -1 and
+  // the -y movers of row ny.
+  auto ym_ghost = [&](int fam, float2 p4, float2 p2) {
+    const int b = A.bc[LBM_SW_SIDE_YM];
+    return b == LBM_SW_BC_WALL      ? (fam == 2 ? make_float2(-p4.x, -p4.y) : p4)
+           : b == LBM_SW_BC_OUTFLOW ? p2
+                                    : dup2(A.inflow_feq[LBM_SW_SIDE_YM * 13 + 2 + 4 * fam]);
+  };
+  auto yp_ghost = [&](int fam, float2 p4, float2 p2) {
+    const int b = A.bc[LBM_SW_SIDE_YP];
+    return b == LBM_SW_BC_WALL      ? (fam == 2 ? make_float2(-p2.x, -p2.y) : p2)
+           : b == LBM_SW_BC_OUTFLOW ? p4
+                                    : dup2(A.inflow_feq[LBM_SW_SIDE_YP * 13 + 4 + 4 * fam]);
+  };
+
   auto issue_row = [&](int j) {
-    if (j < iters && in_tile) {
-      const int r = ys - K + j;
-      const int gr = ((r % ny) + ny) % ny;
+    const int r = ys - K + j;
+    if (j < iters && col_live && (py || (r >= 0 && r < ny))) {
+      const int gr = py ? ((r % ny) + ny) % ny : r;
       const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
       float* sa = l0a + (j % S::A0) * 3 * RS + col + 2;
       float* sb = l0b + (j % S::B0) * S::BP * RS + col + 2;
@@ -466,12 +544,42 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
 #pragma unroll
       for (int fam = 0; fam < 3; ++fam) c_now[0][fam] = ld2(rf + (1 + fam) * RS);
     }
+    if constexpr (!PER) {
+      // level 0 y sides, from the landed rows (this thread's own columns, which only this
+      // thread reads before the next barrier)
+      const int r = ys - K + j;
+      float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;
+      if (col_live && !py && r == 0) {
+        // the +y movers of row -1, read by level 1 as the row two back
+#pragma unroll
+        for (int fam = 0; fam < 3; ++fam) {
+          if constexpr (L0R) {
+            c_prev1[0][fam] = ym_ghost(fam, ld2(ra + fam * RS), c_now[0][fam]);
+          } else {
+            const float* rc = l0c + (j % S::C0) * 3 * RS + col + 2;
+            st2(l0c + ((j + S::C0 - 1) % S::C0) * 3 * RS + col + 2 + fam * RS,
+                ym_ghost(fam, ld2(ra + fam * RS), ld2(rc + fam * RS)));
+          }
+        }
+      }
+      if (col_live && !py && r == ny) {
+        // the -y movers of row ny, read by level 1 in this iteration from the landed slot
+        // (row ny is not loaded; row ny - 1's slots are not reused while no row is loaded)
+        const float* ra1 = l0a + ((j + S::A0 - 1) % S::A0) * 3 * RS + col + 2;
+#pragma unroll
+        for (int fam = 0; fam < 3; ++fam) {
+          const float2 p2 = L0R ? c_prev1[0][fam] : ld2(l0c + ((j + S::C0 - 1) % S::C0) * 3 * RS + col + 2 + fam * RS);
+          st2(ra + fam * RS, yp_ghost(fam, ld2(ra1 + fam * RS), p2));
+        }
+      }
+    }
     issue_row(j + PF);
 #pragma unroll
     for (int t = 1; t <= K; ++t) {
       const int R = ys - K + j - t;
       const bool row_ok = R >= ys - K + t && R < ye + K - t;
-      if (row_ok && col + 1 >= t && col < w + 2 * K - t) {
+      const bool row_live = py || (R >= 0 && R < ny);
+      if (row_ok && row_live && col_live && col + 1 >= t && col < w + 2 * K - t) {
         float2 f[13];
         if (t == 1 && L0R) {
           const float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;                 // row R + 1
@@ -481,10 +589,9 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
           for (int fam = 0; fam < 3; ++fam) {
             const float* px = rb + (2 * fam) * RS;      // +x movers from columns 2c - 1, 2c
             const float* mx = rb + (2 * fam + 1) * RS;  // -x movers from columns 2c + 1, 2c + 2
-            f[1 + 4 * fam] = make_float2(px[-1], px[0]);
             f[2 + 4 * fam] = c_prev2[0][fam];
-            f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
             f[4 + 4 * fam] = ld2(ra + fam * RS);
+            pull_x(fam, px, mx, f);
           }
         } else if (t == 1) {
           const float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;
@@ -495,10 +602,9 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
           for (int fam = 0; fam < 3; ++fam) {
             const float* px = rb + (1 + 2 * fam) * RS;  // +x movers from columns 2c - 1, 2c
             const float* mx = rb + (2 + 2 * fam) * RS;  // -x movers from columns 2c + 1, 2c + 2
-            f[1 + 4 * fam] = make_float2(px[-1], px[0]);
             f[2 + 4 * fam] = ld2(rc + fam * RS);
-            f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
             f[4 + 4 * fam] = ld2(ra + fam * RS);
+            pull_x(fam, px, mx, f);
           }
         } else {
           const float* x = xm(t - 1, (j + 1) & 1) + col + 2;
@@ -507,10 +613,9 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
           for (int fam = 0; fam < 3; ++fam) {
             const float* px = x + (2 * fam) * RS;
             const float* mx = x + (2 * fam + 1) * RS;
-            f[1 + 4 * fam] = make_float2(px[-1], px[0]);
             f[2 + 4 * fam] = c_prev2[t - 1][fam];
-            f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
             f[4 + 4 * fam] = a_now[t - 1][fam];
+            pull_x(fam, px, mx, f);
           }
         }
         float2 wh, wx, wy;
@@ -531,11 +636,23 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
             c_now[t][fam] = f[2 + 4 * fam];
           }
           f0_now[t] = f[0];
+          if constexpr (!PER) {
+            if (!py && R == 0) {
+              // row -1's +y movers: aged into the row two back by the time level t + 1 pulls row 0
+#pragma unroll
+              for (int fam = 0; fam < 3; ++fam) c_prev1[t][fam] = ym_ghost(fam, f[4 + 4 * fam], f[2 + 4 * fam]);
+            }
+          }
         } else if (col >= K && col < K + w && gx_raw < nx) {
           float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
 #pragma unroll
           for (int p = 0; p < 13; ++p) st2(g + p * A.plane, f[p]);
         }
+      } else if (!PER && t < K && !py && R == ny) {
+        // row ny's -y movers, pulled by level t + 1 in this iteration; a_now / c_now still hold
+        // row ny - 1
+#pragma unroll
+        for (int fam = 0; fam < 3; ++fam) a_now[t][fam] = yp_ghost(fam, a_now[t][fam], c_now[t][fam]);
       }
       if (t > 1 || L0R) {
         f0_prev[t - 1] = f0_now[t - 1];
@@ -548,6 +665,17 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
     }
   }
   __pipeline_wait_prior(0);
+}
+
+// The paired wavefront with the boundary rules of any sides (even nx).
+template <int K, int COLS, int PF, bool STORE_W = false, bool L0R = false>
+__global__ void __launch_bounds__(COLS / 2, 2)
+    step2d_temporal_x2(const StepArgs<float> A, const Consts<float> Kc, const Partition P,
+                       float* __restrict__ wout = nullptr, long long wslot = 0) {
+  extern __shared__ __align__(16) float smem[];
+  run_segment(P, A.ny, [&](int strip, int ys, int ye) {
+    pair_wave<K, COLS, PF, STORE_W, L0R, false>(A, Kc, smem, strip * P.w, P.w, ys, ye, wout, wslot);
+  });
 }
 
 template <int K, int COLS, int PF, bool STORE_W = false, bool L0R = false>
@@ -647,11 +775,12 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
   return cudaGetLastError();
 }
 
-// The paired periodic kernel: COLS tile columns, COLS / 2 threads, w even.
-template <int K, int COLS, int PF, bool L0R = false>
+// The paired kernel: COLS tile columns, COLS / 2 threads, w even; PER: every side periodic.
+template <int K, int COLS, int PF, bool L0R = false, bool PER = true>
 cudaError_t launch_k_pairs(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t st, int sm_count) {
   const size_t smem = PairShape<K, COLS, PF, L0R>::floats() * sizeof(float);
-  const void* fn = reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF, false, L0R>);
+  const void* fn = PER ? reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF, false, L0R>)
+                       : reinterpret_cast<const void*>(step2d_temporal_x2<K, COLS, PF, false, L0R>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int resident = cached_resident(fn, COLS / 2, smem);
@@ -660,18 +789,22 @@ cudaError_t launch_k_pairs(const StepArgs<float>& a, const ConstsD& kd, cudaStre
   P.strips = (a.nx + P.w - 1) / P.w;
   const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
   const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
-  step2d_temporal_periodic_x2<K, COLS, PF, false, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q);
+  if constexpr (PER)
+    step2d_temporal_periodic_x2<K, COLS, PF, false, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q);
+  else
+    step2d_temporal_x2<K, COLS, PF, false, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q);
   return cudaGetLastError();
 }
 
-template <int K>
+template <int K, bool PER>
 cudaError_t launch_k_pairs_w(const StepArgs<float>& a, const ConstsD& kd, float* wout, long long wslot,
                              cudaStream_t st, int sm_count) {
   // the configuration of the forward kernel at each K
   constexpr int COLS = K <= 6 ? 256 : 192, PF = K <= 4 ? 2 : 1;
   constexpr bool L0R = K == 6;
   const size_t smem = PairShape<K, COLS, PF, L0R>::floats() * sizeof(float);
-  const void* fn = reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF, true, L0R>);
+  const void* fn = PER ? reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF, true, L0R>)
+                       : reinterpret_cast<const void*>(step2d_temporal_x2<K, COLS, PF, true, L0R>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int resident = cached_resident(fn, COLS / 2, smem);
@@ -680,9 +813,20 @@ cudaError_t launch_k_pairs_w(const StepArgs<float>& a, const ConstsD& kd, float*
   P.strips = (a.nx + P.w - 1) / P.w;
   const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
   const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
-  step2d_temporal_periodic_x2<K, COLS, PF, true, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q, wout,
-                                                                                                  wslot);
+  if constexpr (PER)
+    step2d_temporal_periodic_x2<K, COLS, PF, true, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q, wout,
+                                                                                                    wslot);
+  else
+    step2d_temporal_x2<K, COLS, PF, true, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q, wout, wslot);
   return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_k_pairs_w(const StepArgs<float>& a, const ConstsD& kd, float* wout, long long wslot,
+                             cudaStream_t st, int sm_count) {
+  const bool per = a.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC && a.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
+  return per ? launch_k_pairs_w<K, true>(a, kd, wout, wslot, st, sm_count)
+             : launch_k_pairs_w<K, false>(a, kd, wout, wslot, st, sm_count);
 }
 
 template <int K>
@@ -691,15 +835,23 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
   // paired kernel (even nx and K), the measured best at each K: 256 columns and two rows of
   // prefetch up to K = 4; at K = 6, 256 columns, one row of prefetch and the input row's f0
   // and +y movers in registers (two CTAs per SM); at K = 8, 192 columns and one row of
-  // prefetch
+  // prefetch.  Sides that are not periodic take the same shapes with their boundary rules.
   if constexpr (K % 2 == 0) {
-    if (per && a.nx % 2 == 0) {
+    if (a.nx % 2 == 0) {
+      if (per) {
+        if constexpr (K <= 4)
+          return launch_k_pairs<K, 256, 2>(a, kd, st, sm_count);
+        else if constexpr (K == 6)
+          return launch_k_pairs<K, 256, 1, true>(a, kd, st, sm_count);
+        else
+          return launch_k_pairs<K, 192, 1>(a, kd, st, sm_count);
+      }
       if constexpr (K <= 4)
-        return launch_k_pairs<K, 256, 2>(a, kd, st, sm_count);
+        return launch_k_pairs<K, 256, 2, false, false>(a, kd, st, sm_count);
       else if constexpr (K == 6)
-        return launch_k_pairs<K, 256, 1, true>(a, kd, st, sm_count);
+        return launch_k_pairs<K, 256, 1, true, false>(a, kd, st, sm_count);
       else
-        return launch_k_pairs<K, 192, 1>(a, kd, st, sm_count);
+        return launch_k_pairs<K, 192, 1, false, false>(a, kd, st, sm_count);
     }
   }
   return per ? launch_k<K, true>(a, kd, st, sm_count) : launch_k<K, false>(a, kd, st, sm_count);
@@ -710,9 +862,7 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
 bool temporal_steps_supported(int k) { return k >= 2 && k <= 8; }
 
 bool temporal_store_w_supported(const StepArgs<float>& a, int k) {
-  bool per = true;
-  for (int s = 0; s < 4; ++s) per = per && a.bc[s] == LBM_SW_BC_PERIODIC;
-  return per && a.nx % 2 == 0 && (k == 2 || k == 4 || k == 6 || k == 8);
+  return a.nx % 2 == 0 && (k == 2 || k == 4 || k == 6 || k == 8);
 }
 
 cudaError_t launch_step2d_temporal_store_w(const StepArgs<float>& a, const ConstsD& kd, int k, float* wout,

@@ -206,13 +206,15 @@ def test_vector_adjoint_equals_scalar_adjoint(nx, ny, bc, precision):
 
 
 def test_fused_launches_give_the_same_fp32_gradient():
-    """1024 x 1024 periodic FP32: the default handle fuses 4 steps per launch in the forward
-    run, in the segment replays (whose kernel also stores every level's moments) and in the
-    adjoint steps (a reverse wavefront of the same shape); a handle held to one step per launch
-    gives the same gradient, with intervals of 16 (fused launches only) and 15 (fused launches
-    and single steps).  The forward run and the replays are bit-identical; the two adjoint
-    kernels evaluate the same plain-arithmetic expressions, whose contraction into fused
-    multiply-adds the compiler may choose per kernel, so they agree to FP32 rounding."""
+    """1024 x 1024 periodic FP32: the default handle fuses 6 steps per launch in the forward
+    run and in the segment replays (whose kernel also stores every level's moments), and 4 in
+    the adjoint steps (a reverse wavefront of the same shape); a handle held to one step per
+    launch gives the same gradient, with intervals of 16 (fused adjoint launches only) and 15
+    (fused launches and single steps).  The forward run and the replays are bit-identical; the
+    two adjoint kernels evaluate the same plain-arithmetic expressions, whose contraction into
+    fused multiply-adds the compiler may choose per kernel, so they agree to FP32 rounding.
+    With walls, outflow and inflow the forward run and the replays are fused, the adjoint
+    steps single."""
     n, steps = 1024, 48
     h_true, h_guess = _workload(n)
     z = np.zeros((n, n))
@@ -225,3 +227,11 @@ def test_fused_launches_give_the_same_fp32_gradient():
         assert np.array_equal(hT_f, hT_s)
         for a, b in zip(fused, single):
             assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max(), interval
+    # walls, outflow and inflow: fused forward run and replays, single adjoint steps in both
+    bc = (W, O, I, W)
+    fused, hT_f, _ = _gpu_gradient((h_guess, z, z), steps, h_obs, precision=lbm_sw.FP32, bc=bc, interval=15)
+    single, hT_s, _ = _gpu_gradient((h_guess, z, z), steps, h_obs, precision=lbm_sw.FP32, bc=bc, interval=15,
+                                    kernel=lbm_sw.KERNEL_VEC)
+    assert np.array_equal(hT_f, hT_s)
+    for a, b in zip(fused, single):
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()

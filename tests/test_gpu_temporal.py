@@ -1,9 +1,9 @@
 """Temporal blocking (K = 2 .. 8 fused steps per launch through shared memory) against the
 one-step-per-launch kernel: every cell update is the same pull + collide, so the results
-must be equal bit for bit, on ragged grids (a strip holds up to 128 - 2K output columns
-with walls, inflow or outflow, and 192 - 2K or 256 - 2K on all-periodic domains, where even
-widths and even K take the kernel that updates two columns per thread with paired FP32
-instructions, at K = 6 with the input row's non-shifting planes in registers), with every
+must be equal bit for bit, on ragged grids (even widths and even K take the kernel that
+updates two columns per thread with paired FP32 instructions, 256 - 2K or 192 - 2K output
+columns per strip, at K = 6 with the input row's non-shifting planes in registers; the
+others a strip of 192 - 2K columns on all-periodic domains, 128 - 2K otherwise), with every
 boundary kind, for step counts that leave a remainder, and on the 4096^2 dam-break."""
 
 import numpy as np
@@ -56,7 +56,10 @@ def test_temporal_equals_single_steps_on_the_benchmark_workload():
 @pytest.mark.parametrize("nx,ny,bc,precision,want", [
     (1024, 1024, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
     (2048, 512, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
-    (1024, 1024, (W, W, W, W), lbm_sw.FP32, lbm_sw.KERNEL_VEC),
+    (1024, 1024, (W, W, W, W), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
+    (2048, 1024, (I, O, W, W), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
+    (1023, 1040, (W, W, W, W), lbm_sw.FP32, lbm_sw.KERNEL_VEC),
+    (1023, 1040, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
     (1024, 1024, (P, P, P, P), lbm_sw.FP64, lbm_sw.KERNEL_VEC),
     (512, 512, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_VEC),
 ])
@@ -76,12 +79,13 @@ def test_auto_temporal_counts_launches_and_steps():
         assert info.steps_done == 22 and info.steps_per_launch == 6 and info.kernel_launches - before == 3 + 4
 
 
+@pytest.mark.parametrize("bc", [(P, P, P, P), (W, W, W, W), (W, O, I, W), (I, W, P, P), (O, I, W, O), (P, P, W, O)],
+                         ids=lambda b: "".join("PWOI"[k] for k in b))
 @pytest.mark.parametrize("nx,ny", [(2, 3), (4, 4), (10, 7), (244, 5), (246, 9), (488, 20), (490, 33), (1024, 130)])
 @pytest.mark.parametrize("k", [2, 4, 6, 8])
-def test_paired_kernel_equals_single_steps(nx, ny, k):
-    """Even widths around the strip width (256 - 2K up to K = 4, 192 - 2K above) on periodic
-    domains, where the paired kernel runs."""
-    bc = (P, P, P, P)
+def test_paired_kernel_equals_single_steps(nx, ny, k, bc):
+    """Even widths around the strip width (256 - 2K up to K = 6, 192 - 2K at K = 8), where the
+    paired kernel runs, with every boundary kind (a width of 2 puts both x sides in one pair)."""
     F0 = inputs.random_populations(13, ny, nx, seed=7500 + nx + ny).astype(np.float32)
     for steps in (k, 3 * k + 1):
         a = _run(F0, steps, bc, lbm_sw.KERNEL_VEC)

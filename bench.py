@@ -62,7 +62,7 @@ def temporal_kernel_name(k: int) -> str:
 NCU_TRAFFIC = {
     "step2d_temporal_periodic_x2<6, 256, 1, 0, 1>": {
         "src_sha256": "13e440f3312594d4188cace7fd2ac49f8dfb5e6d94fa35b2d55c6c5652cd51ae",
-        "sources": ("temporal.cu", "scheme.cuh"), "bytes_per_launch": 1745.69e6,
+        "sources": ("temporal.cu", "temporal.cuh", "scheme.cuh"), "bytes_per_launch": 1745.69e6,
         "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of the 5 launches of "
                 "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.88 MB read + 823.81 MB "
                 "written per launch (mean)"},

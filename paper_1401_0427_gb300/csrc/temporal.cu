@@ -25,6 +25,7 @@
 
 #include "internal.h"
 #include "scheme.cuh"
+#include "temporal.cuh"
 
 namespace lbm {
 namespace {
@@ -34,21 +35,6 @@ struct TemporalShape {
   static constexpr int L0 = 5;                // level-0 ring (prefetch distance 2)
   static constexpr int RING = 3;              // rows kept per intermediate level
   static constexpr size_t smem_floats() { return static_cast<size_t>(COLS) * 13 * (L0 + RING * (K - 1)); }
-};
-
-// All-periodic domains.  Row R of level t - 1 feeds level t in three ways: its -y movers
-// (planes 4, 8, 12) to row R - 1, f0 and the x movers to row R, its +y movers (2, 6, 10)
-// to row R + 1.  Only the x movers cross columns, so for t - 1 >= 1 only they go through
-// shared memory (two rows: the one read now and the one being written); the others stay
-// in the registers of the column's thread.  Level 0 arrives by cp.async into a ring per
-// plane group that holds each group as long as it is read: the -y movers 3 rows (the row
-// read now plus two in flight), f0 and the x movers 4, the +y movers 5.
-template <int K, int COLS>
-struct PeriodicShape {
-  static constexpr int A0 = 3, B0 = 4, C0 = 5;
-  static constexpr int L0_FLOATS = COLS * (3 * A0 + 7 * B0 + 3 * C0);
-  static constexpr int LV_FLOATS = COLS * 2 * 6;
-  static constexpr size_t floats() { return static_cast<size_t>(L0_FLOATS) + (K - 1) * LV_FLOATS; }
 };
 
 // Level-0 plane p -> (group, index): A = {4, 8, 12}, B = {0, 1, 3, 5, 7, 9, 11}, C = {2, 6, 10}.
@@ -109,24 +95,6 @@ __device__ __forceinline__ void pull_level(const float* row_m, const float* row_
       else f[p4] = inflow_feq[LBM_SW_SIDE_YP * 13 + p4];
     }
   }
-}
-
-// Work of one launch: the domain is cut into `strips` column strips of width w (the last
-// one narrower) and each strip into `segments` row segments.  CTA b takes segment
-// b / strips of strip b % strips, so the CTAs resident together work on the same rows of
-// neighbouring strips and share the strips' halo columns in L2.
-struct Partition {
-  int w;             // output columns per strip (every strip but the last is exactly w wide)
-  int strips;        // ceil(nx / w)
-  int rows_per_cta;  // output rows per segment (the last segment may be shorter)
-  int segments;      // row segments per strip
-};
-
-template <class F>
-__device__ __forceinline__ void run_segment(const Partition& P, int ny, F&& segment) {
-  const int strip = static_cast<int>(blockIdx.x % P.strips);
-  const int ys = static_cast<int>(blockIdx.x / P.strips) * P.rows_per_cta;
-  if (ys < ny) segment(strip, ys, min(ny, ys + P.rows_per_cta));
 }
 
 template <int K, int COLS>
@@ -710,46 +678,6 @@ __global__ void __launch_bounds__(COLS / 2, 2)
   }
 }
 
-// Resident CTAs per SM of a kernel at its dynamic shared-memory size.
-inline int resident_ctas(const void* fn, int threads, size_t smem) {
-  int r = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fn, threads, smem) != cudaSuccess) return 1;
-  return std::max(r, 1);
-}
-
-// The same, asked once per kernel and device.
-inline int cached_resident(const void* fn, int threads, size_t smem) {
-  static std::mutex mu;
-  static std::map<std::pair<int, const void*>, int> cache;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return resident_ctas(fn, threads, smem);
-  std::lock_guard<std::mutex> lock(mu);
-  auto it = cache.find({dev, fn});
-  if (it != cache.end()) return it->second;
-  const int v = resident_ctas(fn, threads, smem);
-  cache[{dev, fn}] = v;
-  return v;
-}
-
-// Strips of equal width <= wmax, then row segments: about `waves` waves of the resident
-// CTAs (`slots` of them), rounded down to whole segments per strip, no segment shorter
-// than 2K rows (the wavefront's fill) unless the domain is.
-inline Partition partition_rows(Partition P, int ny, int K, int slots, int waves) {
-  const int min_rows = std::min(2 * K, ny);
-  int seg = std::max(1, (waves * slots) / P.strips);
-  seg = std::min(seg, std::max(1, ny / min_rows));
-  P.rows_per_cta = (ny + seg - 1) / seg;
-  P.segments = (ny + P.rows_per_cta - 1) / P.rows_per_cta;
-  return P;
-}
-
-inline Partition partition(int nx, int ny, int wmax, int K, int slots, int waves) {
-  Partition P;
-  P.strips = (nx + wmax - 1) / wmax;
-  P.w = (nx + P.strips - 1) / P.strips;
-  return partition_rows(P, ny, K, slots, waves);
-}
-
 // Launch one kernel of K steps.  Column counts: 192 for the periodic kernel (its shared
 // memory allows two CTAs per SM at K = 6 .. 8), 128 for the general one (full rings).
 template <int K, bool PER>
@@ -886,194 +814,6 @@ cudaError_t launch_step2d_temporal(const StepArgs<float>& a, const ConstsD& kd, 
     case 7: return launch_k<7>(a, kd, st, sm_count);
     case 8: return launch_k<8>(a, kd, st, sm_count);
     default: return launch_k<4>(a, kd, st, sm_count);
-  }
-}
-
-// ---------------------------------------------------------------- discrete adjoint
-// K reverse steps of the discrete adjoint per launch on an all-periodic domain:
-// Phi^{n-1} = J_C(W^{n-1})^T S^T Phi^n, where the transposed pull S^T reads population q
-// of the cell the forward step sent it to (+x movers from column c + 1, -x movers from
-// c - 1, +y movers from row R + 1, -y movers from row R - 1) and J_C^T psi =
-// (1 - s) psi + s M^T D(W)^T psi.  Level 0 is Phi^{n0} (A.src), level t is Phi^{n0 - t},
-// level K goes to A.dst; level t reads the moments W^{n0 - t} at w0 - (t - 1) * wslot.
-// The wavefront is the forward one with the roles of the y movers swapped: the +y movers
-// are read from the newest row (registers), the -y movers two rows later.  The rows of
-// moments each level needs land by cp.async with the input row, two iterations ahead.
-__host__ __device__ constexpr int adj_group(int p) {
-  return (p == 2 || p == 6 || p == 10) ? 0 : ((p == 4 || p == 8 || p == 12) ? 2 : 1);
-}
-__host__ __device__ constexpr int adj_index(int p) {
-  return adj_group(p) == 0 ? (p - 2) / 4 : (adj_group(p) == 2 ? (p - 4) / 4 : (p == 0 ? 0 : (p + 1) / 2));
-}
-
-template <int K, int COLS>
-__device__ __forceinline__ void adjoint_wave(const StepArgs<float>& A, const float* __restrict__ w0, long long wslot,
-                                             const Consts<float>& Kc, float* smem, int x0, int w, int ys, int ye) {
-  using S = PeriodicShape<K, COLS>;
-  const int c = threadIdx.x;
-  const int nx = A.nx, ny = A.ny;
-  float* const l0a = smem;
-  float* const l0b = l0a + S::A0 * 3 * COLS;
-  float* const l0c = l0b + S::B0 * 7 * COLS;
-  auto xm = [&](int t, int slot) { return smem + S::L0_FLOATS + (t - 1) * S::LV_FLOATS + slot * 6 * COLS; };
-  // moments of every level, prefetched like the input rows: [K][3 rows][3 planes][COLS]
-  auto wr = [&](int t, int slot) { return smem + S::floats() + ((t - 1) * 3 + slot) * 3 * COLS; };
-  const int gx_raw = x0 - K + c;
-  const bool in_tile = c < w + 2 * K;
-  const int gx = ((gx_raw % nx) + nx) % nx;
-  const int iters = (ye - ys) + 2 * K;
-  const float oms = 1.0f - Kc.s;
-
-  // level t as the input of level t + 1: the +y movers of the row computed now, f0 of the
-  // previous row, the -y movers of the previous two rows (stale where not computed)
-  float a_now[K][3], f0_now[K], c_now[K][3], f0_prev[K], c_prev1[K][3], c_prev2[K][3];
-#pragma unroll
-  for (int t = 0; t < K; ++t) {
-    f0_now[t] = f0_prev[t] = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = 0.0f;
-  }
-
-  auto issue_row = [&](int j) {
-    if (j < iters && in_tile) {
-      const int r = ys - K + j;
-      const int gr = ((r % ny) + ny) % ny;
-      const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
-      float* sa = l0a + (j % S::A0) * 3 * COLS + c;
-      float* sb = l0b + (j % S::B0) * 7 * COLS + c;
-      float* sc = l0c + (j % S::C0) * 3 * COLS + c;
-#pragma unroll
-      for (int p = 0; p < 13; ++p) {
-        float* d = adj_group(p) == 0 ? sa : (adj_group(p) == 1 ? sb : sc);
-        __pipeline_memcpy_async(d + adj_index(p) * COLS, g + p * A.plane, sizeof(float));
-      }
-      // the moments level t will read at iteration j (row r - t)
-#pragma unroll
-      for (int t = 1; t <= K; ++t) {
-        const int rt = ((r - t) % ny + ny) % ny;
-        const float* gw = w0 - (t - 1) * wslot + static_cast<long long>(rt) * A.pitch + gx;
-        float* d = wr(t, j % 3) + c;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) __pipeline_memcpy_async(d + q * COLS, gw + q * A.plane, sizeof(float));
-      }
-    }
-    __pipeline_commit();
-  };
-
-  issue_row(0);
-  issue_row(1);
-  for (int j = 0; j < iters; ++j) {
-    __pipeline_wait_prior(1);
-    __syncthreads();
-    issue_row(j + 2);
-#pragma unroll
-    for (int t = 1; t <= K; ++t) {
-      const int R = ys - K + j - t;
-      const bool row_ok = R >= ys - K + t && R < ye + K - t;
-      if (row_ok && c >= t && c < w + 2 * K - t) {
-        const float* wp = wr(t, j % 3) + c;
-        const float wh = wp[0], wx = wp[COLS], wy = wp[2 * COLS];
-        float psi[13];
-        if (t == 1) {
-          const float* ra = l0a + (j % S::A0) * 3 * COLS + c;                 // row R + 1
-          const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 7 * COLS + c;  // row R
-          const float* rc = l0c + ((j + S::C0 - 2) % S::C0) * 3 * COLS + c;  // row R - 1
-          psi[0] = rb[0];
-#pragma unroll
-          for (int fam = 0; fam < 3; ++fam) {
-            psi[1 + 4 * fam] = rb[(1 + 2 * fam) * COLS + 1];
-            psi[2 + 4 * fam] = ra[fam * COLS];
-            psi[3 + 4 * fam] = rb[(2 + 2 * fam) * COLS - 1];
-            psi[4 + 4 * fam] = rc[fam * COLS];
-          }
-        } else {
-          const float* x = xm(t - 1, (j + 1) & 1) + c;
-          psi[0] = f0_prev[t - 1];
-#pragma unroll
-          for (int fam = 0; fam < 3; ++fam) {
-            psi[1 + 4 * fam] = x[(2 * fam) * COLS + 1];
-            psi[2 + 4 * fam] = a_now[t - 1][fam];
-            psi[3 + 4 * fam] = x[(2 * fam + 1) * COLS - 1];
-            psi[4 + 4 * fam] = c_prev2[t - 1][fam];
-          }
-        }
-        float zh, zx, zy;
-        equilibrium_vjp(wh, wx, wy, psi, Kc, zh, zx, zy);
-        float out[13];
-#pragma unroll
-        for (int q = 0; q < 13; ++q) out[q] = oms * psi[q] + Kc.s * (q < 5 ? zh : (q < 9 ? zx : zy));
-        if (t < K) {
-          float* x = xm(t, j & 1) + c;
-#pragma unroll
-          for (int fam = 0; fam < 3; ++fam) {
-            x[(2 * fam) * COLS] = out[1 + 4 * fam];
-            x[(2 * fam + 1) * COLS] = out[3 + 4 * fam];
-            a_now[t][fam] = out[2 + 4 * fam];
-            c_now[t][fam] = out[4 + 4 * fam];
-          }
-          f0_now[t] = out[0];
-        } else if (c >= K && c < K + w && gx_raw < nx) {
-          float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
-#pragma unroll
-          for (int p = 0; p < 13; ++p) g[p * A.plane] = out[p];
-        }
-      }
-      if (t > 1) {
-        f0_prev[t - 1] = f0_now[t - 1];
-#pragma unroll
-        for (int fam = 0; fam < 3; ++fam) {
-          c_prev2[t - 1][fam] = c_prev1[t - 1][fam];
-          c_prev1[t - 1][fam] = c_now[t - 1][fam];
-        }
-      }
-    }
-  }
-  __pipeline_wait_prior(0);
-}
-
-template <int K, int COLS>
-__global__ void __launch_bounds__(COLS, 2)
-    adjoint_temporal_periodic(const StepArgs<float> A, const float* __restrict__ w0, long long wslot,
-                              const Consts<float> Kc, const Partition P) {
-  extern __shared__ __align__(16) float smem[];
-  run_segment(P, A.ny, [&](int strip, int ys, int ye) {
-    adjoint_wave<K, COLS>(A, w0, wslot, Kc, smem, strip * P.w, P.w, ys, ye);
-  });
-}
-
-namespace {
-
-template <int K>
-cudaError_t launch_adjoint_k(const StepArgs<float>& a, const float* w0, long long wslot, const ConstsD& kd,
-                             cudaStream_t st, int sm_count) {
-  constexpr int COLS = 192;
-  const size_t smem = (PeriodicShape<K, COLS>::floats() + static_cast<size_t>(K) * 3 * 3 * COLS) * sizeof(float);
-  const void* fn = reinterpret_cast<const void*>(adjoint_temporal_periodic<K, COLS>);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  const int resident = cached_resident(fn, COLS, smem);
-  const Partition P = partition(a.nx, a.ny, COLS - 2 * K, K, resident * std::max(sm_count, 1), 1);
-  const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
-  adjoint_temporal_periodic<K, COLS><<<P.strips * P.segments, COLS, smem, st>>>(a, w0, wslot, K_, P);
-  return cudaGetLastError();
-}
-
-}  // namespace
-
-bool adjoint_temporal_supported(const StepArgs<float>& a, int k) {
-  bool per = true;
-  for (int s = 0; s < 4; ++s) per = per && a.bc[s] == LBM_SW_BC_PERIODIC;
-  return per && (k == 2 || k == 4 || k == 6 || k == 8);
-}
-
-cudaError_t launch_adjoint_temporal(const StepArgs<float>& a, const float* w0, long long wslot, const ConstsD& kd,
-                                    int k, cudaStream_t st, int sm_count) {
-  if (!adjoint_temporal_supported(a, k)) return cudaErrorNotSupported;
-  switch (k) {
-    case 2: return launch_adjoint_k<2>(a, w0, wslot, kd, st, sm_count);
-    case 6: return launch_adjoint_k<6>(a, w0, wslot, kd, st, sm_count);
-    case 8: return launch_adjoint_k<8>(a, w0, wslot, kd, st, sm_count);
-    default: return launch_adjoint_k<4>(a, w0, wslot, kd, st, sm_count);
   }
 }
 

@@ -61,10 +61,10 @@ def temporal_kernel_name(k: int) -> str:
 # kernel sources it was taken on.
 NCU_TRAFFIC = {
     "step2d_temporal_periodic_x2<6, 256, 1, 0, 1>": {
-        "src_sha256": "13e440f3312594d4188cace7fd2ac49f8dfb5e6d94fa35b2d55c6c5652cd51ae",
-        "sources": ("temporal.cu", "temporal.cuh", "scheme.cuh"), "bytes_per_launch": 1745.69e6,
+        "src_sha256": "c8d896d324e08b3558ec128165997e7739956461094d6961477489546c4c7db9",
+        "sources": ("temporal.cu", "temporal.cuh", "scheme.cuh"), "bytes_per_launch": 1745.88e6,
         "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of the 5 launches of "
-                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.88 MB read + 823.81 MB "
+                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.90 MB read + 823.92 MB "
                 "written per launch (mean)"},
 }
 
@@ -689,6 +689,15 @@ def profile_case(args, local):
             sim.step(args.warmup)
             t = _timed(stream, torch, lambda: sim.step(args.steps))
         out["cells"] = n * n
+    elif args.case == "basin":
+        W = lbm_sw.WALL
+        with lbm_sw.Simulation(n, n, lam=LAM, s=S_RATE, a=A_REST, bc=(W, W, W, W), stream=stream.cuda_stream,
+                               graph_chunk=-1) as sim:
+            sim.set_state(*inputs.circular_dam_break_2d(n, seed=inputs.stream_seed(3)))
+            sim.step(args.warmup)
+            t = _timed(stream, torch, lambda: sim.step(args.steps))
+            out["steps_per_launch"] = sim.info().steps_per_launch
+        out["cells"] = n * n
     elif args.case == "shock_tube":
         h, q = inputs.dam_break_1d(1000)
         with lbm_sw.Simulation(1000, 1, dim=1, precision=lbm_sw.FP64, lam=LAM, s=S_RATE, a=0.15,
@@ -725,8 +734,10 @@ def main():
     ap.add_argument("--temporal-steps", type=int, default=0,
                     help="steps per launch of the temporal kernel (0: the library default, 6 here; for "
                          "--case batched: 0 or 1 = one step per launch)")
-    ap.add_argument("--case", choices=["step", "batched", "adjoint", "reflection", "shock_tube", "diag"], default="step",
-                    help="kernel to run for profiling (only 'step' prints the benchmark line)")
+    ap.add_argument("--case", choices=["step", "batched", "adjoint", "reflection", "basin", "shock_tube", "diag"],
+                    default="step",
+                    help="kernel to run for profiling (only 'step' prints the benchmark line; basin: the "
+                         "dam-break with walls on every side)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
                     help="population precision of the timed loop (fp32 is the workload)")
     args = ap.parse_args()

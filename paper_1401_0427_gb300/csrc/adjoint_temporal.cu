@@ -160,6 +160,206 @@ __global__ void __launch_bounds__(COLS, 2)
   });
 }
 
+// ---- Two columns per thread ----
+// The same reverse wavefront with tile columns 2c and 2c + 1 in one thread and the local
+// product J_C^T on FP32 pairs.  Shared memory per CTA: the input ring (the +y movers read
+// in the landing iteration, f0 and the x movers one iteration later, the -y movers two
+// later, each with PF rows in flight), two rows of x movers per intermediate level, and
+// the moment rows of every level (1 + PF rows each).  Rows carry two pad floats each side,
+// so the x-shifted reads of the edge pairs stay in bounds.
+template <int K, int COLS, int PF>
+struct AdjPairShape {
+  static constexpr int RS = COLS + 4;
+  static constexpr int A0 = 1 + PF, B0 = 2 + PF, C0 = 3 + PF, W0 = 1 + PF;
+  static constexpr int L0_FLOATS = RS * (3 * A0 + 7 * B0 + 3 * C0);
+  static constexpr int LV_FLOATS = RS * 2 * 6;
+  static constexpr int W_FLOATS = RS * 3 * W0;  // per level
+  static constexpr size_t floats() {
+    return static_cast<size_t>(L0_FLOATS) + (K - 1) * LV_FLOATS + static_cast<size_t>(K) * W_FLOATS;
+  }
+};
+
+// z = D(W)^T psi on a pair of cells (the products of equilibrium_vjp, contracted freely).
+__device__ __forceinline__ void equilibrium_vjp_x2(float2 h, float2 qx, float2 qy, const float2 psi[13],
+                                                   const Consts<float>& K, float2& zh, float2& zx, float2& zy) {
+  const float2 nz = dup2(K.nz);
+  auto mul = [&](float2 a, float2 b) { return fma2(a, b, nz); };
+  const float2 rh = make_float2(1.0f / h.x, 1.0f / h.y);
+  const float2 u = mul(qx, rh), v = mul(qy, rh);
+  const float2 gh = mul(dup2(2.0f * K.half_g), h);
+  const float2 inv2gh = mul(dup2(2.0f * K.inv4g), rh);
+  const float2 uu = mul(u, u), vv = mul(v, v);
+  const float2 kh = fma2(add2(uu, vv), inv2gh, dup2(0.5f));
+  const float2 kx = mul(make_float2(-u.x, -u.y), inv2gh);
+  const float2 ky = mul(make_float2(-v.x, -v.y), inv2gh);
+  const float2 Sf = add2(add2(psi[1], psi[3]), add2(psi[2], psi[4]));
+  const float2 Af = fma2(dup2(-0.25f), Sf, psi[0]);
+  const float2 Df13 = sub2(psi[1], psi[3]), Df24 = sub2(psi[2], psi[4]);
+  const float2 Sx = add2(add2(psi[5], psi[7]), add2(psi[6], psi[8]));
+  const float2 Dx13 = sub2(psi[5], psi[7]), Dx24 = sub2(psi[6], psi[8]);
+  const float2 Sy = add2(add2(psi[9], psi[11]), add2(psi[10], psi[12]));
+  const float2 Dy13 = sub2(psi[9], psi[11]), Dy24 = sub2(psi[10], psi[12]);
+  const float2 X = add2(Dx24, Dy13);
+  const float2 c = dup2(K.c), a = dup2(K.a), q = dup2(0.25f);
+  // zh = a kh Af + Sf / 4 + c (Dx13 (gh - u u) - X u v + Dy24 (gh - v v))
+  float2 t = mul(Dx13, sub2(gh, uu));
+  t = fma2(make_float2(-X.x, -X.y), mul(u, v), t);
+  t = fma2(Dy24, sub2(gh, vv), t);
+  zh = fma2(c, t, fma2(mul(a, kh), Af, mul(q, Sf)));
+  // zx = a kx Af + c Df13 + Sx / 4 + c (2 Dx13 u + X v)
+  t = fma2(add2(Dx13, Dx13), u, mul(X, v));
+  zx = fma2(c, add2(Df13, t), fma2(mul(a, kx), Af, mul(q, Sx)));
+  // zy = a ky Af + c Df24 + Sy / 4 + c (X u + 2 Dy24 v)
+  t = fma2(X, u, mul(add2(Dy24, Dy24), v));
+  zy = fma2(c, add2(Df24, t), fma2(mul(a, ky), Af, mul(q, Sy)));
+}
+
+template <int K, int COLS, int PF>
+__device__ __forceinline__ void adjoint_pair_wave(const StepArgs<float>& A, const float* __restrict__ w0,
+                                                  long long wslot, const Consts<float>& Kc, float* smem, int x0,
+                                                  int w, int ys, int ye) {
+  using S = AdjPairShape<K, COLS, PF>;
+  constexpr int RS = S::RS;
+  const int c = threadIdx.x;  // pair index: tile columns 2c, 2c + 1
+  const int col = 2 * c;
+  const int nx = A.nx, ny = A.ny;
+  float* const l0a = smem;
+  float* const l0b = l0a + S::A0 * 3 * RS;
+  float* const l0c = l0b + S::B0 * 7 * RS;
+  auto xm = [&](int t, int slot) { return smem + S::L0_FLOATS + (t - 1) * S::LV_FLOATS + slot * 6 * RS; };
+  auto wr = [&](int t, int slot) {
+    return smem + S::L0_FLOATS + (K - 1) * S::LV_FLOATS + (t - 1) * S::W_FLOATS + slot * 3 * RS;
+  };
+  auto ld2 = [](const float* q) { return *reinterpret_cast<const float2*>(q); };
+  auto st2 = [](float* q, float2 v) { *reinterpret_cast<float2*>(q) = v; };
+  const int gx_raw = x0 - K + col;
+  const bool in_tile = col < w + 2 * K;
+  const int gx = ((gx_raw % nx) + nx) % nx;
+  const int iters = (ye - ys) + 2 * K;
+  const float2 oms = dup2(1.0f - Kc.s), sv = dup2(Kc.s);
+
+  // level t as the input of level t + 1 (as adjoint_wave, on pairs)
+  float2 a_now[K][3], f0_now[K], c_now[K][3], f0_prev[K], c_prev1[K][3], c_prev2[K][3];
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    f0_now[t] = f0_prev[t] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = make_float2(0.f, 0.f);
+  }
+
+  auto issue_row = [&](int j) {
+    if (j < iters && in_tile) {
+      const int r = ys - K + j;
+      const int gr = ((r % ny) + ny) % ny;
+      const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
+      float* sa = l0a + (j % S::A0) * 3 * RS + col + 2;
+      float* sb = l0b + (j % S::B0) * 7 * RS + col + 2;
+      float* sc = l0c + (j % S::C0) * 3 * RS + col + 2;
+#pragma unroll
+      for (int p = 0; p < 13; ++p) {
+        float* d = adj_group(p) == 0 ? sa : (adj_group(p) == 1 ? sb : sc);
+        __pipeline_memcpy_async(d + adj_index(p) * RS, g + p * A.plane, 2 * sizeof(float));
+      }
+      // the moments level t reads at iteration j (row r - t)
+#pragma unroll
+      for (int t = 1; t <= K; ++t) {
+        const int rt = ((r - t) % ny + ny) % ny;
+        const float* gw = w0 - (t - 1) * wslot + static_cast<long long>(rt) * A.pitch + gx;
+        float* d = wr(t, j % S::W0) + col + 2;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) __pipeline_memcpy_async(d + q * RS, gw + q * A.plane, 2 * sizeof(float));
+      }
+    }
+    __pipeline_commit();
+  };
+
+#pragma unroll
+  for (int q = 0; q < PF; ++q) issue_row(q);
+  for (int j = 0; j < iters; ++j) {
+    __pipeline_wait_prior(PF - 1);
+    __syncthreads();
+    issue_row(j + PF);
+#pragma unroll
+    for (int t = 1; t <= K; ++t) {
+      const int R = ys - K + j - t;
+      const bool row_ok = R >= ys - K + t && R < ye + K - t;
+      if (row_ok && in_tile && col + 1 >= t && col < w + 2 * K - t) {
+        const float* wp = wr(t, j % S::W0) + col + 2;
+        const float2 wh = ld2(wp), wx = ld2(wp + RS), wy = ld2(wp + 2 * RS);
+        float2 psi[13];
+        if (t == 1) {
+          const float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;                 // row R + 1
+          const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 7 * RS + col + 2;  // row R
+          const float* rc = l0c + ((j + S::C0 - 2) % S::C0) * 3 * RS + col + 2;  // row R - 1
+          psi[0] = ld2(rb);
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            const float* px = rb + (1 + 2 * fam) * RS;  // +x movers from columns 2c + 1, 2c + 2
+            const float* mx = rb + (2 + 2 * fam) * RS;  // -x movers from columns 2c - 1, 2c
+            psi[1 + 4 * fam] = make_float2(px[1], px[2]);
+            psi[2 + 4 * fam] = ld2(ra + fam * RS);
+            psi[3 + 4 * fam] = make_float2(mx[-1], mx[0]);
+            psi[4 + 4 * fam] = ld2(rc + fam * RS);
+          }
+        } else {
+          const float* x = xm(t - 1, (j + 1) & 1) + col + 2;
+          psi[0] = f0_prev[t - 1];
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            const float* px = x + (2 * fam) * RS;
+            const float* mx = x + (2 * fam + 1) * RS;
+            psi[1 + 4 * fam] = make_float2(px[1], px[2]);
+            psi[2 + 4 * fam] = a_now[t - 1][fam];
+            psi[3 + 4 * fam] = make_float2(mx[-1], mx[0]);
+            psi[4 + 4 * fam] = c_prev2[t - 1][fam];
+          }
+        }
+        float2 zh, zx, zy;
+        equilibrium_vjp_x2(wh, wx, wy, psi, Kc, zh, zx, zy);
+        const float2 szh = fma2(sv, zh, dup2(Kc.nz)), szx = fma2(sv, zx, dup2(Kc.nz)),
+                     szy = fma2(sv, zy, dup2(Kc.nz));
+        float2 out[13];
+#pragma unroll
+        for (int q = 0; q < 13; ++q) out[q] = fma2(oms, psi[q], q < 5 ? szh : (q < 9 ? szx : szy));
+        if (t < K) {
+          float* x = xm(t, j & 1) + col + 2;
+#pragma unroll
+          for (int fam = 0; fam < 3; ++fam) {
+            st2(x + (2 * fam) * RS, out[1 + 4 * fam]);
+            st2(x + (2 * fam + 1) * RS, out[3 + 4 * fam]);
+            a_now[t][fam] = out[2 + 4 * fam];
+            c_now[t][fam] = out[4 + 4 * fam];
+          }
+          f0_now[t] = out[0];
+        } else if (col >= K && col < K + w && gx_raw < nx) {
+          float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
+#pragma unroll
+          for (int p = 0; p < 13; ++p) st2(g + p * A.plane, out[p]);
+        }
+      }
+      if (t > 1) {
+        f0_prev[t - 1] = f0_now[t - 1];
+#pragma unroll
+        for (int fam = 0; fam < 3; ++fam) {
+          c_prev2[t - 1][fam] = c_prev1[t - 1][fam];
+          c_prev1[t - 1][fam] = c_now[t - 1][fam];
+        }
+      }
+    }
+  }
+  __pipeline_wait_prior(0);
+}
+
+template <int K, int COLS, int PF>
+__global__ void __launch_bounds__(COLS / 2, 2)
+    adjoint_temporal_periodic_x2(const StepArgs<float> A, const float* __restrict__ w0, long long wslot,
+                                 const Consts<float> Kc, const Partition P) {
+  extern __shared__ __align__(16) float smem[];
+  run_segment(P, A.ny, [&](int strip, int ys, int ye) {
+    adjoint_pair_wave<K, COLS, PF>(A, w0, wslot, Kc, smem, strip * P.w, P.w, ys, ye);
+  });
+}
+
 namespace {
 
 template <int K>
@@ -177,6 +377,35 @@ cudaError_t launch_adjoint_k(const StepArgs<float>& a, const float* w0, long lon
   return cudaGetLastError();
 }
 
+template <int K, int COLS, int PF>
+cudaError_t launch_adjoint_pairs(const StepArgs<float>& a, const float* w0, long long wslot, const ConstsD& kd,
+                                 cudaStream_t st, int sm_count) {
+  const size_t smem = AdjPairShape<K, COLS, PF>::floats() * sizeof(float);
+  const void* fn = reinterpret_cast<const void*>(adjoint_temporal_periodic_x2<K, COLS, PF>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const int resident = cached_resident(fn, COLS / 2, smem);
+  Partition P = partition(a.nx, a.ny, COLS - 2 * K, K, resident * std::max(sm_count, 1), 1);
+  P.w += P.w & 1;  // even strip width
+  P.strips = (a.nx + P.w - 1) / P.w;
+  const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
+  const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
+  adjoint_temporal_periodic_x2<K, COLS, PF><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, w0, wslot, K_, Q);
+  return cudaGetLastError();
+}
+
+// Even widths at K <= 4 (the library's adjoint launches): two columns per thread, 192-column
+// strips, two rows of prefetch (97 KB of shared memory at K = 4, two CTAs per SM; measured
+// on the 1024^2 and 2048^2 inverse problems against 256 columns with one row of prefetch
+// and 128 columns with two: 9-16 % and 0.5-1.5 % faster).  Otherwise one column per thread.
+template <int K>
+cudaError_t launch_adjoint_any(const StepArgs<float>& a, const float* w0, long long wslot, const ConstsD& kd,
+                               cudaStream_t st, int sm_count) {
+  if constexpr (K <= 4)
+    if (a.nx % 2 == 0) return launch_adjoint_pairs<K, 192, 2>(a, w0, wslot, kd, st, sm_count);
+  return launch_adjoint_k<K>(a, w0, wslot, kd, st, sm_count);
+}
+
 }  // namespace
 
 bool adjoint_temporal_supported(const StepArgs<float>& a, int k) {
@@ -189,10 +418,10 @@ cudaError_t launch_adjoint_temporal(const StepArgs<float>& a, const float* w0, l
                                     int k, cudaStream_t st, int sm_count) {
   if (!adjoint_temporal_supported(a, k)) return cudaErrorNotSupported;
   switch (k) {
-    case 2: return launch_adjoint_k<2>(a, w0, wslot, kd, st, sm_count);
-    case 6: return launch_adjoint_k<6>(a, w0, wslot, kd, st, sm_count);
-    case 8: return launch_adjoint_k<8>(a, w0, wslot, kd, st, sm_count);
-    default: return launch_adjoint_k<4>(a, w0, wslot, kd, st, sm_count);
+    case 2: return launch_adjoint_any<2>(a, w0, wslot, kd, st, sm_count);
+    case 6: return launch_adjoint_any<6>(a, w0, wslot, kd, st, sm_count);
+    case 8: return launch_adjoint_any<8>(a, w0, wslot, kd, st, sm_count);
+    default: return launch_adjoint_any<4>(a, w0, wslot, kd, st, sm_count);
   }
 }
 

@@ -62,7 +62,7 @@ def temporal_kernel_name(k: int) -> str:
 NCU_TRAFFIC = {
     "step2d_temporal_periodic_x2<6, 256, 1, 0, 1>": {
         "src_sha256": "c8d896d324e08b3558ec128165997e7739956461094d6961477489546c4c7db9",
-        "sources": ("temporal.cu", "temporal.cuh", "scheme.cuh"), "bytes_per_launch": 1745.88e6,
+        "sources": ("temporal.cu", "temporal.cuh", "temporal_pair.cuh", "scheme.cuh"), "bytes_per_launch": 1745.88e6,
         "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of the 5 launches of "
                 "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.90 MB read + 823.92 MB "
                 "written per launch (mean)"},

@@ -109,10 +109,11 @@ typedef struct lbm_sw lbm_sw;
 #define LBM_SW_KERNEL_CLUSTER 3 /* 1D: all n steps of lbm_sw_step in one thread-block-cluster
                                    launch, the line held in shared memory (up to 16384 cells on a
                                    GB300; longer lines use SIMPLE) */
-#define LBM_SW_KERNEL_TEMPORAL 4 /* 2D FP32 BGK: temporal_steps steps per launch (temporal
+#define LBM_SW_KERNEL_TEMPORAL 4 /* 2D FP32: temporal_steps steps per launch (temporal
                                     blocking: a row wavefront through shared memory, 104/k bytes of
-                                    HBM traffic per cell update plus halos); the remainder of n and
-                                    other cases use VEC; results equal VEC bit for bit */
+                                    HBM traffic per cell update plus halos), BGK, or MRT with an even
+                                    nx and temporal_steps; the remainder of n, obstacles and other
+                                    cases use VEC; results equal VEC bit for bit */
 
 typedef struct lbm_sw_params {
   int dim;             /* 1 (D1Q3Q2) or 2 (D2Q5Q4Q4) */
@@ -139,9 +140,9 @@ typedef struct lbm_sw_info {
   double bytes_per_update;   /* algorithmic DRAM bytes per lattice-cell update: 2 q sizeof(T) */
   long long steps_done;      /* steps taken since the last set_state / set_populations */
   long long kernel_launches; /* kernels this handle has launched */
-  int steps_per_launch;      /* steps one step-kernel launch advances: temporal_steps for TEMPORAL
-                                (FP32 BGK), 0 for CLUSTER (all n steps of lbm_sw_step in one
-                                launch), else 1 */
+  int steps_per_launch;      /* steps one step-kernel launch advances: temporal_steps where
+                                TEMPORAL fuses steps (see LBM_SW_KERNEL_TEMPORAL), 0 for CLUSTER
+                                (all n steps of lbm_sw_step in one launch), else 1 */
 } lbm_sw_info;
 
 /* Fill *p with defaults: dim 2, FP32, g = 1, lambda = 8, s = 1.8, a = 0.05,

@@ -46,6 +46,13 @@ lbm::StepArgs<T> args(const lbm_sw* h, int src_buf) {
 
 lbm::ConstsD consts(const lbm_sw* h) { return lbm::handle_consts(h); }
 
+// Whether lbm_sw_step fuses temporal_k steps per launch: FP32 2D TEMPORAL handles without
+// obstacles, with the BGK collision or with MRT where the two-column kernel applies.
+bool temporal_active(const lbm_sw* h) {
+  return h->p.dim == 2 && h->kernel == LBM_SW_KERNEL_TEMPORAL && h->p.precision == LBM_SW_FP32 &&
+         !h->has_obstacles && (!h->mrt || lbm::temporal_mrt_supported(h->p.nx, h->temporal_k));
+}
+
 // One step from buffer `from` into the other buffer, on stream st (the TEMPORAL choice
 // takes single steps with the VEC kernel).
 cudaError_t launch_one_step(lbm_sw* h, int from, cudaStream_t st) {
@@ -308,11 +315,12 @@ int lbm_sw_step(lbm_sw* h, int n) {
       return LBM_SW_OK;
     }
   }
-  if (h->p.dim == 2 && h->kernel == LBM_SW_KERNEL_TEMPORAL && h->p.precision == LBM_SW_FP32 && !h->mrt &&
-      !h->has_obstacles) {
+  if (temporal_active(h)) {
     const int K = h->temporal_k;
     while (n >= K) {
-      cudaError_t e = lbm::launch_step2d_temporal(args<float>(h, h->cur), consts(h), K, h->stream, h->sm_count);
+      cudaError_t e = h->mrt ? lbm::launch_step2d_temporal_mrt(args<float>(h, h->cur), consts(h), K, h->stream,
+                                                               h->sm_count)
+                             : lbm::launch_step2d_temporal(args<float>(h, h->cur), consts(h), K, h->stream, h->sm_count);
       if (e != cudaSuccess) return cuda_fail(h, e, "temporal step launch");
       h->cur ^= 1;
       n -= K;
@@ -536,8 +544,7 @@ int lbm_sw_get_info(const lbm_sw* h, lbm_sw_info* out) {
   out->kernel_launches = h->launches;
   out->steps_per_launch = 1;
   if (out->kernel == LBM_SW_KERNEL_CLUSTER) out->steps_per_launch = 0;
-  if (h->kernel == LBM_SW_KERNEL_TEMPORAL && h->p.precision == LBM_SW_FP32 && !h->mrt && !h->has_obstacles)
-    out->steps_per_launch = h->temporal_k;
+  if (temporal_active(h)) out->steps_per_launch = h->temporal_k;
   return LBM_SW_OK;
 }
 

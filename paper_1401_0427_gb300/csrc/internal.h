@@ -108,6 +108,10 @@ cudaError_t launch_step2d_temporal_store_w(const StepArgs<float>& a, const Const
                                            long long wslot, cudaStream_t st, int sm_count);
 cudaError_t launch_step2d_temporal(const StepArgs<float>& a, const ConstsD& kd, int k, cudaStream_t st,
                                    int sm_count);
+// The same with the MRT collision (temporal_mrt.cu; kd.mrt set; even nx and k, any sides).
+bool temporal_mrt_supported(int nx, int k);
+cudaError_t launch_step2d_temporal_mrt(const StepArgs<float>& a, const ConstsD& kd, int k, cudaStream_t st,
+                                       int sm_count);
 
 // ---- 1D launchers (kernels_1d.cu) ----
 template <class T>

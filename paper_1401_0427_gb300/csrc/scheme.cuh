@@ -142,13 +142,13 @@ __device__ __forceinline__ void collide13(T f[13], const Consts<T>& k) {
 //       back: dg1,3 = (dXX_u/2 +- dfxx/lam)/2, dg2,4 = (-dXX_u/2 +- dfxy/lam)/2;  gy alike (r7..r9).
 template <class T>
 __device__ __forceinline__ void mrt_family4(const T d[4], T ra, T rb, T rx, T g[4]) {
-  const T a = ra * (d[0] - d[2]);
-  const T b = rb * (d[1] - d[3]);
-  const T xx = T(0.5) * rx * ((d[0] + d[2]) - (d[1] + d[3]));
-  g[0] = T(0.5) * (xx + a);
-  g[2] = T(0.5) * (xx - a);
-  g[1] = T(0.5) * (-xx + b);
-  g[3] = T(0.5) * (-xx - b);
+  const T a = mul(ra, sub(d[0], d[2]));
+  const T b = mul(rb, sub(d[1], d[3]));
+  const T xx = mul(mul(T(0.5), rx), sub(add(d[0], d[2]), add(d[1], d[3])));
+  g[0] = mul(T(0.5), add(xx, a));
+  g[2] = mul(T(0.5), sub(xx, a));
+  g[1] = mul(T(0.5), sub(b, xx));
+  g[3] = mul(T(0.5), sub(-xx, b));
 }
 
 template <class T>
@@ -158,28 +158,28 @@ __device__ __forceinline__ void collide13_mrt(T f[13], const Consts<T>& k, T& h,
   equilibrium13(h, qx, qy, k, e);
   T d[13];
 #pragma unroll
-  for (int j = 0; j < 13; ++j) d[j] = e[j] - f[j];
-  const T jx = k.r[0] * (d[1] - d[3]);
-  const T jy = k.r[1] * (d[2] - d[4]);
-  const T e5 = k.r[2] * ((d[1] + d[2]) + (d[3] + d[4]) - T(4) * d[0]) * T(0.2);
-  const T xx = k.r[3] * ((d[1] + d[3]) - (d[2] + d[4]));
-  const T s13 = T(0.5) * (e5 + xx), s24 = T(0.5) * (e5 - xx);
-  f[0] = f[0] - e5;
-  f[1] = f[1] + T(0.5) * (s13 + jx);
-  f[3] = f[3] + T(0.5) * (s13 - jx);
-  f[2] = f[2] + T(0.5) * (s24 + jy);
-  f[4] = f[4] + T(0.5) * (s24 - jy);
+  for (int j = 0; j < 13; ++j) d[j] = sub(e[j], f[j]);
+  const T jx = mul(k.r[0], sub(d[1], d[3]));
+  const T jy = mul(k.r[1], sub(d[2], d[4]));
+  const T e5 = mul(mul(k.r[2], sub(add(add(d[1], d[2]), add(d[3], d[4])), mul(T(4), d[0]))), T(0.2));
+  const T xx = mul(k.r[3], sub(add(d[1], d[3]), add(d[2], d[4])));
+  const T s13 = mul(T(0.5), add(e5, xx)), s24 = mul(T(0.5), sub(e5, xx));
+  f[0] = sub(f[0], e5);
+  f[1] = add(f[1], mul(T(0.5), add(s13, jx)));
+  f[3] = add(f[3], mul(T(0.5), sub(s13, jx)));
+  f[2] = add(f[2], mul(T(0.5), add(s24, jy)));
+  f[4] = add(f[4], mul(T(0.5), sub(s24, jy)));
   T gx[4], gy[4];
   mrt_family4(d + 5, k.r[4], k.r[5], k.r[6], gx);
   mrt_family4(d + 9, k.r[7], k.r[8], k.r[9], gy);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    f[5 + j] = f[5 + j] + gx[j];
-    f[9 + j] = f[9 + j] + gy[j];
+    f[5 + j] = add(f[5 + j], gx[j]);
+    f[9 + j] = add(f[9 + j], gy[j]);
   }
 }
 
-// Relaxation of either form (the BGK path keeps its explicitly rounded operations).
+// Relaxation of either form.
 template <class T, bool MRT>
 __device__ __forceinline__ void collide13_any(T f[13], const Consts<T>& k, T& h, T& qx, T& qy) {
   if (MRT)
@@ -250,8 +250,9 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
-// (h, qx, qy) receive the conserved moments of the pulled populations (as collide13's).
-__device__ __forceinline__ void collide13x2(float2 f[13], const Consts<float>& k, float2& h, float2& qx, float2& qy) {
+// Moments and equilibria of two cells, as moments13 and equilibrium13.
+__device__ __forceinline__ void moments_equilibrium13x2(const float2 f[13], const Consts<float>& k, float2& h,
+                                                        float2& qx, float2& qy, float2 e[13]) {
   const float2 nz = dup2(k.nz);
   auto mul2 = [&](float2 a, float2 b) { return fma2(a, b, nz); };  // the rounded product a b
   h = add2(f[0], add2(add2(f[1], f[3]), add2(f[2], f[4])));
@@ -273,7 +274,6 @@ __device__ __forceinline__ void collide13x2(float2 f[13], const Consts<float>& k
   const float2 pxx = mul2(fma2(qx, u, p), c);
   const float2 pyy = mul2(fma2(qy, v, p), c);
   const float2 pxy = mul2(mul2(mul2(qx, qy), rh), c);
-  float2 e[13];
   e[0] = f0;
   e[1] = add2(r, ax);
   e[2] = add2(r, ay);
@@ -287,6 +287,12 @@ __device__ __forceinline__ void collide13x2(float2 f[13], const Consts<float>& k
   e[10] = add2(y4, pyy);
   e[11] = sub2(y4, pxy);
   e[12] = sub2(y4, pyy);
+}
+
+// (h, qx, qy) receive the conserved moments of the pulled populations (as collide13's).
+__device__ __forceinline__ void collide13x2(float2 f[13], const Consts<float>& k, float2& h, float2& qx, float2& qy) {
+  float2 e[13];
+  moments_equilibrium13x2(f, k, h, qx, qy, e);
   const float2 s = dup2(k.s);
 #pragma unroll
   for (int j = 0; j < 13; ++j) f[j] = fma2(s, sub2(e[j], f[j]), f[j]);
@@ -295,6 +301,59 @@ __device__ __forceinline__ void collide13x2(float2 f[13], const Consts<float>& k
 __device__ __forceinline__ void collide13x2(float2 f[13], const Consts<float>& k) {
   float2 h, qx, qy;
   collide13x2(f, k, h, qx, qy);
+}
+
+// The MRT form of collide13_mrt on (cell a, cell b) pairs, operation for operation.
+__device__ __forceinline__ void mrt_family4x2(const float2 d[4], float ra, float rb, float rx, float2 nz, float2 g[4]) {
+  auto mul2 = [&](float2 a, float2 b) { return fma2(a, b, nz); };
+  const float2 half = dup2(0.5f);
+  const float2 a = mul2(dup2(ra), sub2(d[0], d[2]));
+  const float2 b = mul2(dup2(rb), sub2(d[1], d[3]));
+  const float2 xx = mul2(dup2(0.5f * rx), sub2(add2(d[0], d[2]), add2(d[1], d[3])));
+  g[0] = mul2(half, add2(xx, a));
+  g[2] = mul2(half, sub2(xx, a));
+  g[1] = mul2(half, sub2(b, xx));
+  g[3] = mul2(half, sub2(make_float2(-xx.x, -xx.y), b));
+}
+
+__device__ __forceinline__ void collide13x2_mrt(float2 f[13], const Consts<float>& k, float2& h, float2& qx,
+                                                float2& qy) {
+  const float2 nz = dup2(k.nz);
+  auto mul2 = [&](float2 a, float2 b) { return fma2(a, b, nz); };
+  float2 e[13];
+  moments_equilibrium13x2(f, k, h, qx, qy, e);
+  float2 d[13];
+#pragma unroll
+  for (int j = 0; j < 13; ++j) d[j] = sub2(e[j], f[j]);
+  const float2 half = dup2(0.5f);
+  const float2 jx = mul2(dup2(k.r[0]), sub2(d[1], d[3]));
+  const float2 jy = mul2(dup2(k.r[1]), sub2(d[2], d[4]));
+  const float2 e5 =
+      mul2(mul2(dup2(k.r[2]), sub2(add2(add2(d[1], d[2]), add2(d[3], d[4])), mul2(dup2(4.0f), d[0]))), dup2(0.2f));
+  const float2 xx = mul2(dup2(k.r[3]), sub2(add2(d[1], d[3]), add2(d[2], d[4])));
+  const float2 s13 = mul2(half, add2(e5, xx)), s24 = mul2(half, sub2(e5, xx));
+  f[0] = sub2(f[0], e5);
+  f[1] = add2(f[1], mul2(half, add2(s13, jx)));
+  f[3] = add2(f[3], mul2(half, sub2(s13, jx)));
+  f[2] = add2(f[2], mul2(half, add2(s24, jy)));
+  f[4] = add2(f[4], mul2(half, sub2(s24, jy)));
+  float2 gx[4], gy[4];
+  mrt_family4x2(d + 5, k.r[4], k.r[5], k.r[6], nz, gx);
+  mrt_family4x2(d + 9, k.r[7], k.r[8], k.r[9], nz, gy);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    f[5 + j] = add2(f[5 + j], gx[j]);
+    f[9 + j] = add2(f[9 + j], gy[j]);
+  }
+}
+
+template <bool MRT>
+__device__ __forceinline__ void collide13x2_any(float2 f[13], const Consts<float>& k, float2& h, float2& qx,
+                                                float2& qy) {
+  if constexpr (MRT)
+    collide13x2_mrt(f, k, h, qx, qy);
+  else
+    collide13x2(f, k, h, qx, qy);
 }
 
 // ---- 1D: populations f0, f+, f-, g+, g- ----

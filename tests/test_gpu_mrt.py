@@ -87,3 +87,49 @@ def test_mrt_validation_and_adjoint_rejects_mrt():
         with pytest.raises(lbm_sw.LbmSwError) as ei:
             lbm_sw.Tape(sim, 10)
         assert "BGK" in str(ei.value)
+
+
+def _run_mrt(F0, steps, bc, kernel, k=0):
+    q, ny, nx = F0.shape
+    with lbm_sw.Simulation(nx, ny, precision=lbm_sw.FP32, bc=bc, inflow=INFLOW, a=0.05, kernel=kernel,
+                           temporal_steps=k, stream=torch_stream()) as sim:
+        sim.set_relaxation(RATES_2D)
+        sim.set_populations(F0, form=lbm_sw.PRE_COLLISION)
+        spl = sim.info().steps_per_launch
+        sim.step(steps)
+        return sim.populations(), spl
+
+
+@pytest.mark.parametrize("bc", [(P, P, P, P), (W, W, W, W), (W, O, I, W), (I, W, P, P), (P, P, W, O)],
+                         ids=lambda b: "".join("PWOI"[k] for k in b))
+@pytest.mark.parametrize("nx,ny", [(2, 3), (10, 7), (244, 5), (250, 33), (488, 20), (1024, 70)])
+@pytest.mark.parametrize("k", [2, 4, 6, 8])
+def test_mrt_temporal_equals_single_steps(nx, ny, bc, k):
+    """FP32 MRT with K steps per launch (the two-column wavefront with collide13x2_mrt) against
+    one MRT step per launch: the same rounded operations on the same values, bit for bit."""
+    F0 = inputs.random_populations(13, ny, nx, seed=6100 + nx + ny).astype(np.float32)
+    for steps in (k, 3 * k + 1):
+        a, _ = _run_mrt(F0, steps, bc, lbm_sw.KERNEL_VEC)
+        b, spl = _run_mrt(F0, steps, bc, lbm_sw.KERNEL_TEMPORAL, k)
+        assert spl == k
+        assert np.array_equal(a, b), (steps, nx, ny)
+
+
+def test_mrt_temporal_choice():
+    """AUTO on 1024^2 FP32 grids keeps temporal blocking with MRT where the two-column kernel
+    applies (even width), one step per launch otherwise."""
+    for nx, bc, want in ((1024, (P, P, P, P), 6), (1024, (W, O, I, W), 6), (1025, (P, P, P, P), 1)):
+        with lbm_sw.Simulation(nx, 1024, a=0.05, bc=bc, inflow=INFLOW, stream=torch_stream()) as sim:
+            sim.set_relaxation(RATES_2D)
+            assert sim.info().steps_per_launch == want, (nx, bc)
+
+
+def test_mrt_temporal_matches_oracle():
+    F0 = inputs.random_populations(13, 40, 250, seed=6200)
+    F0 = F0.astype(np.float32).astype(np.float64)
+    bc = (W, O, I, W)
+    p = oracle.params(250, 40, a=0.05, bc=bc, inflow=INFLOW, s_moments=RATES_2D)
+    want = oracle_post(F0, 12, p, 2)
+    got, spl = _run_mrt(F0, 12, bc, lbm_sw.KERNEL_TEMPORAL, 6)
+    assert spl == 6
+    assert rel_max(got.astype(np.float64), want) <= FP32_ELEM_TOL

@@ -461,7 +461,7 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
   // and +y movers in registers (two CTAs per SM); at K = 8, 192 columns and one row of
   // prefetch.  Sides that are not periodic take the same shapes with their boundary rules.
   if constexpr (K % 2 == 0) {
-    if (a.nx % 2 == 0) {
+    if (a.nx % 2 == 0 || a.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC) {
       if (per) {
         if constexpr (K <= 4)
           return launch_k_pairs<K, 256, 2>(a, kd, st, sm_count);
@@ -486,7 +486,7 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
 bool temporal_steps_supported(int k) { return k >= 2 && k <= 8; }
 
 bool temporal_store_w_supported(const StepArgs<float>& a, int k) {
-  return a.nx % 2 == 0 && (k == 2 || k == 4 || k == 6 || k == 8);
+  return (a.nx % 2 == 0 || a.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC) && (k == 2 || k == 4 || k == 6 || k == 8);
 }
 
 cudaError_t launch_step2d_temporal_store_w(const StepArgs<float>& a, const ConstsD& kd, int k, float* wout,
@@ -666,7 +666,8 @@ cudaError_t batch_waves_build(int count, const int* nx, const int* ny, const lon
   if (e != cudaSuccess) return e;
   const PairCfg pc = pair_cfg(k);
   std::vector<int> odd, even;
-  for (int i = 0; i < count; ++i) (pc.cols > 0 && nx[i] % 2 == 0 ? even : odd).push_back(i);
+  // at even K every instance takes the paired kernel (periodic sides: any width)
+  for (int i = 0; i < count; ++i) (pc.cols > 0 ? even : odd).push_back(i);
   out->grid = std::max(1, resident * std::max(sm_count, 1));
   e = build_list(odd, nx, ny, offset, pitch, plane, k, 192 - 2 * k, false, out->grid, &out->units, &out->first,
                  &out->count);

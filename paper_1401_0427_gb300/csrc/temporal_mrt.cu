@@ -1,6 +1,6 @@
 // K fused D2Q5Q4Q4 steps per launch with the MRT collision (Eq. 2-relaxation with one rate
 // per non-conserved moment), FP32: the two-column wavefront of temporal_pair.cuh with
-// collide13x2_mrt, for even nx and K.  Every cell update is the pull + collide13_mrt of the
+// collide13x2_mrt, for even K and an even nx or periodic x sides.  Every cell update is the pull + collide13_mrt of the
 // one-step kernels on the same values, in the same rounded operations, so K steps of this
 // kernel equal K single steps bit for bit.
 #include <cuda_pipeline.h>
@@ -56,11 +56,13 @@ cudaError_t launch_mrt_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream
 
 }  // namespace
 
-bool temporal_mrt_supported(int nx, int k) { return nx % 2 == 0 && (k == 2 || k == 4 || k == 6 || k == 8); }
+bool temporal_mrt_supported(const int bc[4], int nx, int k) {
+  return (nx % 2 == 0 || bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC) && (k == 2 || k == 4 || k == 6 || k == 8);
+}
 
 cudaError_t launch_step2d_temporal_mrt(const StepArgs<float>& a, const ConstsD& kd, int k, cudaStream_t st,
                                        int sm_count) {
-  if (!kd.mrt || !temporal_mrt_supported(a.nx, k)) return cudaErrorNotSupported;
+  if (!kd.mrt || !temporal_mrt_supported(a.bc, a.nx, k)) return cudaErrorNotSupported;
   switch (k) {
     case 2: return launch_mrt_k<2>(a, kd, st, sm_count);
     case 6: return launch_mrt_k<6>(a, kd, st, sm_count);

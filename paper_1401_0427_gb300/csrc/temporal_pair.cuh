@@ -24,8 +24,9 @@ __host__ __device__ constexpr int plane_index(int p) {
 // Rows of the shared-memory planes have COLS + 4 floats, tile column i at i + 2, so a
 // pair is 8-byte aligned and a read one column beyond either end of the tile stays inside
 // the row (the cells that read it lie outside the level's valid range and are never used).
-// Input pairs land by 8-byte cp.async, which needs even nx and K: then every strip starts
-// at an even column, has an even width, and no pair straddles the periodic seam.
+// Input pairs land by 8-byte cp.async; with even K and even strip widths every strip
+// starts at an even column, so with an even nx no pair straddles the periodic seam (with
+// an odd nx the few that do land in two 4-byte copies).
 template <int K, int COLS, int PF, bool L0R = false>
 struct PairShape {
   static constexpr int RS = COLS + 4;  // floats per plane row
@@ -88,6 +89,12 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
   const bool py = PER || A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
   const bool col_live = col < w + 2 * K && (px || (gx_raw >= 0 && gx_raw < nx));
   const int gx = px ? ((gx_raw % nx) + nx) % nx : gx_raw;
+  // An odd nx (periodic x only) puts the pairs of the halo that wraps around at odd columns
+  // and one pair across the periodic seam: those land by two 4-byte copies, and the output
+  // pair at the last column stores its first lane only.
+  const int gx2 = px ? (gx + 1 == nx ? 0 : gx + 1) : gx + 1;
+  const bool split = (gx & 1) || gx2 != gx + 1;
+  const bool lane_y_out = gx_raw + 1 >= nx;
   const bool at_xm = !px && gx_raw == 0;           // lane .x is the domain's first column
   const bool at_xp = !px && gx_raw + 1 == nx - 1;  // lane .y is its last
   const int iters = (ye - ys) + 2 * K;
@@ -172,10 +179,20 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
       float* sa = l0a + (j % S::A0) * 3 * RS + col + 2;
       float* sb = l0b + (j % S::B0) * S::BP * RS + col + 2;
       float* sc = l0c + (j % S::C0) * S::CP * RS + col + 2;
+      if (!split) {
 #pragma unroll
-      for (int p = 0; p < 13; ++p) {
-        float* d = grp(p) == 0 ? sa : (grp(p) == 1 ? sb : sc);
-        __pipeline_memcpy_async(d + idx(p) * RS, g + p * A.plane, 2 * sizeof(float));
+        for (int p = 0; p < 13; ++p) {
+          float* d = grp(p) == 0 ? sa : (grp(p) == 1 ? sb : sc);
+          __pipeline_memcpy_async(d + idx(p) * RS, g + p * A.plane, 2 * sizeof(float));
+        }
+      } else {
+        const float* g2 = A.src + static_cast<long long>(gr) * A.pitch + gx2;
+#pragma unroll
+        for (int p = 0; p < 13; ++p) {
+          float* d = grp(p) == 0 ? sa : (grp(p) == 1 ? sb : sc);
+          __pipeline_memcpy_async(d + idx(p) * RS, g + p * A.plane, sizeof(float));
+          __pipeline_memcpy_async(d + idx(p) * RS + 1, g2 + p * A.plane, sizeof(float));
+        }
       }
     }
     __pipeline_commit();
@@ -272,9 +289,15 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
         collide13x2_any<MRT>(f, Kc, wh, wx, wy);
         if (STORE_W && R >= ys && R < ye && col >= K && col < K + w && gx_raw < nx) {
           float* wp = wout + (t - 1) * wslot + static_cast<long long>(R) * A.pitch + gx_raw;
-          st2(wp, wh);
-          st2(wp + A.plane, wx);
-          st2(wp + 2 * A.plane, wy);
+          if (!lane_y_out) {
+            st2(wp, wh);
+            st2(wp + A.plane, wx);
+            st2(wp + 2 * A.plane, wy);
+          } else {
+            wp[0] = wh.x;
+            wp[A.plane] = wx.x;
+            wp[2 * A.plane] = wy.x;
+          }
         }
         if (t < K) {
           float* x = xm(t, j & 1) + col + 2;
@@ -295,8 +318,13 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
           }
         } else if (col >= K && col < K + w && gx_raw < nx) {
           float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
+          if (!lane_y_out) {
 #pragma unroll
-          for (int p = 0; p < 13; ++p) st2(g + p * A.plane, f[p]);
+            for (int p = 0; p < 13; ++p) st2(g + p * A.plane, f[p]);
+          } else {
+#pragma unroll
+            for (int p = 0; p < 13; ++p) g[p * A.plane] = f[p].x;
+          }
         }
       } else if (!PER && t < K && !py && R == ny) {
         // row ny's -y movers, pulled by level t + 1 in this iteration; a_now / c_now still hold

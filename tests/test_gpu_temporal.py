@@ -1,10 +1,11 @@
 """Temporal blocking (K = 2 .. 8 fused steps per launch through shared memory) against the
 one-step-per-launch kernel: every cell update is the same pull + collide, so the results
-must be equal bit for bit, on ragged grids (even widths and even K take the kernel that
-updates two columns per thread with paired FP32 instructions, 256 - 2K or 192 - 2K output
-columns per strip, at K = 6 with the input row's non-shifting planes in registers; the
-others a strip of 192 - 2K columns on all-periodic domains, 128 - 2K otherwise), with every
-boundary kind, for step counts that leave a remainder, and on the 4096^2 dam-break."""
+must be equal bit for bit, on ragged grids (even K with an even width or periodic x sides
+takes the kernel that updates two columns per thread with paired FP32 instructions, 256 - 2K
+or 192 - 2K output columns per strip, at K = 6 with the input row's non-shifting planes in
+registers; the others a strip of 192 - 2K columns on all-periodic domains, 128 - 2K
+otherwise), with every boundary kind, for step counts that leave a remainder, and on the
+4096^2 dam-break."""
 
 import numpy as np
 import pytest
@@ -60,6 +61,7 @@ def test_temporal_equals_single_steps_on_the_benchmark_workload():
     (2048, 1024, (I, O, W, W), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
     (1023, 1040, (W, W, W, W), lbm_sw.FP32, lbm_sw.KERNEL_VEC),
     (1023, 1040, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
+    (1023, 1040, (P, P, W, O), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
     (1024, 1024, (P, P, P, P), lbm_sw.FP64, lbm_sw.KERNEL_VEC),
     (512, 512, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_VEC),
 ])
@@ -81,11 +83,13 @@ def test_auto_temporal_counts_launches_and_steps():
 
 @pytest.mark.parametrize("bc", [(P, P, P, P), (W, W, W, W), (W, O, I, W), (I, W, P, P), (O, I, W, O), (P, P, W, O)],
                          ids=lambda b: "".join("PWOI"[k] for k in b))
-@pytest.mark.parametrize("nx,ny", [(2, 3), (4, 4), (10, 7), (244, 5), (246, 9), (488, 20), (490, 33), (1024, 130)])
+@pytest.mark.parametrize("nx,ny", [(2, 3), (4, 4), (10, 7), (244, 5), (246, 9), (488, 20), (490, 33), (1024, 130),
+                                   (3, 4), (245, 9), (247, 6), (489, 20), (1023, 17)])
 @pytest.mark.parametrize("k", [2, 4, 6, 8])
 def test_paired_kernel_equals_single_steps(nx, ny, k, bc):
-    """Even widths around the strip width (256 - 2K up to K = 6, 192 - 2K at K = 8), where the
-    paired kernel runs, with every boundary kind (a width of 2 puts both x sides in one pair)."""
+    """Widths around the strip width (256 - 2K up to K = 6, 192 - 2K at K = 8), where the
+    paired kernel runs, with every boundary kind (a width of 2 puts both x sides in one pair;
+    odd widths run it with periodic x sides, the pairs across the seam in two copies)."""
     F0 = inputs.random_populations(13, ny, nx, seed=7500 + nx + ny).astype(np.float32)
     for steps in (k, 3 * k + 1):
         a = _run(F0, steps, bc, lbm_sw.KERNEL_VEC)

@@ -331,28 +331,40 @@ __global__ void __launch_bounds__(COLS, COLS == 192 ? 2 : (K <= 4 ? 5 : 3))
   }
 }
 
-// The paired wavefront with the boundary rules of any sides (even nx).
+// The paired wavefront with the boundary rules of any sides (even nx, or periodic x sides
+// with ODD).
 template <int K, int COLS, int PF, bool STORE_W = false, bool L0R = false>
 __global__ void __launch_bounds__(COLS / 2, 2)
     step2d_temporal_x2(const StepArgs<float> A, const Consts<float> Kc, const Partition P,
                        float* __restrict__ wout = nullptr, long long wslot = 0) {
   extern __shared__ __align__(16) float smem[];
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
-    pair_wave<K, COLS, PF, STORE_W, L0R, false>(A, Kc, smem, strip * P.w, P.w, ys, ye, wout, wslot);
+    pair_wave<K, COLS, PF, STORE_W, L0R, false, false, STORE_W>(A, Kc, smem, strip * P.w, P.w, ys, ye, wout, wslot);
   });
 }
 
+// Every side periodic.  The plain kernel runs even widths; the one that also stores the
+// moments of every level (the adjoint's replays) and the _odd kernels any width.
 template <int K, int COLS, int PF, bool STORE_W = false, bool L0R = false>
 __global__ void __launch_bounds__(COLS / 2, 2)
     step2d_temporal_periodic_x2(const StepArgs<float> A, const Consts<float> Kc, const Partition P,
                                 float* __restrict__ wout = nullptr, long long wslot = 0) {
   extern __shared__ __align__(16) float smem[];
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
-    pair_wave<K, COLS, PF, STORE_W, L0R>(A, Kc, smem, strip * P.w, P.w, ys, ye, wout, wslot);
+    pair_wave<K, COLS, PF, STORE_W, L0R, true, false, STORE_W>(A, Kc, smem, strip * P.w, P.w, ys, ye, wout, wslot);
   });
 }
 
-// The same for even-width instances with the paired wavefront (two columns per thread).
+template <int K, int COLS, int PF, bool L0R, bool PER>
+__global__ void __launch_bounds__(COLS / 2, 2)
+    step2d_temporal_x2_odd(const StepArgs<float> A, const Consts<float> Kc, const Partition P) {
+  extern __shared__ __align__(16) float smem[];
+  run_segment(P, A.ny, [&](int strip, int ys, int ye) {
+    pair_wave<K, COLS, PF, false, L0R, PER, false, true>(A, Kc, smem, strip * P.w, P.w, ys, ye, nullptr, 0);
+  });
+}
+
+// The same for instances of any width with the paired wavefront (two columns per thread).
 template <int K, int COLS, int PF, bool L0R>
 __global__ void __launch_bounds__(COLS / 2, 2)
     batch_temporal_pairs(const WaveUnit* __restrict__ units, const int* __restrict__ first,
@@ -369,7 +381,7 @@ __global__ void __launch_bounds__(COLS / 2, 2)
     A.pitch = U.pitch;
     A.plane = U.plane;
     for (int s = 0; s < 4; ++s) A.bc[s] = LBM_SW_BC_PERIODIC;
-    pair_wave<K, COLS, PF, false, L0R>(A, Kc, smem, U.x0, U.w, U.ys, U.ye, nullptr, 0);
+    pair_wave<K, COLS, PF, false, L0R, true, false, true>(A, Kc, smem, U.x0, U.w, U.ys, U.ye, nullptr, 0);
     __syncthreads();  // the next unit reuses the rings
   }
 }
@@ -403,8 +415,10 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
 template <int K, int COLS, int PF, bool L0R = false, bool PER = true>
 cudaError_t launch_k_pairs(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t st, int sm_count) {
   const size_t smem = PairShape<K, COLS, PF, L0R>::floats() * sizeof(float);
-  const void* fn = PER ? reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF, false, L0R>)
-                       : reinterpret_cast<const void*>(step2d_temporal_x2<K, COLS, PF, false, L0R>);
+  const bool odd = a.nx & 1;
+  const void* fn = odd ? reinterpret_cast<const void*>(step2d_temporal_x2_odd<K, COLS, PF, L0R, PER>)
+                   : PER ? reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF, false, L0R>)
+                         : reinterpret_cast<const void*>(step2d_temporal_x2<K, COLS, PF, false, L0R>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int resident = cached_resident(fn, COLS / 2, smem);
@@ -413,7 +427,9 @@ cudaError_t launch_k_pairs(const StepArgs<float>& a, const ConstsD& kd, cudaStre
   P.strips = (a.nx + P.w - 1) / P.w;
   const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
   const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
-  if constexpr (PER)
+  if (odd)
+    step2d_temporal_x2_odd<K, COLS, PF, L0R, PER><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q);
+  else if constexpr (PER)
     step2d_temporal_periodic_x2<K, COLS, PF, false, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q);
   else
     step2d_temporal_x2<K, COLS, PF, false, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q);

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(COLS / 2, 2)
     step2d_temporal_x2_mrt(const StepArgs<float> A, const Consts<float> Kc, const Partition P) {
   extern __shared__ __align__(16) float smem[];
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
-    pair_wave<K, COLS, PF, false, L0R, PER, true>(A, Kc, smem, strip * P.w, P.w, ys, ye, nullptr, 0);
+    pair_wave<K, COLS, PF, false, L0R, PER, true, true>(A, Kc, smem, strip * P.w, P.w, ys, ye, nullptr, 0);
   });
 }
 

@@ -52,7 +52,8 @@ __host__ __device__ constexpr int reg_index(int p) {
   return reg_group(p) == 0 ? (p - 4) / 4 : (reg_group(p) == 1 ? (p - 1) / 2 : (p == 0 ? 0 : (p - 2) / 4 + 1));
 }
 
-// MRT: the MRT collision (collide13x2_mrt) in place of BGK.
+// MRT: the MRT collision (collide13x2_mrt) in place of BGK.  ODD: any nx (see below); false
+// for kernels launched on even widths only.
 // With STORE_W, the moments (h, hu, hv) of every time level t = 1 .. K are also written, for
 // the launch's output cells, to the three planes at wout + (t - 1) * wslot (the replay of the
 // discrete adjoint keeps the moments of every step).
@@ -66,7 +67,7 @@ __host__ __device__ constexpr int reg_index(int p) {
 // is put in the register the next level pulls from (for level 0, in the input ring).  Tile
 // columns and rows outside the domain are neither loaded nor computed; nx is even, so a pair
 // never straddles the domain's edge.
-template <int K, int COLS, int PF, bool STORE_W, bool L0R, bool PER = true, bool MRT = false>
+template <int K, int COLS, int PF, bool STORE_W, bool L0R, bool PER = true, bool MRT = false, bool ODD = true>
 __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts<float>& Kc, float* smem, int x0, int w,
                                           int ys, int ye, float* __restrict__ wout, long long wslot) {
   using S = PairShape<K, COLS, PF, L0R>;
@@ -91,10 +92,11 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
   const int gx = px ? ((gx_raw % nx) + nx) % nx : gx_raw;
   // An odd nx (periodic x only) puts the pairs of the halo that wraps around at odd columns
   // and one pair across the periodic seam: those land by two 4-byte copies, and the output
-  // pair at the last column stores its first lane only.
+  // pair at the last column stores its first lane only.  ODD = false: nx is even (no such
+  // pairs, and no test for them).
   const int gx2 = px ? (gx + 1 == nx ? 0 : gx + 1) : gx + 1;
-  const bool split = (gx & 1) || gx2 != gx + 1;
-  const bool lane_y_out = gx_raw + 1 >= nx;
+  const bool split = ODD && ((gx & 1) || gx2 != gx + 1);
+  const bool lane_y_out = ODD && gx_raw + 1 >= nx;
   const bool at_xm = !px && gx_raw == 0;           // lane .x is the domain's first column
   const bool at_xp = !px && gx_raw + 1 == nx - 1;  // lane .y is its last
   const int iters = (ye - ys) + 2 * K;

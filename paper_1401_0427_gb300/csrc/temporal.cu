@@ -351,7 +351,8 @@ __global__ void __launch_bounds__(COLS / 2, 2)
                                 float* __restrict__ wout = nullptr, long long wslot = 0) {
   extern __shared__ __align__(16) float smem[];
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
-    pair_wave<K, COLS, PF, STORE_W, L0R, true, false, STORE_W>(A, Kc, smem, strip * P.w, P.w, ys, ye, wout, wslot);
+    pair_wave<K, COLS, PF, STORE_W, L0R, true, false, STORE_W, !STORE_W && K <= 6>(A, Kc, smem, strip * P.w, P.w, ys,
+                                                                                   ye, wout, wslot);
   });
 }
 
@@ -360,7 +361,8 @@ __global__ void __launch_bounds__(COLS / 2, 2)
     step2d_temporal_x2_odd(const StepArgs<float> A, const Consts<float> Kc, const Partition P) {
   extern __shared__ __align__(16) float smem[];
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
-    pair_wave<K, COLS, PF, false, L0R, PER, false, true>(A, Kc, smem, strip * P.w, P.w, ys, ye, nullptr, 0);
+    pair_wave<K, COLS, PF, false, L0R, PER, false, true, PER && K <= 6>(A, Kc, smem, strip * P.w, P.w, ys, ye, nullptr,
+                                                                         0);
   });
 }
 
@@ -381,7 +383,7 @@ __global__ void __launch_bounds__(COLS / 2, 2)
     A.pitch = U.pitch;
     A.plane = U.plane;
     for (int s = 0; s < 4; ++s) A.bc[s] = LBM_SW_BC_PERIODIC;
-    pair_wave<K, COLS, PF, false, L0R, true, false, true>(A, Kc, smem, U.x0, U.w, U.ys, U.ye, nullptr, 0);
+    pair_wave<K, COLS, PF, false, L0R, true, false, true, K <= 6>(A, Kc, smem, U.x0, U.w, U.ys, U.ye, nullptr, 0);
     __syncthreads();  // the next unit reuses the rings
   }
 }

@@ -5,6 +5,8 @@
 #include <cuda_pipeline.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "internal.h"
 #include "scheme.cuh"
 
@@ -53,7 +55,11 @@ __host__ __device__ constexpr int reg_index(int p) {
 }
 
 // MRT: the MRT collision (collide13x2_mrt) in place of BGK.  ODD: any nx (see below); false
-// for kernels launched on even widths only.
+// for kernels launched on even widths only.  U3: the row loop unrolled by three, so the
+// register rows of the previous rows are addressed by the iteration mod 3 instead of being
+// moved down at every iteration.  Measured at 4096^2: +6 % for the periodic BGK kernels up
+// to K = 6 and +4 % for the batch; slower where the tripled code or its registers cost more
+// than the moves (K = 8, walls, MRT, the replay that stores the moments), which move them.
 // With STORE_W, the moments (h, hu, hv) of every time level t = 1 .. K are also written, for
 // the launch's output cells, to the three planes at wout + (t - 1) * wslot (the replay of the
 // discrete adjoint keeps the moments of every step).
@@ -67,7 +73,8 @@ __host__ __device__ constexpr int reg_index(int p) {
 // is put in the register the next level pulls from (for level 0, in the input ring).  Tile
 // columns and rows outside the domain are neither loaded nor computed; nx is even, so a pair
 // never straddles the domain's edge.
-template <int K, int COLS, int PF, bool STORE_W, bool L0R, bool PER = true, bool MRT = false, bool ODD = true>
+template <int K, int COLS, int PF, bool STORE_W, bool L0R, bool PER = true, bool MRT = false, bool ODD = true,
+          bool U3 = false>
 __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts<float>& Kc, float* smem, int x0, int w,
                                           int ys, int ye, float* __restrict__ wout, long long wslot) {
   using S = PairShape<K, COLS, PF, L0R>;
@@ -101,12 +108,21 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
   const bool at_xp = !px && gx_raw + 1 == nx - 1;  // lane .y is its last
   const int iters = (ye - ys) + 2 * K;
 
-  float2 a_now[K][3], f0_now[K], c_now[K][3], f0_prev[K], c_prev1[K][3], c_prev2[K][3];
+  // Level t's values as the input of level t + 1: the -y movers of the row computed now
+  // (a_now), and f0 (f0r) and the +y movers (cr) of the rows of the last three iterations,
+  // at slot j mod 3 with U3 (the rows of iterations j, j - 1, j - 2 at slots PH, P1, P2),
+  // else at slots 0, 1, 2, moved down once the next level has read them.
+  constexpr int NF = U3 ? 3 : 2;
+  float2 a_now[K][3], f0r[K][NF], cr[K][3][3];
 #pragma unroll
   for (int t = 0; t < K; ++t) {
-    f0_now[t] = f0_prev[t] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < 3; ++q) {
+      a_now[t][q] = make_float2(0.f, 0.f);
+      if (q < NF) f0r[t][q] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 3; ++u) cr[t][q][u] = make_float2(0.f, 0.f);
+    }
   }
 
   // x sides: offsets of the edge lane's pulled x movers from the +x (-x) plane pointer at
@@ -202,16 +218,18 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
 
 #pragma unroll
   for (int q = 0; q < PF; ++q) issue_row(q);
-  for (int j = 0; j < iters; ++j) {
+  auto iter = [&](int j, auto phc) {
+    // slots of the rows of iterations j, j - 1, j - 2
+    constexpr int PH = decltype(phc)::value, P1 = U3 ? (PH + 2) % 3 : 1, P2 = U3 ? (PH + 1) % 3 : 2;
     __pipeline_wait_prior(PF - 1);  // row j has landed (this thread's copies)
     __syncthreads();                // ... and every thread's; iteration j - 1 is over everywhere
     if (L0R) {
       // f0 and the +y movers of the row just landed, into registers (read by level 1 one
       // and two iterations later)
       const float* rf = l0c + (j % S::C0) * S::CP * RS + col + 2;
-      f0_now[0] = ld2(rf);
+      f0r[0][PH] = ld2(rf);
 #pragma unroll
-      for (int fam = 0; fam < 3; ++fam) c_now[0][fam] = ld2(rf + (1 + fam) * RS);
+      for (int fam = 0; fam < 3; ++fam) cr[0][PH][fam] = ld2(rf + (1 + fam) * RS);
     }
     if constexpr (!PER) {
       // level 0 y sides, from the landed rows (this thread's own columns, which only this
@@ -223,7 +241,7 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
 #pragma unroll
         for (int fam = 0; fam < 3; ++fam) {
           if constexpr (L0R) {
-            c_prev1[0][fam] = ym_ghost(fam, ld2(ra + fam * RS), c_now[0][fam]);
+            cr[0][P1][fam] = ym_ghost(fam, ld2(ra + fam * RS), cr[0][PH][fam]);
           } else {
             const float* rc = l0c + (j % S::C0) * 3 * RS + col + 2;
             st2(l0c + ((j + S::C0 - 1) % S::C0) * 3 * RS + col + 2 + fam * RS,
@@ -237,7 +255,7 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
         const float* ra1 = l0a + ((j + S::A0 - 1) % S::A0) * 3 * RS + col + 2;
 #pragma unroll
         for (int fam = 0; fam < 3; ++fam) {
-          const float2 p2 = L0R ? c_prev1[0][fam] : ld2(l0c + ((j + S::C0 - 1) % S::C0) * 3 * RS + col + 2 + fam * RS);
+          const float2 p2 = L0R ? cr[0][P1][fam] : ld2(l0c + ((j + S::C0 - 1) % S::C0) * 3 * RS + col + 2 + fam * RS);
           st2(ra + fam * RS, yp_ghost(fam, ld2(ra1 + fam * RS), p2));
         }
       }
@@ -253,12 +271,12 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
         if (t == 1 && L0R) {
           const float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;                 // row R + 1
           const float* rb = l0b + ((j + S::B0 - 1) % S::B0) * 6 * RS + col + 2;  // row R
-          f[0] = f0_prev[0];
+          f[0] = f0r[0][P1];
 #pragma unroll
           for (int fam = 0; fam < 3; ++fam) {
             const float* px = rb + (2 * fam) * RS;      // +x movers from columns 2c - 1, 2c
             const float* mx = rb + (2 * fam + 1) * RS;  // -x movers from columns 2c + 1, 2c + 2
-            f[2 + 4 * fam] = c_prev2[0][fam];
+            f[2 + 4 * fam] = cr[0][P2][fam];
             f[4 + 4 * fam] = ld2(ra + fam * RS);
             pull_x(fam, px, mx, f);
           }
@@ -277,12 +295,12 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
           }
         } else {
           const float* x = xm(t - 1, (j + 1) & 1) + col + 2;
-          f[0] = f0_prev[t - 1];
+          f[0] = f0r[t - 1][P1];
 #pragma unroll
           for (int fam = 0; fam < 3; ++fam) {
             const float* px = x + (2 * fam) * RS;
             const float* mx = x + (2 * fam + 1) * RS;
-            f[2 + 4 * fam] = c_prev2[t - 1][fam];
+            f[2 + 4 * fam] = cr[t - 1][P2][fam];
             f[4 + 4 * fam] = a_now[t - 1][fam];
             pull_x(fam, px, mx, f);
           }
@@ -308,14 +326,14 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
             st2(x + (2 * fam) * RS, f[1 + 4 * fam]);
             st2(x + (2 * fam + 1) * RS, f[3 + 4 * fam]);
             a_now[t][fam] = f[4 + 4 * fam];
-            c_now[t][fam] = f[2 + 4 * fam];
+            cr[t][PH][fam] = f[2 + 4 * fam];
           }
-          f0_now[t] = f[0];
+          f0r[t][PH] = f[0];
           if constexpr (!PER) {
             if (!py && R == 0) {
               // row -1's +y movers: aged into the row two back by the time level t + 1 pulls row 0
 #pragma unroll
-              for (int fam = 0; fam < 3; ++fam) c_prev1[t][fam] = ym_ghost(fam, f[4 + 4 * fam], f[2 + 4 * fam]);
+              for (int fam = 0; fam < 3; ++fam) cr[t][P1][fam] = ym_ghost(fam, f[4 + 4 * fam], f[2 + 4 * fam]);
             }
           }
         } else if (col >= K && col < K + w && gx_raw < nx) {
@@ -332,17 +350,31 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
         // row ny's -y movers, pulled by level t + 1 in this iteration; a_now / c_now still hold
         // row ny - 1
 #pragma unroll
-        for (int fam = 0; fam < 3; ++fam) a_now[t][fam] = yp_ghost(fam, a_now[t][fam], c_now[t][fam]);
+        for (int fam = 0; fam < 3; ++fam) a_now[t][fam] = yp_ghost(fam, a_now[t][fam], cr[t][P1][fam]);
       }
-      if (t > 1 || L0R) {
-        f0_prev[t - 1] = f0_now[t - 1];
+      if constexpr (!U3) {
+        // level t - 1's rows move down a slot once level t has read them
+        if (t > 1 || L0R) {
+          f0r[t - 1][1] = f0r[t - 1][0];
 #pragma unroll
-        for (int fam = 0; fam < 3; ++fam) {
-          c_prev2[t - 1][fam] = c_prev1[t - 1][fam];
-          c_prev1[t - 1][fam] = c_now[t - 1][fam];
+          for (int fam = 0; fam < 3; ++fam) {
+            cr[t - 1][2][fam] = cr[t - 1][1][fam];
+            cr[t - 1][1][fam] = cr[t - 1][0][fam];
+          }
         }
       }
     }
+  };
+  if constexpr (U3) {
+    // extra iterations past iters compute and load nothing (their rows are out of range)
+    const int iters3 = (iters + 2) / 3 * 3;
+    for (int j = 0; j < iters3; j += 3) {
+      iter(j, std::integral_constant<int, 0>{});
+      iter(j + 1, std::integral_constant<int, 1>{});
+      iter(j + 2, std::integral_constant<int, 2>{});
+    }
+  } else {
+    for (int j = 0; j < iters; ++j) iter(j, std::integral_constant<int, 0>{});
   }
   __pipeline_wait_prior(0);
 }

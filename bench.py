@@ -61,10 +61,10 @@ def temporal_kernel_name(k: int) -> str:
 # kernel sources it was taken on.
 NCU_TRAFFIC = {
     "step2d_temporal_periodic_x2<6, 256, 1, 0, 1>": {
-        "src_sha256": "b8e7adf199b49693cff591b0e40f2d3504a5b41dd839b84406dd3b85b2bd8035",
-        "sources": ("temporal.cu", "temporal.cuh", "temporal_pair.cuh", "scheme.cuh"), "bytes_per_launch": 1746.00e6,
+        "src_sha256": "1662278086c45ad1c60f9ce37e2f04c62dab4f781427dd98f392a80fe22f8d6d",
+        "sources": ("temporal.cu", "temporal.cuh", "temporal_pair.cuh", "scheme.cuh"), "bytes_per_launch": 1745.88e6,
         "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of the 5 launches of "
-                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.88 MB read + 824.12 MB "
+                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.80 MB read + 824.08 MB "
                 "written per launch (mean)"},
 }
 

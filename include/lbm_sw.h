@@ -101,8 +101,8 @@ typedef struct lbm_sw lbm_sw;
 
 /* step kernel variants */
 #define LBM_SW_KERNEL_AUTO 0    /* library choice: TEMPORAL for 2D FP32 grids of >= 2^20 cells with
-                                   every side periodic, or with an even temporal_steps and an
-                                   even nx or periodic x sides, else VEC in 2D; CLUSTER in 1D */
+                                   every side periodic or an even temporal_steps, else VEC in 2D;
+                                   CLUSTER in 1D */
 #define LBM_SW_KERNEL_SIMPLE 1  /* one launch per step, one thread per cell, scalar loads */
 #define LBM_SW_KERNEL_VEC 2     /* 2D: 16-byte vectors along x (4 FP32 or 2 FP64 cells per thread),
                                    x-neighbours exchanged with warp shuffles */
@@ -112,9 +112,8 @@ typedef struct lbm_sw lbm_sw;
 #define LBM_SW_KERNEL_TEMPORAL 4 /* 2D FP32: temporal_steps steps per launch (temporal
                                     blocking: a row wavefront through shared memory, 104/k bytes of
                                     HBM traffic per cell update plus halos), BGK, or MRT with an even
-                                    temporal_steps and an even nx or periodic x sides; the
-                                    remainder of n, obstacles and other cases use VEC; results
-                                    equal VEC bit for bit */
+                                    temporal_steps; the remainder of n, obstacles and other cases
+                                    use VEC; results equal VEC bit for bit */
 
 typedef struct lbm_sw_params {
   int dim;             /* 1 (D1Q3Q2) or 2 (D2Q5Q4Q4) */

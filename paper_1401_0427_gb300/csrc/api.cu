@@ -214,12 +214,10 @@ int lbm_sw_create(const lbm_sw_params* p, lbm_sw** out) {
   const bool all_periodic = p->bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC && p->bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
   if (p->dim == 2) {
     // AUTO: temporal blocking where it was measured faster (FP32, at least 2^20 cells, all
-    // sides periodic or the two-column kernel: even K, and an even nx or periodic x sides),
-    // otherwise one vectorised step per launch
+    // sides periodic or the two-column kernel: even K), otherwise one vectorised step per
+    // launch
     const int k = p->temporal_steps ? p->temporal_steps : 6;
-    const bool x_periodic = p->bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC;
-    const bool temporal = p->precision == LBM_SW_FP32 &&
-                          (all_periodic || (k % 2 == 0 && (p->nx % 2 == 0 || x_periodic))) &&
+    const bool temporal = p->precision == LBM_SW_FP32 && (all_periodic || k % 2 == 0) &&
                           static_cast<long long>(p->nx) * p->ny >= (1LL << 20);
     h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? (temporal ? LBM_SW_KERNEL_TEMPORAL : LBM_SW_KERNEL_VEC) : p->kernel;
   } else {

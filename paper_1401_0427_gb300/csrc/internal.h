@@ -102,14 +102,13 @@ cudaError_t launch_batch_temporal(const BatchWaves& w, int k, const float* src, 
 // k fused steps per launch (temporal.cu; FP32, BGK; k in 2 .. 8): src -> dst.
 bool temporal_steps_supported(int k);
 // k fused steps that also write the moments of every level t = 1 .. k, for every cell, to
-// the three planes at wout + (t - 1) * wslot (even k, and an even nx or periodic x sides).
+// the three planes at wout + (t - 1) * wslot (even k).
 bool temporal_store_w_supported(const StepArgs<float>& a, int k);
 cudaError_t launch_step2d_temporal_store_w(const StepArgs<float>& a, const ConstsD& kd, int k, float* wout,
                                            long long wslot, cudaStream_t st, int sm_count);
 cudaError_t launch_step2d_temporal(const StepArgs<float>& a, const ConstsD& kd, int k, cudaStream_t st,
                                    int sm_count);
-// The same with the MRT collision (temporal_mrt.cu; kd.mrt set; even k, and an even nx or
-// periodic x sides).
+// The same with the MRT collision (temporal_mrt.cu; kd.mrt set; even k).
 bool temporal_mrt_supported(const int bc[4], int nx, int k);
 cudaError_t launch_step2d_temporal_mrt(const StepArgs<float>& a, const ConstsD& kd, int k, cudaStream_t st,
                                        int sm_count);

@@ -331,8 +331,7 @@ __global__ void __launch_bounds__(COLS, COLS == 192 ? 2 : (K <= 4 ? 5 : 3))
   }
 }
 
-// The paired wavefront with the boundary rules of any sides (even nx, or periodic x sides
-// with ODD).
+// The paired wavefront with the boundary rules of any sides (even nx; odd nx with ODD).
 template <int K, int COLS, int PF, bool STORE_W = false, bool L0R = false>
 __global__ void __launch_bounds__(COLS / 2, 2)
     step2d_temporal_x2(const StepArgs<float> A, const Consts<float> Kc, const Partition P,
@@ -474,27 +473,25 @@ cudaError_t launch_k_pairs_w(const StepArgs<float>& a, const ConstsD& kd, float*
 template <int K>
 cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t st, int sm_count) {
   const bool per = a.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC && a.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
-  // paired kernel (even nx and K), the measured best at each K: 256 columns and two rows of
+  // even K: the paired kernel, the measured best at each K: 256 columns and two rows of
   // prefetch up to K = 4; at K = 6, 256 columns, one row of prefetch and the input row's f0
   // and +y movers in registers (two CTAs per SM); at K = 8, 192 columns and one row of
   // prefetch.  Sides that are not periodic take the same shapes with their boundary rules.
   if constexpr (K % 2 == 0) {
-    if (a.nx % 2 == 0 || a.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC) {
-      if (per) {
-        if constexpr (K <= 4)
-          return launch_k_pairs<K, 256, 2>(a, kd, st, sm_count);
-        else if constexpr (K == 6)
-          return launch_k_pairs<K, 256, 1, true>(a, kd, st, sm_count);
-        else
-          return launch_k_pairs<K, 192, 1>(a, kd, st, sm_count);
-      }
+    if (per) {
       if constexpr (K <= 4)
-        return launch_k_pairs<K, 256, 2, false, false>(a, kd, st, sm_count);
+        return launch_k_pairs<K, 256, 2>(a, kd, st, sm_count);
       else if constexpr (K == 6)
-        return launch_k_pairs<K, 256, 1, true, false>(a, kd, st, sm_count);
+        return launch_k_pairs<K, 256, 1, true>(a, kd, st, sm_count);
       else
-        return launch_k_pairs<K, 192, 1, false, false>(a, kd, st, sm_count);
+        return launch_k_pairs<K, 192, 1>(a, kd, st, sm_count);
     }
+    if constexpr (K <= 4)
+      return launch_k_pairs<K, 256, 2, false, false>(a, kd, st, sm_count);
+    else if constexpr (K == 6)
+      return launch_k_pairs<K, 256, 1, true, false>(a, kd, st, sm_count);
+    else
+      return launch_k_pairs<K, 192, 1, false, false>(a, kd, st, sm_count);
   }
   return per ? launch_k<K, true>(a, kd, st, sm_count) : launch_k<K, false>(a, kd, st, sm_count);
 }
@@ -503,9 +500,7 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
 
 bool temporal_steps_supported(int k) { return k >= 2 && k <= 8; }
 
-bool temporal_store_w_supported(const StepArgs<float>& a, int k) {
-  return (a.nx % 2 == 0 || a.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC) && (k == 2 || k == 4 || k == 6 || k == 8);
-}
+bool temporal_store_w_supported(const StepArgs<float>&, int k) { return k == 2 || k == 4 || k == 6 || k == 8; }
 
 cudaError_t launch_step2d_temporal_store_w(const StepArgs<float>& a, const ConstsD& kd, int k, float* wout,
                                            long long wslot, cudaStream_t st, int sm_count) {

@@ -1,6 +1,6 @@
 // K fused D2Q5Q4Q4 steps per launch with the MRT collision (Eq. 2-relaxation with one rate
 // per non-conserved moment), FP32: the two-column wavefront of temporal_pair.cuh with
-// collide13x2_mrt, for even K and an even nx or periodic x sides.  Every cell update is the pull + collide13_mrt of the
+// collide13x2_mrt, for even K.  Every cell update is the pull + collide13_mrt of the
 // one-step kernels on the same values, in the same rounded operations, so K steps of this
 // kernel equal K single steps bit for bit.
 #include <cuda_pipeline.h>
@@ -56,9 +56,7 @@ cudaError_t launch_mrt_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream
 
 }  // namespace
 
-bool temporal_mrt_supported(const int bc[4], int nx, int k) {
-  return (nx % 2 == 0 || bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC) && (k == 2 || k == 4 || k == 6 || k == 8);
-}
+bool temporal_mrt_supported(const int*, int, int k) { return k == 2 || k == 4 || k == 6 || k == 8; }
 
 cudaError_t launch_step2d_temporal_mrt(const StepArgs<float>& a, const ConstsD& kd, int k, cudaStream_t st,
                                        int sm_count) {

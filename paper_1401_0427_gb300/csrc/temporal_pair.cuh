@@ -105,7 +105,8 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
   const bool split = ODD && ((gx & 1) || gx2 != gx + 1);
   const bool lane_y_out = ODD && gx_raw + 1 >= nx;
   const bool at_xm = !px && gx_raw == 0;           // lane .x is the domain's first column
-  const bool at_xp = !px && gx_raw + 1 == nx - 1;  // lane .y is its last
+  const bool at_xp = !px && gx_raw + 1 == nx - 1;  // lane .y is its last (even nx)
+  const bool at_xp_x = !px && gx_raw == nx - 1;    // lane .x is its last (odd nx)
   const int iters = (ye - ys) + 2 * K;
 
   // Level t's values as the input of level t + 1: the -y movers of the row computed now
@@ -126,22 +127,29 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
   }
 
   // x sides: offsets of the edge lane's pulled x movers from the +x (-x) plane pointer at
-  // this pair (normally -1 and 2), and the sign of the hu family's
-  int o_p1 = -1, o_p3 = 2;
-  float2 sgn1 = make_float2(1.f, 1.f);
+  // this pair (normally -1 for lane .x of the +x movers, 1 and 2 for the lanes of the -x
+  // movers), and the signs of the hu family's.  With an odd nx the last column is lane .x of
+  // a pair whose lane .y lies outside the domain (computed, never stored, never pulled).
+  int o_p1 = -1, o_p3x = 1, o_p3 = 2;
+  float sgn1x = 1.f;
+  float2 sgn3 = make_float2(1.f, 1.f);
   if (!PER) {
     const int bm = A.bc[LBM_SW_SIDE_XM], bp = A.bc[LBM_SW_SIDE_XP];
     if (at_xm && bm != LBM_SW_BC_INFLOW) {
       o_p1 = bm == LBM_SW_BC_WALL ? RS : 0;  // own -x mover / own +x mover
-      if (bm == LBM_SW_BC_WALL) sgn1.x = -1.f;
+      if (bm == LBM_SW_BC_WALL) sgn1x = -1.f;
     }
     if (at_xp && bp != LBM_SW_BC_INFLOW) {
       o_p3 = bp == LBM_SW_BC_WALL ? 1 - RS : 1;  // own +x mover / own -x mover
-      if (bp == LBM_SW_BC_WALL) sgn1.y = -1.f;
+      if (bp == LBM_SW_BC_WALL) sgn3.y = -1.f;
     }
-    // INFLOW: the column outside the domain of every x-mover row holds the inflow
-    // equilibrium (nothing else writes there)
-    const bool in_m = at_xm && bm == LBM_SW_BC_INFLOW, in_p = at_xp && bp == LBM_SW_BC_INFLOW;
+    if (at_xp_x) {
+      o_p3x = bp == LBM_SW_BC_WALL ? -RS : (bp == LBM_SW_BC_OUTFLOW ? 0 : 2);  // own +x, own -x, inflow column
+      if (bp == LBM_SW_BC_WALL) sgn3.x = -1.f;
+    }
+    // INFLOW: the column outside the domain of every x-mover row (for an odd nx the one past
+    // the pair at the last column) holds the inflow equilibrium (nothing else writes there)
+    const bool in_m = at_xm && bm == LBM_SW_BC_INFLOW, in_p = (at_xp || at_xp_x) && bp == LBM_SW_BC_INFLOW;
     if (in_m || in_p) {
       for (int fam = 0; fam < 3; ++fam) {
         const float vm = A.inflow_feq[LBM_SW_SIDE_XM * 13 + 1 + 4 * fam];
@@ -167,10 +175,11 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
       f[3 + 4 * fam] = make_float2(mx[1], mx[2]);
     } else {
       f[1 + 4 * fam] = make_float2(px[o_p1], px[0]);
-      f[3 + 4 * fam] = make_float2(mx[1], mx[o_p3]);
+      f[3 + 4 * fam] = make_float2(mx[o_p3x], mx[o_p3]);
       if (fam == 1) {
-        f[5].x *= sgn1.x;
-        f[7].y *= sgn1.y;
+        f[5].x *= sgn1x;
+        f[7].x *= sgn3.x;
+        f[7].y *= sgn3.y;
       }
     }
   };

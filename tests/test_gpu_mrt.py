@@ -106,22 +106,21 @@ def _run_mrt(F0, steps, bc, kernel, k=0):
                                    (1024, 70)])
 @pytest.mark.parametrize("k", [2, 4, 6, 8])
 def test_mrt_temporal_equals_single_steps(nx, ny, bc, k):
-    """FP32 MRT with K steps per launch (the two-column wavefront with collide13x2_mrt; odd
-    widths with periodic x sides only, else one step per launch) against one MRT step per
-    launch: the same rounded operations on the same values, bit for bit."""
+    """FP32 MRT with K steps per launch (the two-column wavefront with collide13x2_mrt) against
+    one MRT step per launch: the same rounded operations on the same values, bit for bit."""
     F0 = inputs.random_populations(13, ny, nx, seed=6100 + nx + ny).astype(np.float32)
     for steps in (k, 3 * k + 1):
         a, _ = _run_mrt(F0, steps, bc, lbm_sw.KERNEL_VEC)
         b, spl = _run_mrt(F0, steps, bc, lbm_sw.KERNEL_TEMPORAL, k)
-        assert spl == (k if nx % 2 == 0 or bc[0] == P else 1)
+        assert spl == k
         assert np.array_equal(a, b), (steps, nx, ny)
 
 
 def test_mrt_temporal_choice():
-    """AUTO on 1024^2 FP32 grids keeps temporal blocking with MRT where the two-column kernel
-    applies (even width or periodic x sides), one step per launch otherwise."""
+    """AUTO on 1024^2 FP32 grids keeps temporal blocking with MRT (the two-column kernel, any
+    width and sides)."""
     for nx, bc, want in ((1024, (P, P, P, P), 6), (1024, (W, O, I, W), 6), (1025, (P, P, P, P), 6),
-                         (1025, (P, P, W, O), 6), (1025, (W, O, I, W), 1)):
+                         (1025, (P, P, W, O), 6), (1025, (W, O, I, W), 6)):
         with lbm_sw.Simulation(nx, 1024, a=0.05, bc=bc, inflow=INFLOW, stream=torch_stream()) as sim:
             sim.set_relaxation(RATES_2D)
             assert sim.info().steps_per_launch == want, (nx, bc)

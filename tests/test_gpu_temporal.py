@@ -1,11 +1,10 @@
 """Temporal blocking (K = 2 .. 8 fused steps per launch through shared memory) against the
 one-step-per-launch kernel: every cell update is the same pull + collide, so the results
-must be equal bit for bit, on ragged grids (even K with an even width or periodic x sides
-takes the kernel that updates two columns per thread with paired FP32 instructions, 256 - 2K
-or 192 - 2K output columns per strip, at K = 6 with the input row's non-shifting planes in
-registers; the others a strip of 192 - 2K columns on all-periodic domains, 128 - 2K
-otherwise), with every boundary kind, for step counts that leave a remainder, and on the
-4096^2 dam-break."""
+must be equal bit for bit, on ragged grids (even K takes the kernel that updates two columns
+per thread with paired FP32 instructions, 256 - 2K or 192 - 2K output columns per strip, at
+K = 6 with the input row's non-shifting planes in registers; odd K a strip of 192 - 2K
+columns on all-periodic domains, 128 - 2K otherwise), with every boundary kind, for step
+counts that leave a remainder, and on the 4096^2 dam-break."""
 
 import numpy as np
 import pytest
@@ -59,7 +58,7 @@ def test_temporal_equals_single_steps_on_the_benchmark_workload():
     (2048, 512, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
     (1024, 1024, (W, W, W, W), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
     (2048, 1024, (I, O, W, W), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
-    (1023, 1040, (W, W, W, W), lbm_sw.FP32, lbm_sw.KERNEL_VEC),
+    (1023, 1040, (W, W, W, W), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
     (1023, 1040, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
     (1023, 1040, (P, P, W, O), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
     (1024, 1024, (P, P, P, P), lbm_sw.FP64, lbm_sw.KERNEL_VEC),
@@ -89,7 +88,8 @@ def test_auto_temporal_counts_launches_and_steps():
 def test_paired_kernel_equals_single_steps(nx, ny, k, bc):
     """Widths around the strip width (256 - 2K up to K = 6, 192 - 2K at K = 8), where the
     paired kernel runs, with every boundary kind (a width of 2 puts both x sides in one pair;
-    odd widths run it with periodic x sides, the pairs across the seam in two copies)."""
+    an odd width puts the last column in the first lane of a pair, and with periodic x sides
+    the pairs across the seam land in two copies)."""
     F0 = inputs.random_populations(13, ny, nx, seed=7500 + nx + ny).astype(np.float32)
     for steps in (k, 3 * k + 1):
         a = _run(F0, steps, bc, lbm_sw.KERNEL_VEC)

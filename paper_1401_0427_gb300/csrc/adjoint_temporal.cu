@@ -1,5 +1,5 @@
 // K reverse steps of the discrete adjoint per launch (temporal blocking of the adjoint
-// recurrence of adjoint.cu), FP32, all-periodic domains.
+// recurrence of adjoint.cu), FP32: all-periodic domains, and any sides with an even nx.
 #include <cuda_pipeline.h>
 #include <cuda_runtime.h>
 
@@ -214,7 +214,16 @@ __device__ __forceinline__ void equilibrium_vjp_x2(float2 h, float2 qx, float2 q
   zy = fma2(c, add2(Df24, t), fma2(mul(a, ky), Af, mul(q, Sy)));
 }
 
-template <int K, int COLS, int PF>
+// PER: every side periodic.  Otherwise (even nx) the sides that are not periodic apply the
+// transposed rules of the one-step adjoint (adjoint.cu reverse_pull): a population whose
+// forward destination lies beyond a WALL takes the cell's own mirror partner (times -1 for
+// the family normal to the wall), beyond OUTFLOW or INFLOW nothing; and where the side
+// behind a cell is OUTFLOW, the cell's own value of the population is added (the forward
+// ghost copied it).  x sides: the edge lane reads the mirror partner through a per-lane
+// offset (with the sign as an exact product) or the zero-filled column outside the domain,
+// and adds its own value where the side behind is OUTFLOW.  y sides: the register (or input
+// ring) rows that the next level pulls for the first and last rows get the rule's values.
+template <int K, int COLS, int PF, bool PER = true>
 __device__ __forceinline__ void adjoint_pair_wave(const StepArgs<float>& A, const float* __restrict__ w0,
                                                   long long wslot, const Consts<float>& Kc, float* smem, int x0,
                                                   int w, int ys, int ye) {
@@ -233,24 +242,90 @@ __device__ __forceinline__ void adjoint_pair_wave(const StepArgs<float>& A, cons
   auto ld2 = [](const float* q) { return *reinterpret_cast<const float2*>(q); };
   auto st2 = [](float* q, float2 v) { *reinterpret_cast<float2*>(q) = v; };
   const int gx_raw = x0 - K + col;
-  const bool in_tile = col < w + 2 * K;
-  const int gx = ((gx_raw % nx) + nx) % nx;
+  const bool px_ = PER || A.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC;
+  const bool py = PER || A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
+  const bool col_live = col < w + 2 * K && (px_ || (gx_raw >= 0 && gx_raw < nx));
+  const int gx = px_ ? ((gx_raw % nx) + nx) % nx : gx_raw;
+  const bool at_xm = !px_ && gx_raw == 0;           // lane .x is the domain's first column
+  const bool at_xp = !px_ && gx_raw + 1 == nx - 1;  // lane .y is its last
   const int iters = (ye - ys) + 2 * K;
   const float2 oms = dup2(1.0f - Kc.s), sv = dup2(Kc.s);
+  const float2 zero = make_float2(0.f, 0.f);
 
   // level t as the input of level t + 1 (as adjoint_wave, on pairs)
   float2 a_now[K][3], f0_now[K], c_now[K][3], f0_prev[K], c_prev1[K][3], c_prev2[K][3];
 #pragma unroll
   for (int t = 0; t < K; ++t) {
-    f0_now[t] = f0_prev[t] = make_float2(0.f, 0.f);
+    f0_now[t] = f0_prev[t] = zero;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < 3; ++q) a_now[t][q] = c_now[t][q] = c_prev1[t][q] = c_prev2[t][q] = zero;
   }
 
+  // x sides: offsets of the pulled +x movers' lane .y (normally 2) and the -x movers' lane
+  // .x (normally -1) from the plane pointers at this pair, their signs, and the additions
+  int o_a = 2, o_b = -1;
+  float sgn_a = 1.f, sgn_b = 1.f;
+  bool add_xm = false, add_xp = false;
+  if constexpr (!PER) {
+    const int bm = A.bc[LBM_SW_SIDE_XM], bp = A.bc[LBM_SW_SIDE_XP];
+    if (at_xp && bp == LBM_SW_BC_WALL) {
+      o_a = RS + 1;  // own -x mover of the last column
+      sgn_a = -1.f;  // (applied to the hu family only)
+    }
+    if (at_xm && bm == LBM_SW_BC_WALL) {
+      o_b = -RS;  // own +x mover of the first column
+      sgn_b = -1.f;
+    }
+    add_xm = at_xm && bm == LBM_SW_BC_OUTFLOW;
+    add_xp = at_xp && bp == LBM_SW_BC_OUTFLOW;
+    // the columns just outside the domain read as zero (nothing else writes there)
+    if (at_xm || at_xp) {
+      for (int fam = 0; fam < 3; ++fam) {
+        for (int q = 0; q < S::B0; ++q) {
+          float* rb = l0b + q * 7 * RS + col + 2;
+          if (at_xm) rb[(2 + 2 * fam) * RS - 1] = 0.f;
+          if (at_xp) rb[(1 + 2 * fam) * RS + 2] = 0.f;
+        }
+        for (int t = 1; t < K; ++t)
+          for (int q = 0; q < 2; ++q) {
+            float* x = xm(t, q) + col + 2;
+            if (at_xm) x[(2 * fam + 1) * RS - 1] = 0.f;
+            if (at_xp) x[(2 * fam) * RS + 2] = 0.f;
+          }
+      }
+    }
+  }
+  // the transposed pull of the x movers of family fam from the +x / -x planes at this pair
+  auto pull_x = [&](int fam, const float* px, const float* mx, float2* psi) {
+    if constexpr (PER) {
+      psi[1 + 4 * fam] = make_float2(px[1], px[2]);  // from columns 2c + 1, 2c + 2
+      psi[3 + 4 * fam] = make_float2(mx[-1], mx[0]);  // from columns 2c - 1, 2c
+    } else {
+      psi[1 + 4 * fam] = make_float2(px[1], px[o_a]);
+      psi[3 + 4 * fam] = make_float2(mx[o_b], mx[0]);
+      if (fam == 1) {
+        psi[5].y *= sgn_a;
+        psi[7].x *= sgn_b;
+      }
+      if (add_xm) psi[1 + 4 * fam].x += px[0];
+      if (add_xp) psi[3 + 4 * fam].y += mx[1];
+    }
+  };
+  // y sides: the -y movers of row -1 (from row 0's +y movers p2) and the +y movers of row ny
+  // (from row ny - 1's -y movers p4) that the pulls of rows 0 and ny - 1 read
+  auto ym_ghost = [&](int fam, float2 p2) {
+    return A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_WALL ? (fam == 2 ? make_float2(-p2.x, -p2.y) : p2) : zero;
+  };
+  auto yp_ghost = [&](int fam, float2 p4) {
+    return A.bc[LBM_SW_SIDE_YP] == LBM_SW_BC_WALL ? (fam == 2 ? make_float2(-p4.x, -p4.y) : p4) : zero;
+  };
+  const bool out_ym = !py && A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_OUTFLOW;
+  const bool out_yp = !py && A.bc[LBM_SW_SIDE_YP] == LBM_SW_BC_OUTFLOW;
+
   auto issue_row = [&](int j) {
-    if (j < iters && in_tile) {
-      const int r = ys - K + j;
-      const int gr = ((r % ny) + ny) % ny;
+    const int r = ys - K + j;
+    if (j < iters && col_live && (py || (r >= 0 && r < ny))) {
+      const int gr = py ? ((r % ny) + ny) % ny : r;
       const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
       float* sa = l0a + (j % S::A0) * 3 * RS + col + 2;
       float* sb = l0b + (j % S::B0) * 7 * RS + col + 2;
@@ -260,14 +335,19 @@ __device__ __forceinline__ void adjoint_pair_wave(const StepArgs<float>& A, cons
         float* d = adj_group(p) == 0 ? sa : (adj_group(p) == 1 ? sb : sc);
         __pipeline_memcpy_async(d + adj_index(p) * RS, g + p * A.plane, 2 * sizeof(float));
       }
+    }
+    if (j < iters && col_live) {
       // the moments level t reads at iteration j (row r - t)
 #pragma unroll
       for (int t = 1; t <= K; ++t) {
-        const int rt = ((r - t) % ny + ny) % ny;
-        const float* gw = w0 - (t - 1) * wslot + static_cast<long long>(rt) * A.pitch + gx;
-        float* d = wr(t, j % S::W0) + col + 2;
+        const int rt0 = r - t;
+        if (py || (rt0 >= 0 && rt0 < ny)) {
+          const int rt = py ? (rt0 % ny + ny) % ny : rt0;
+          const float* gw = w0 - (t - 1) * wslot + static_cast<long long>(rt) * A.pitch + gx;
+          float* d = wr(t, j % S::W0) + col + 2;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) __pipeline_memcpy_async(d + q * RS, gw + q * A.plane, 2 * sizeof(float));
+          for (int q = 0; q < 3; ++q) __pipeline_memcpy_async(d + q * RS, gw + q * A.plane, 2 * sizeof(float));
+        }
       }
     }
     __pipeline_commit();
@@ -278,12 +358,32 @@ __device__ __forceinline__ void adjoint_pair_wave(const StepArgs<float>& A, cons
   for (int j = 0; j < iters; ++j) {
     __pipeline_wait_prior(PF - 1);
     __syncthreads();
+    if constexpr (!PER) {
+      // level 0's y sides in the landed rows (this thread's own columns, which only this
+      // thread reads before the next barrier; the slots of the previous row are still
+      // intact because the next copy is issued below)
+      const int r = ys - K + j;
+      if (col_live && !py) {
+        float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;                    // +y movers of row r
+        float* ra1 = l0a + ((j + S::A0 - 1) % S::A0) * 3 * RS + col + 2;     // of row r - 1
+        float* rc = l0c + (j % S::C0) * 3 * RS + col + 2;                    // -y movers of row r
+        float* rc1 = l0c + ((j + S::C0 - 1) % S::C0) * 3 * RS + col + 2;     // of row r - 1
+#pragma unroll
+        for (int fam = 0; fam < 3; ++fam) {
+          if (r == 0) st2(rc1 + fam * RS, ym_ghost(fam, ld2(ra + fam * RS)));
+          if (r == ny) st2(ra + fam * RS, yp_ghost(fam, ld2(rc1 + fam * RS)));
+          if (out_ym && r == 1) st2(ra + fam * RS, add2(ld2(ra + fam * RS), ld2(ra1 + fam * RS)));
+          if (out_yp && r == ny - 1) st2(rc1 + fam * RS, add2(ld2(rc1 + fam * RS), ld2(rc + fam * RS)));
+        }
+      }
+    }
     issue_row(j + PF);
 #pragma unroll
     for (int t = 1; t <= K; ++t) {
       const int R = ys - K + j - t;
       const bool row_ok = R >= ys - K + t && R < ye + K - t;
-      if (row_ok && in_tile && col + 1 >= t && col < w + 2 * K - t) {
+      const bool row_live = py || (R >= 0 && R < ny);
+      if (row_ok && row_live && col_live && col + 1 >= t && col < w + 2 * K - t) {
         const float* wp = wr(t, j % S::W0) + col + 2;
         const float2 wh = ld2(wp), wx = ld2(wp + RS), wy = ld2(wp + 2 * RS);
         float2 psi[13];
@@ -294,24 +394,18 @@ __device__ __forceinline__ void adjoint_pair_wave(const StepArgs<float>& A, cons
           psi[0] = ld2(rb);
 #pragma unroll
           for (int fam = 0; fam < 3; ++fam) {
-            const float* px = rb + (1 + 2 * fam) * RS;  // +x movers from columns 2c + 1, 2c + 2
-            const float* mx = rb + (2 + 2 * fam) * RS;  // -x movers from columns 2c - 1, 2c
-            psi[1 + 4 * fam] = make_float2(px[1], px[2]);
             psi[2 + 4 * fam] = ld2(ra + fam * RS);
-            psi[3 + 4 * fam] = make_float2(mx[-1], mx[0]);
             psi[4 + 4 * fam] = ld2(rc + fam * RS);
+            pull_x(fam, rb + (1 + 2 * fam) * RS, rb + (2 + 2 * fam) * RS, psi);
           }
         } else {
           const float* x = xm(t - 1, (j + 1) & 1) + col + 2;
           psi[0] = f0_prev[t - 1];
 #pragma unroll
           for (int fam = 0; fam < 3; ++fam) {
-            const float* px = x + (2 * fam) * RS;
-            const float* mx = x + (2 * fam + 1) * RS;
-            psi[1 + 4 * fam] = make_float2(px[1], px[2]);
             psi[2 + 4 * fam] = a_now[t - 1][fam];
-            psi[3 + 4 * fam] = make_float2(mx[-1], mx[0]);
             psi[4 + 4 * fam] = c_prev2[t - 1][fam];
+            pull_x(fam, x + (2 * fam) * RS, x + (2 * fam + 1) * RS, psi);
           }
         }
         float2 zh, zx, zy;
@@ -327,14 +421,29 @@ __device__ __forceinline__ void adjoint_pair_wave(const StepArgs<float>& A, cons
           for (int fam = 0; fam < 3; ++fam) {
             st2(x + (2 * fam) * RS, out[1 + 4 * fam]);
             st2(x + (2 * fam + 1) * RS, out[3 + 4 * fam]);
+            const float2 prev = a_now[t][fam];  // row R - 1's +y movers
             a_now[t][fam] = out[2 + 4 * fam];
             c_now[t][fam] = out[4 + 4 * fam];
+            if constexpr (!PER) {
+              if (!py && R == 0) c_prev1[t][fam] = ym_ghost(fam, out[2 + 4 * fam]);
+              if (out_yp && R == ny - 1) c_prev1[t][fam] = add2(c_prev1[t][fam], out[4 + 4 * fam]);
+              if (out_ym && R == 1) a_now[t][fam] = add2(a_now[t][fam], prev);
+            }
           }
           f0_now[t] = out[0];
         } else if (col >= K && col < K + w && gx_raw < nx) {
           float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
 #pragma unroll
           for (int p = 0; p < 13; ++p) st2(g + p * A.plane, out[p]);
+        }
+      } else if (!PER && t < K && !py && R == ny) {
+        // row ny's +y movers, pulled by level t + 1 in this iteration (c_now still holds row
+        // ny - 1's -y movers; with ny = 1 the OUTFLOW addition of row 0 too)
+#pragma unroll
+        for (int fam = 0; fam < 3; ++fam) {
+          const float2 prev = a_now[t][fam];
+          a_now[t][fam] = yp_ghost(fam, c_now[t][fam]);
+          if (out_ym && ny == 1) a_now[t][fam] = add2(a_now[t][fam], prev);
         }
       }
       if (t > 1) {
@@ -360,6 +469,17 @@ __global__ void __launch_bounds__(COLS / 2, 2)
   });
 }
 
+// The same with the transposed rules of sides that are not periodic (even nx).
+template <int K, int COLS, int PF>
+__global__ void __launch_bounds__(COLS / 2, 2)
+    adjoint_temporal_x2(const StepArgs<float> A, const float* __restrict__ w0, long long wslot,
+                        const Consts<float> Kc, const Partition P) {
+  extern __shared__ __align__(16) float smem[];
+  run_segment(P, A.ny, [&](int strip, int ys, int ye) {
+    adjoint_pair_wave<K, COLS, PF, false>(A, w0, wslot, Kc, smem, strip * P.w, P.w, ys, ye);
+  });
+}
+
 namespace {
 
 template <int K>
@@ -377,11 +497,12 @@ cudaError_t launch_adjoint_k(const StepArgs<float>& a, const float* w0, long lon
   return cudaGetLastError();
 }
 
-template <int K, int COLS, int PF>
+template <int K, int COLS, int PF, bool PER>
 cudaError_t launch_adjoint_pairs(const StepArgs<float>& a, const float* w0, long long wslot, const ConstsD& kd,
                                  cudaStream_t st, int sm_count) {
   const size_t smem = AdjPairShape<K, COLS, PF>::floats() * sizeof(float);
-  const void* fn = reinterpret_cast<const void*>(adjoint_temporal_periodic_x2<K, COLS, PF>);
+  const void* fn = PER ? reinterpret_cast<const void*>(adjoint_temporal_periodic_x2<K, COLS, PF>)
+                       : reinterpret_cast<const void*>(adjoint_temporal_x2<K, COLS, PF>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int resident = cached_resident(fn, COLS / 2, smem);
@@ -390,19 +511,27 @@ cudaError_t launch_adjoint_pairs(const StepArgs<float>& a, const float* w0, long
   P.strips = (a.nx + P.w - 1) / P.w;
   const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
   const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
-  adjoint_temporal_periodic_x2<K, COLS, PF><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, w0, wslot, K_, Q);
+  if constexpr (PER)
+    adjoint_temporal_periodic_x2<K, COLS, PF><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, w0, wslot, K_, Q);
+  else
+    adjoint_temporal_x2<K, COLS, PF><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, w0, wslot, K_, Q);
   return cudaGetLastError();
 }
 
 // Even widths at K <= 4 (the library's adjoint launches): two columns per thread, 192-column
 // strips, two rows of prefetch (97 KB of shared memory at K = 4, two CTAs per SM; measured
 // on the 1024^2 and 2048^2 inverse problems against 256 columns with one row of prefetch
-// and 128 columns with two: 9-16 % and 0.5-1.5 % faster).  Otherwise one column per thread.
+// and 128 columns with two: 9-16 % and 0.5-1.5 % faster), any sides.  Otherwise one column
+// per thread (every side periodic).
 template <int K>
 cudaError_t launch_adjoint_any(const StepArgs<float>& a, const float* w0, long long wslot, const ConstsD& kd,
                                cudaStream_t st, int sm_count) {
+  bool per = true;
+  for (int s = 0; s < 4; ++s) per = per && a.bc[s] == LBM_SW_BC_PERIODIC;
   if constexpr (K <= 4)
-    if (a.nx % 2 == 0) return launch_adjoint_pairs<K, 192, 2>(a, w0, wslot, kd, st, sm_count);
+    if (a.nx % 2 == 0)
+      return per ? launch_adjoint_pairs<K, 192, 2, true>(a, w0, wslot, kd, st, sm_count)
+                 : launch_adjoint_pairs<K, 192, 2, false>(a, w0, wslot, kd, st, sm_count);
   return launch_adjoint_k<K>(a, w0, wslot, kd, st, sm_count);
 }
 
@@ -411,7 +540,8 @@ cudaError_t launch_adjoint_any(const StepArgs<float>& a, const float* w0, long l
 bool adjoint_temporal_supported(const StepArgs<float>& a, int k) {
   bool per = true;
   for (int s = 0; s < 4; ++s) per = per && a.bc[s] == LBM_SW_BC_PERIODIC;
-  return per && (k == 2 || k == 4 || k == 6 || k == 8);
+  if (per) return k == 2 || k == 4 || k == 6 || k == 8;
+  return a.nx % 2 == 0 && (k == 2 || k == 4);  // the two-column kernel
 }
 
 cudaError_t launch_adjoint_temporal(const StepArgs<float>& a, const float* w0, long long wslot, const ConstsD& kd,

@@ -260,3 +260,32 @@ def test_fused_adjoint_on_ragged_grids(nx, ny, k):
     assert np.array_equal(h_a, h_b)
     for a, b in zip(g_a, g_b):
         assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("bc", [(W, W, W, W), (W, O, I, W), (I, W, P, P), (O, I, W, O), (P, P, W, O), (O, O, O, O)],
+                         ids=lambda b: "".join("PWOI"[k] for k in b))
+@pytest.mark.parametrize("nx,ny", [(2, 3), (10, 1), (10, 2), (7, 5), (246, 9), (250, 33)])
+@pytest.mark.parametrize("k", [2, 4])
+def test_fused_adjoint_with_boundaries(nx, ny, bc, k):
+    """The reverse wavefront with the transposed rules of walls, inflow and outflow (two
+    columns per thread, even widths; odd widths take single adjoint steps) against one adjoint
+    step per launch, on grids one or two rows high and one pair wide among others.  The bound
+    is FP32 rounding of the gradient's scale (its largest component): in one row between two
+    walls dL/dhv is orders of magnitude below dL/dh and carries the same absolute rounding."""
+    steps = 24
+    W0 = [x.reshape(ny, nx) for x in inputs.random_states(nx * ny, seed=520 + nx + ny, h=(0.8, 1.4), speed=0.25)]
+    h_obs = np.ones((ny, nx))
+    out = []
+    for kernel in (lbm_sw.KERNEL_TEMPORAL, lbm_sw.KERNEL_VEC):
+        with lbm_sw.Simulation(nx, ny, precision=lbm_sw.FP32, kernel=kernel, temporal_steps=k, bc=bc, inflow=INFLOW,
+                               stream=torch_stream()) as sim:
+            sim.set_state(*W0)
+            with lbm_sw.Tape(sim, steps) as tape:
+                tape.record()
+                hT = sim.moments()[0]
+                out.append((hT, tape.adjoint(hT - h_obs, want_momentum=True)))
+    (h_a, g_a), (h_b, g_b) = out
+    assert np.array_equal(h_a, h_b)
+    scale = max(np.abs(b).max() for b in g_b)
+    for a, b in zip(g_a, g_b):
+        assert np.abs(a - b).max() <= 1e-5 * scale

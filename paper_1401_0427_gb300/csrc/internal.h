@@ -59,9 +59,10 @@ cudaError_t launch_moments2d_planes(const StepArgs<T>& a, T* w_out, cudaStream_t
 template <class Tin, class Tout>
 cudaError_t launch_convert(const Tin* in, Tout* out, long long n, cudaStream_t st);
 
-// K reverse steps of the discrete adjoint per launch (adjoint_temporal.cu; FP32, every side periodic,
-// k in {2, 4, 6, 8}): Phi^{n0} in a.src -> Phi^{n0 - k} in a.dst; reverse step t reads the
-// moments W^{n0 - t} at w0 - (t - 1) * wslot.
+// K reverse steps of the discrete adjoint per launch (adjoint_temporal.cu; FP32; every side
+// periodic with k in {2, 4, 6, 8}, or any sides with an even nx and k in {2, 4}): Phi^{n0}
+// in a.src -> Phi^{n0 - k} in a.dst; reverse step t reads the moments W^{n0 - t} at
+// w0 - (t - 1) * wslot.
 bool adjoint_temporal_supported(const StepArgs<float>& a, int k);
 cudaError_t launch_adjoint_temporal(const StepArgs<float>& a, const float* w0, long long wslot, const ConstsD& kd,
                                     int k, cudaStream_t st, int sm_count);

@@ -61,10 +61,10 @@ def temporal_kernel_name(k: int) -> str:
 # kernel sources it was taken on.
 NCU_TRAFFIC = {
     "step2d_temporal_periodic_x2<6, 256, 1, 0, 1>": {
-        "src_sha256": "1662278086c45ad1c60f9ce37e2f04c62dab4f781427dd98f392a80fe22f8d6d",
+        "src_sha256": "978d482fd72f6aa60a8f008255e14cf410d352b5cd218121f14fec38d3dab2cb",
         "sources": ("temporal.cu", "temporal.cuh", "temporal_pair.cuh", "scheme.cuh"), "bytes_per_launch": 1745.88e6,
         "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of the 5 launches of "
-                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.80 MB read + 824.08 MB "
+                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.88 MB read + 824.00 MB "
                 "written per launch (mean)"},
 }
 

@@ -719,6 +719,14 @@ def profile_case(args, local):
             t = _timed(stream, torch, lambda: sim.step(args.steps))
             out["steps_per_launch"] = sim.info().steps_per_launch
         out["cells"] = n * n
+    elif args.case == "mrt":
+        with lbm_sw.Simulation(n, n, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream, graph_chunk=-1) as sim:
+            sim.set_relaxation(MRT_RATES)
+            sim.set_state(*inputs.circular_dam_break_2d(n, seed=inputs.stream_seed(3)))
+            sim.step(args.warmup)
+            t = _timed(stream, torch, lambda: sim.step(args.steps))
+            out["steps_per_launch"] = sim.info().steps_per_launch
+        out["cells"] = n * n
     elif args.case == "shock_tube":
         h, q = inputs.dam_break_1d(1000)
         with lbm_sw.Simulation(1000, 1, dim=1, precision=lbm_sw.FP64, lam=LAM, s=S_RATE, a=0.15,
@@ -755,10 +763,10 @@ def main():
     ap.add_argument("--temporal-steps", type=int, default=0,
                     help="steps per launch of the temporal kernel (0: the library default, 6 here; for "
                          "--case batched: 0 or 1 = one step per launch)")
-    ap.add_argument("--case", choices=["step", "batched", "adjoint", "reflection", "basin", "shock_tube", "diag"],
+    ap.add_argument("--case", choices=["step", "batched", "adjoint", "reflection", "basin", "mrt", "shock_tube", "diag"],
                     default="step",
                     help="kernel to run for profiling (only 'step' prints the benchmark line; basin: the "
-                         "dam-break with walls on every side)")
+                         "dam-break with walls on every side; mrt: the dam-break with the MRT collision)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
                     help="population precision of the timed loop (fp32 is the workload)")
     args = ap.parse_args()

@@ -112,7 +112,12 @@ def _patch_step(F, x0, y0, w, h):
     ny, nx = F.shape[1:]
     ys = np.arange(y0 - 1, y0 + h + 1) % ny
     xs = np.arange(x0 - 1, x0 + w + 1) % nx
-    sub = F[:, ys][:, :, xs].astype(np.float64)
+    return _haloed_patch_step(F[:, ys][:, :, xs], w, h)
+
+
+def _haloed_patch_step(sub, w, h):
+    """The same from the patch with its one-cell halo, sub[13][h + 2][w + 2]."""
+    sub = sub.astype(np.float64)
     p = oracle.params(w + 2, h + 2, a=0.05)
     streamed = oracle.stream_2d(np.ascontiguousarray(sub), p)  # halo ring is garbage, interior exact
     interior = np.ascontiguousarray(streamed[:, 1:-1, 1:-1])
@@ -150,3 +155,37 @@ def test_dam_break_4096_d4_symmetry_and_conservation():
     assert h.max() < 2.0 + 1e-5 and not np.array_equal(h, W0[0])  # FP32 rounding of the untouched column
     assert abs(d1[0] - d0[0]) <= 1e-6 * d0[0]  # FP32 state, FP64 totals
     assert abs(d1[1]) <= 1e-6 * d0[0] and abs(d1[2]) <= 1e-6 * d0[0]
+
+
+def test_grid_past_32_bit_indices():
+    """16384 x 12288 cells in FP32: each population buffer holds 2.6e9 elements, past 32-bit
+    indexing.  The temporal kernel (6 steps per launch) equals 6 single steps bit for bit,
+    and one more step on patches at the far end of the buffers (the last rows and columns)
+    matches the oracle.  The state is a seeded random 1024 x 1536 tile repeated."""
+    import torch
+
+    nx, ny, tw, th = 16384, 12288, 1024, 1536
+    tile = inputs.random_states(tw * th, seed=inputs.stream_seed(7), h=(0.8, 1.4), speed=0.25)
+    W0 = [np.tile(w.reshape(th, tw), (ny // th, nx // tw)) for w in tile]
+    out = []
+    for kernel in (lbm_sw.KERNEL_TEMPORAL, lbm_sw.KERNEL_VEC):
+        with lbm_sw.Simulation(nx, ny, precision=lbm_sw.FP32, a=0.05, kernel=kernel, stream=torch_stream()) as sim:
+            assert sim.info().steps_per_launch == (6 if kernel == lbm_sw.KERNEL_TEMPORAL else 1)
+            sim.set_state(*W0)
+            sim.step(6)
+            F = torch.empty((13, ny, nx), dtype=torch.float32, device="cuda")
+            sim.populations_into(F)
+            out.append(F)
+            if kernel == lbm_sw.KERNEL_VEC:
+                sim.step(1)
+                F1 = torch.empty_like(F)
+                sim.populations_into(F1)
+    assert torch.equal(out[0], out[1])
+    F = out[1]
+    for x0, y0 in [(nx - 40, ny - 40), (0, ny - 40), (nx - 40, 0), (8190, ny - 40)]:
+        ys = torch.arange(y0 - 1, y0 + 41, device="cuda") % ny
+        xs = torch.arange(x0 - 1, x0 + 41, device="cuda") % nx
+        sub = F[:, ys][:, :, xs].cpu().numpy()
+        want = _haloed_patch_step(sub, 40, 40)
+        got = F1[:, y0:y0 + 40, x0:x0 + 40].cpu().numpy().astype(np.float64)
+        assert rel_max(got, want) <= FP32_ELEM_TOL, (x0, y0)

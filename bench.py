@@ -47,12 +47,12 @@ REF_SAMPLE = 512   # side of the periodic window the CPU oracle advances per ref
 KERNEL_NAMES = {(2, "f32"): "step2d_vec<float>", (2, "f64"): "step2d_vec<double>"}
 
 
-def temporal_kernel_name(k: int) -> str:
+def temporal_kernel_name(k: int, cells: int = 4096 * 4096) -> str:
     """The periodic temporal kernel the library launches for an even-width grid."""
     if k % 2:
         return f"step2d_temporal_periodic<{k}, 192>"
     if k == 6:
-        return "step2d_temporal_periodic_x2<6, 256, 1, 0, 1>"
+        return f"step2d_temporal_periodic_x2<6, {128 if cells < 2 ** 23 else 256}, 1, 0, 1>"
     return f"step2d_temporal_periodic_x2<{k}, 256, 2>" if k <= 4 else f"step2d_temporal_periodic_x2<{k}, 192, 1>"
 
 
@@ -331,7 +331,7 @@ def run_ours(args, world, rank, local):
     sim.set_state(*W0)
     info = sim.info()
     unit = max(1, info.steps_per_launch)  # steps per launch of the step kernel
-    kname = temporal_kernel_name(unit) if unit > 1 else KERNEL_NAMES[(lbm_sw.KERNEL_VEC, dt_name)]
+    kname = temporal_kernel_name(unit, cells) if unit > 1 else KERNEL_NAMES[(lbm_sw.KERNEL_VEC, dt_name)]
     # The timed region is exactly --steps time steps: full launches of `unit` steps, then
     # the remainder (one step per launch, bit-identical results).
     nfull, rem = divmod(args.steps, unit)
@@ -450,7 +450,7 @@ def variants(args, W0, stream, lbm_sw, torch):
         bpl = BYTES_PER_LUP["f64" if name == "fp64" else "f32"]
         spl = max(1, info.steps_per_launch)
         out[name] = {"MLUPS": N * N / (ms * 1e-3) / 1e6, "ms_per_step": ms, "steps_per_launch": spl,
-                     "kernel": temporal_kernel_name(spl) if spl > 1
+                     "kernel": temporal_kernel_name(spl, N * N) if spl > 1
                      else KERNEL_NAMES[(lbm_sw.KERNEL_VEC, "f64" if name == "fp64" else "f32")],
                      "HBM_GB_per_s": bpl * N * N / spl / (ms * 1e-3) / 1e9,
                      "frac_of_hbm_peak": bpl * N * N / spl / (ms * 1e-3) / 1e9 / peak}

@@ -437,11 +437,11 @@ cudaError_t launch_k_pairs(const StepArgs<float>& a, const ConstsD& kd, cudaStre
   return cudaGetLastError();
 }
 
-template <int K, bool PER>
+template <int K, bool PER, int COLS = K <= 6 ? 256 : 192>
 cudaError_t launch_k_pairs_w(const StepArgs<float>& a, const ConstsD& kd, float* wout, long long wslot,
                              cudaStream_t st, int sm_count) {
   // the configuration of the forward kernel at each K
-  constexpr int COLS = K <= 6 ? 256 : 192, PF = K <= 4 ? 2 : 1;
+  constexpr int PF = K <= 4 ? 2 : 1;
   constexpr bool L0R = K == 6;
   const size_t smem = PairShape<K, COLS, PF, L0R>::floats() * sizeof(float);
   const void* fn = PER ? reinterpret_cast<const void*>(step2d_temporal_periodic_x2<K, COLS, PF, true, L0R>)
@@ -466,6 +466,10 @@ template <int K>
 cudaError_t launch_k_pairs_w(const StepArgs<float>& a, const ConstsD& kd, float* wout, long long wslot,
                              cudaStream_t st, int sm_count) {
   const bool per = a.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC && a.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
+  if constexpr (K == 6)
+    if (static_cast<long long>(a.nx) * a.ny < (1LL << 23))  // as the forward kernel
+      return per ? launch_k_pairs_w<K, true, 128>(a, kd, wout, wslot, st, sm_count)
+                 : launch_k_pairs_w<K, false, 128>(a, kd, wout, wslot, st, sm_count);
   return per ? launch_k_pairs_w<K, true>(a, kd, wout, wslot, st, sm_count)
              : launch_k_pairs_w<K, false>(a, kd, wout, wslot, st, sm_count);
 }
@@ -478,18 +482,24 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
   // and +y movers in registers (two CTAs per SM); at K = 8, 192 columns and one row of
   // prefetch.  Sides that are not periodic take the same shapes with their boundary rules.
   if constexpr (K % 2 == 0) {
+    // K = 6 below 2^23 cells: 128-column strips (four CTAs per SM), whose row segments are
+    // longer for the same number of CTAs, so less of the work is the wavefront's fill
+    // (measured +5 % at 1024^2, +3 % at 2048^2, -2 % at 4096^2)
+    const bool small = static_cast<long long>(a.nx) * a.ny < (1LL << 23);
     if (per) {
       if constexpr (K <= 4)
         return launch_k_pairs<K, 256, 2>(a, kd, st, sm_count);
       else if constexpr (K == 6)
-        return launch_k_pairs<K, 256, 1, true>(a, kd, st, sm_count);
+        return small ? launch_k_pairs<K, 128, 1, true>(a, kd, st, sm_count)
+                     : launch_k_pairs<K, 256, 1, true>(a, kd, st, sm_count);
       else
         return launch_k_pairs<K, 192, 1>(a, kd, st, sm_count);
     }
     if constexpr (K <= 4)
       return launch_k_pairs<K, 256, 2, false, false>(a, kd, st, sm_count);
     else if constexpr (K == 6)
-      return launch_k_pairs<K, 256, 1, true, false>(a, kd, st, sm_count);
+      return small ? launch_k_pairs<K, 128, 1, true, false>(a, kd, st, sm_count)
+                   : launch_k_pairs<K, 256, 1, true, false>(a, kd, st, sm_count);
     else
       return launch_k_pairs<K, 192, 1, false, false>(a, kd, st, sm_count);
   }
@@ -529,13 +539,15 @@ cudaError_t launch_step2d_temporal(const StepArgs<float>& a, const ConstsD& kd, 
 // ---------------------------------------------------------------- batched instances
 namespace {
 
-// Configuration of the paired batch kernel at K (0 columns: no paired kernel for odd K).
+// Configuration of the paired batch kernel at K (0 columns: no paired kernel for odd K): the
+// single-grid shapes, with the small grids' 128-column strips at K = 6 (the instances are
+// 64 to 1024 wide; measured 200k against 194k MLUPS with 256 columns).
 struct PairCfg {
   int cols, pf;
   bool l0r;
 };
 constexpr PairCfg pair_cfg(int k) {
-  return k % 2 ? PairCfg{0, 0, false} : (k <= 4 ? PairCfg{256, 2, false} : (k == 6 ? PairCfg{256, 1, true} : PairCfg{192, 1, false}));
+  return k % 2 ? PairCfg{0, 0, false} : (k <= 4 ? PairCfg{256, 2, false} : (k == 6 ? PairCfg{128, 1, true} : PairCfg{192, 1, false}));
 }
 
 template <int K>

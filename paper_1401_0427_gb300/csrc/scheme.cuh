@@ -102,28 +102,29 @@ __device__ __forceinline__ void equilibrium13(T h, T qx, T qy, const Consts<T>& 
   const T uu = add(mul(u, u), mul(v, v));
   const T kap = fmad(-uu, k.inv4g, mul(T(0.5), h));
   const T f0 = mul(k.a, kap);
-  const T r = mul(sub(h, f0), T(0.25));
+  const T hf = sub(h, f0);  // r = hf / 4
   const T p = mul(mul(k.half_g, h), h);
   const T ax = mul(qx, k.c);
   const T ay = mul(qy, k.c);
-  const T x4 = mul(qx, T(0.25));
-  const T y4 = mul(qy, T(0.25));
   const T pxx = mul(fmad(qx, u, p), k.c);
   const T pyy = mul(fmad(qy, v, p), k.c);
   const T pxy = mul(mul(mul(qx, qy), rh), k.c);
+  // r +- a and q/4 +- b as one fused multiply-add each: the quarter is exact, so each is the
+  // rounded sum of the exact quarter and the other term, as add(mul(., 1/4), +-b) would give
+  const T q4 = T(0.25);
   e[0] = f0;
-  e[1] = add(r, ax);
-  e[2] = add(r, ay);
-  e[3] = sub(r, ax);
-  e[4] = sub(r, ay);
-  e[5] = add(x4, pxx);
-  e[6] = add(x4, pxy);
-  e[7] = sub(x4, pxx);
-  e[8] = sub(x4, pxy);
-  e[9] = add(y4, pxy);
-  e[10] = add(y4, pyy);
-  e[11] = sub(y4, pxy);
-  e[12] = sub(y4, pyy);
+  e[1] = fmad(hf, q4, ax);
+  e[2] = fmad(hf, q4, ay);
+  e[3] = fmad(hf, q4, -ax);
+  e[4] = fmad(hf, q4, -ay);
+  e[5] = fmad(qx, q4, pxx);
+  e[6] = fmad(qx, q4, pxy);
+  e[7] = fmad(qx, q4, -pxx);
+  e[8] = fmad(qx, q4, -pxy);
+  e[9] = fmad(qy, q4, pxy);
+  e[10] = fmad(qy, q4, pyy);
+  e[11] = fmad(qy, q4, -pxy);
+  e[12] = fmad(qy, q4, -pyy);
 }
 
 // Moments -> equilibria -> BGK relaxation, in place; the moments (h, qx, qy) are
@@ -380,16 +381,16 @@ __device__ __forceinline__ void equilibrium5(T h, T q, const Consts<T>& k, T e[5
   const T u = mul(q, rh);
   const T kap = fmad(-mul(u, u), k.inv4g, mul(T(0.5), h));
   const T f0 = mul(k.a, kap);
-  const T half = mul(sub(h, f0), T(0.5));
+  const T hf = sub(h, f0);  // half = hf / 2
   const T aq = mul(q, k.c);
   const T p = mul(mul(k.half_g, h), h);
-  const T q2 = mul(q, T(0.5));
   const T pq = mul(fmad(q, u, p), k.c);
+  // exact halves folded into fused multiply-adds, as in equilibrium13
   e[0] = f0;
-  e[1] = add(half, aq);
-  e[2] = sub(half, aq);
-  e[3] = add(q2, pq);
-  e[4] = sub(q2, pq);
+  e[1] = fmad(hf, T(0.5), aq);
+  e[2] = fmad(hf, T(0.5), -aq);
+  e[3] = fmad(q, T(0.5), pq);
+  e[4] = fmad(q, T(0.5), -pq);
 }
 
 template <class T>

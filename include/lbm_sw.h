@@ -227,8 +227,8 @@ LBM_SW_API int lbm_sw_set_populations(lbm_sw* h, const void* src, int on_device,
  * the same scheme parameters and boundary kinds, advanced together: one kernel launch per
  * time step walks a list of tiles (rows x 32 vectors) covering every instance, either one CTA
  * per tile or a persistent grid of a few CTAs per SM striding through the list,
- * and long runs replay a CUDA graph of graph_chunk steps; FP32 batches with every side
- * periodic fuse temporal_steps steps per launch instead (temporal blocking).  Each instance evolves exactly as
+ * and long runs replay a CUDA graph of graph_chunk steps; FP32 batches fuse temporal_steps
+ * steps per launch instead (temporal blocking).  Each instance evolves exactly as
  * it would in its own lbm_sw handle (same device arithmetic, bit for bit).  Tile shape and
  * schedule come from lbm_sw_batch_autotune (or the params).  All instances share two device
  * buffers (double buffering); instance i stores its planes like a single handle does
@@ -247,9 +247,9 @@ typedef struct lbm_sw_batch_params {
   int tile_rows;          /* rows per CTA tile: 1, 2, 4 or 8; 0 = default (4) */
   int ctas_per_sm;        /* persistent CTAs per SM, 1 .. 32; 0 = one CTA per tile (default) */
   int graph_chunk;        /* steps per captured CUDA graph; 0 = default (50), < 0 = off */
-  int temporal_steps;     /* steps fused per launch (temporal blocking, FP32 with every side
-                             periodic): 2 .. 8; 1 = one step per launch; 0 = default (6 where
-                             allowed, else 1; lbm_sw_batch_autotune may change it) */
+  int temporal_steps;     /* steps fused per launch (temporal blocking, FP32; an even value
+                             unless every side is periodic): 2 .. 8; 1 = one step per launch;
+                             0 = default (6 in FP32, else 1; lbm_sw_batch_autotune may change it) */
   int reserved[4];        /* must be zero */
 } lbm_sw_batch_params;
 

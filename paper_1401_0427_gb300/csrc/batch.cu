@@ -103,7 +103,7 @@ struct lbm_sw_batch {
   int candidates = 0;
   double tuned_ms = 0.0;
   int graph_chunk = 50;
-  bool temporal_allowed = false;  // FP32 and every side periodic
+  bool temporal_allowed = false;  // FP32
   bool temporal_auto = false;     // temporal_steps left to the library (autotune may choose)
   int temporal_k = 0;             // steps per temporal launch; 0 = one step per launch
   lbm::BatchWaves waves[9];       // work lists by K (built on first use)
@@ -203,7 +203,8 @@ int ensure_waves(lbm_sw_batch* b, int k) {
 
 cudaError_t launch_temporal(const lbm_sw_batch* b, int from, int k, cudaStream_t st) {
   return lbm::launch_batch_temporal(b->waves[k], k, static_cast<const float*>(b->buf[from]),
-                                    static_cast<float*>(b->buf[1 - from]), bconsts(b), st);
+                                    static_cast<float*>(b->buf[1 - from]), bconsts(b), b->p.bc,
+                                    static_cast<const float*>(b->inflow_feq), st);
 }
 
 void drop_graphs(lbm_sw_batch* b) {
@@ -280,8 +281,8 @@ int validate_batch(const lbm_sw_batch_params* p, lbm_sw_batch* b) {
   if (p->temporal_steps >= 2) {
     bool per = true;
     for (int s = 0; s < 4; ++s) per = per && p->bc[s] == LBM_SW_BC_PERIODIC;
-    if (p->precision != LBM_SW_FP32 || !per)
-      return bfail(b, LBM_SW_E_ARG, "temporal_steps >= 2 needs FP32 and every side periodic");
+    if (p->precision != LBM_SW_FP32 || (!per && p->temporal_steps % 2))
+      return bfail(b, LBM_SW_E_ARG, "temporal_steps >= 2 needs FP32, and an even value unless every side is periodic");
   }
   for (int r = 0; r < 4; ++r)
     if (p->reserved[r] != 0) return bfail(b, LBM_SW_E_ARG, "reserved fields must be zero");
@@ -350,8 +351,7 @@ int lbm_sw_batch_create(const lbm_sw_batch_params* p, lbm_sw_batch** out) {
   b->tile_rows = p->tile_rows ? p->tile_rows : 4;
   b->ctas_per_sm = p->ctas_per_sm;  // 0: one CTA per tile
   b->graph_chunk = p->graph_chunk == 0 ? 50 : (p->graph_chunk < 0 ? 0 : p->graph_chunk + (p->graph_chunk & 1));
-  b->temporal_allowed = p->precision == LBM_SW_FP32;
-  for (int s = 0; s < 4; ++s) b->temporal_allowed = b->temporal_allowed && p->bc[s] == LBM_SW_BC_PERIODIC;
+  b->temporal_allowed = p->precision == LBM_SW_FP32;  // any sides (even K where not periodic)
   b->temporal_auto = p->temporal_steps == 0 && b->temporal_allowed;
   b->temporal_k = p->temporal_steps >= 2 ? p->temporal_steps : (b->temporal_auto ? 6 : 0);
   b->has_state.assign(p->count, 0);

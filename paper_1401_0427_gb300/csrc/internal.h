@@ -96,9 +96,10 @@ struct BatchWaves {
 cudaError_t batch_waves_build(int count, const int* nx, const int* ny, const long long* offset, const long long* pitch,
                               const long long* plane, int k, int sm_count, BatchWaves* out);
 void batch_waves_free(BatchWaves* w);
-// k fused steps of every instance: src -> dst (the batch's two buffers).
+// k fused steps of every instance: src -> dst (the batch's two buffers), under the batch's
+// sides bc (sides that are not periodic need an even k; inflow_feq: [4][13] device floats).
 cudaError_t launch_batch_temporal(const BatchWaves& w, int k, const float* src, float* dst, const ConstsD& kd,
-                                  cudaStream_t st);
+                                  const int bc[4], const float* inflow_feq, cudaStream_t st);
 
 // k fused steps per launch (temporal.cu; FP32, BGK; k in 2 .. 8): src -> dst.
 bool temporal_steps_supported(int k);

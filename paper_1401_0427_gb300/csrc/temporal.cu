@@ -365,6 +365,12 @@ __global__ void __launch_bounds__(COLS / 2, 2)
   });
 }
 
+// Sides of a batch (shared by its instances) and the inflow equilibria of its INFLOW sides.
+struct BatchSides {
+  int bc[4];
+  const float* inflow_feq;  // [4][13] (device)
+};
+
 // The same for instances of any width with the paired wavefront (two columns per thread).
 template <int K, int COLS, int PF, bool L0R>
 __global__ void __launch_bounds__(COLS / 2, 2)
@@ -383,6 +389,29 @@ __global__ void __launch_bounds__(COLS / 2, 2)
     A.plane = U.plane;
     for (int s = 0; s < 4; ++s) A.bc[s] = LBM_SW_BC_PERIODIC;
     pair_wave<K, COLS, PF, false, L0R, true, false, true, K <= 6>(A, Kc, smem, U.x0, U.w, U.ys, U.ye, nullptr, 0);
+    __syncthreads();  // the next unit reuses the rings
+  }
+}
+
+// The same with the boundary rules of sides that are not periodic (even K).
+template <int K, int COLS, int PF, bool L0R>
+__global__ void __launch_bounds__(COLS / 2, 2)
+    batch_temporal_pairs_bounded(const WaveUnit* __restrict__ units, const int* __restrict__ first,
+                                 const float* __restrict__ src, float* __restrict__ dst, const Consts<float> Kc,
+                                 const BatchSides sides) {
+  extern __shared__ __align__(16) float smem[];
+  for (int u = first[blockIdx.x]; u < first[blockIdx.x + 1]; ++u) {
+    const WaveUnit U = units[u];
+    StepArgs<float> A;
+    A.src = src + U.offset;
+    A.dst = dst + U.offset;
+    A.inflow_feq = sides.inflow_feq;
+    A.nx = U.nx;
+    A.ny = U.ny;
+    A.pitch = U.pitch;
+    A.plane = U.plane;
+    for (int s = 0; s < 4; ++s) A.bc[s] = sides.bc[s];
+    pair_wave<K, COLS, PF, false, L0R, false, false, true, false>(A, Kc, smem, U.x0, U.w, U.ys, U.ye, nullptr, 0);
     __syncthreads();  // the next unit reuses the rings
   }
 }
@@ -564,13 +593,15 @@ size_t batch_pair_smem() {
     return PairShape<K, c.cols, c.pf, c.l0r>::floats() * sizeof(float);
 }
 
-template <int K>
+template <int K, bool PER = true>
 const void* batch_pair_fn() {
   constexpr PairCfg c = pair_cfg(K);
   if constexpr (c.cols == 0)
     return nullptr;
-  else
+  else if constexpr (PER)
     return reinterpret_cast<const void*>(batch_temporal_pairs<K, c.cols, c.pf, c.l0r>);
+  else
+    return reinterpret_cast<const void*>(batch_temporal_pairs_bounded<K, c.cols, c.pf, c.l0r>);
 }
 
 // Shared-memory attributes of both kernels on this device; resident CTAs per SM of each
@@ -585,6 +616,10 @@ cudaError_t batch_prepare(int* resident, int* resident_pairs) {
   if (const void* pf = batch_pair_fn<K>()) {
     e = cudaFuncSetAttribute(pf, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(batch_pair_smem<K>()));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(batch_pair_fn<K, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(batch_pair_smem<K>()));
+    if (e != cudaSuccess) return e;
+    // (the bounded form has the same shape; its list is balanced over the same CTAs)
     *resident_pairs = cached_resident(pf, pair_cfg(K).cols / 2, batch_pair_smem<K>());
   }
   return cudaSuccess;
@@ -603,13 +638,19 @@ cudaError_t batch_prepare_k(int k, int* resident, int* resident_pairs) {
 }
 
 template <int K>
-void batch_launch(const BatchWaves& w, const float* src, float* dst, const Consts<float>& c, cudaStream_t st) {
+void batch_launch(const BatchWaves& w, const float* src, float* dst, const Consts<float>& c, const BatchSides& sides,
+                  bool per, cudaStream_t st) {
   if (w.count > 0) batch_temporal_periodic<K, 192><<<w.grid, 192, batch_smem<K>(), st>>>(w.units, w.first, src, dst, c);
   constexpr PairCfg pc = pair_cfg(K);
   if constexpr (pc.cols > 0)
-    if (w.pcount > 0)
-      batch_temporal_pairs<K, pc.cols, pc.pf, pc.l0r>
-          <<<w.pgrid, pc.cols / 2, batch_pair_smem<K>(), st>>>(w.punits, w.pfirst, src, dst, c);
+    if (w.pcount > 0) {
+      if (per)
+        batch_temporal_pairs<K, pc.cols, pc.pf, pc.l0r>
+            <<<w.pgrid, pc.cols / 2, batch_pair_smem<K>(), st>>>(w.punits, w.pfirst, src, dst, c);
+      else
+        batch_temporal_pairs_bounded<K, pc.cols, pc.pf, pc.l0r>
+            <<<w.pgrid, pc.cols / 2, batch_pair_smem<K>(), st>>>(w.punits, w.pfirst, src, dst, c, sides);
+    }
 }
 
 // Units of the given instances at strip width <= wmax (even widths when `even`), balanced
@@ -714,20 +755,28 @@ void batch_waves_free(BatchWaves* w) {
 }
 
 cudaError_t launch_batch_temporal(const BatchWaves& w, int k, const float* src, float* dst, const ConstsD& kd,
-                                  cudaStream_t st) {
+                                  const int bc[4], const float* inflow_feq, cudaStream_t st) {
   if (w.grid < 1) return cudaErrorInvalidValue;
+  bool per = true;
+  BatchSides sides;
+  for (int s = 0; s < 4; ++s) {
+    sides.bc[s] = bc[s];
+    per = per && bc[s] == LBM_SW_BC_PERIODIC;
+  }
+  sides.inflow_feq = inflow_feq;
+  if (!per && (k % 2 || w.count > 0)) return cudaErrorNotSupported;  // the bounded form is the paired one
   int resident = 1, resident_pairs = 0;
   cudaError_t e = batch_prepare_k(k, &resident, &resident_pairs);  // the shared-memory attributes, on this device
   if (e != cudaSuccess) return e;
   const Consts<float> c = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
   switch (k) {
-    case 2: batch_launch<2>(w, src, dst, c, st); break;
-    case 3: batch_launch<3>(w, src, dst, c, st); break;
-    case 5: batch_launch<5>(w, src, dst, c, st); break;
-    case 6: batch_launch<6>(w, src, dst, c, st); break;
-    case 7: batch_launch<7>(w, src, dst, c, st); break;
-    case 8: batch_launch<8>(w, src, dst, c, st); break;
-    default: batch_launch<4>(w, src, dst, c, st);
+    case 2: batch_launch<2>(w, src, dst, c, sides, per, st); break;
+    case 3: batch_launch<3>(w, src, dst, c, sides, per, st); break;
+    case 5: batch_launch<5>(w, src, dst, c, sides, per, st); break;
+    case 6: batch_launch<6>(w, src, dst, c, sides, per, st); break;
+    case 7: batch_launch<7>(w, src, dst, c, sides, per, st); break;
+    case 8: batch_launch<8>(w, src, dst, c, sides, per, st); break;
+    default: batch_launch<4>(w, src, dst, c, sides, per, st);
   }
   return cudaGetLastError();
 }

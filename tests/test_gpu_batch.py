@@ -165,10 +165,33 @@ def test_batch_temporal_on_the_benchmark_table_and_autotune():
         assert np.array_equal(a, b)
 
 
-def test_batch_temporal_needs_fp32_and_periodic_sides():
+def test_batch_temporal_needs_fp32_and_even_k_with_boundaries():
     with pytest.raises(lbm_sw.LbmSwError):
-        lbm_sw.Batch([(32, 32)], bc=(W, W, P, P), stream=torch_stream(), temporal_steps=4)
+        lbm_sw.Batch([(32, 32)], bc=(W, W, P, P), stream=torch_stream(), temporal_steps=5)
     with pytest.raises(lbm_sw.LbmSwError):
         lbm_sw.Batch([(32, 32)], precision=lbm_sw.FP64, stream=torch_stream(), temporal_steps=4)
     with lbm_sw.Batch([(32, 32)], bc=(W, W, P, P), stream=torch_stream()) as batch:
-        assert batch.tuning().temporal_steps == 1  # the default falls back to one step per launch
+        assert batch.tuning().temporal_steps == 6
+    with lbm_sw.Batch([(32, 32)], precision=lbm_sw.FP64, stream=torch_stream()) as batch:
+        assert batch.tuning().temporal_steps == 1  # FP64 keeps one step per launch
+
+
+@pytest.mark.parametrize("bc", [(W, W, W, W), (W, O, I, W), (I, W, P, P), (P, P, W, O)],
+                         ids=lambda b: "".join("PWOI"[k] for k in b))
+@pytest.mark.parametrize("k", [2, 4, 6, 8])
+def test_batch_temporal_with_boundaries(k, bc):
+    """Walls, inflow and outflow shared by the batch's instances: the two-column wavefront with
+    the side rules over the work list against one tile-list launch per step, bit for bit, on
+    odd and even sizes, instances narrower than a strip and wider than several."""
+    sizes = [(1, 1), (2, 3), (7, 5), (64, 64), (130, 9), (257, 33), (100, 200), (513, 3), (400, 37)]
+    states = _states(sizes, seed=1400 + k)
+    out = []
+    for temporal in (1, k):
+        with lbm_sw.Batch(sizes, bc=bc, inflow=INFLOW, stream=torch_stream(), temporal_steps=temporal) as batch:
+            for i, W0 in enumerate(states):
+                batch.set_state(i, *W0)
+            batch.step(2 * k + 3)
+            assert batch.tuning().temporal_steps == temporal
+            out.append([batch.populations(i) for i in range(len(sizes))])
+    for i in range(len(sizes)):
+        assert np.array_equal(out[0][i], out[1][i]), (k, sizes[i])

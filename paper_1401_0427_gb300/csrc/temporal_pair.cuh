@@ -21,8 +21,8 @@ __host__ __device__ constexpr int plane_index(int p) {
   return plane_group(p) == 0 ? (p - 4) / 4 : (plane_group(p) == 2 ? (p - 2) / 4 : (p == 0 ? 0 : (p + 1) / 2));
 }
 
-// The periodic wavefront with two columns per thread (tile columns 2c and 2c + 1) and the
-// collision on FP32 pairs (collide13x2: the same rounded operations, so the same bits).
+// The wavefront with two columns per thread (tile columns 2c and 2c + 1) and the collision
+// on FP32 pairs (collide13x2: the same rounded operations, so the same bits).
 // Rows of the shared-memory planes have COLS + 4 floats, tile column i at i + 2, so a
 // pair is 8-byte aligned and a read one column beyond either end of the tile stays inside
 // the row (the cells that read it lie outside the level's valid range and are never used).
@@ -71,8 +71,9 @@ __host__ __device__ constexpr int reg_index(int p) {
 // the domain, which holds the inflow equilibrium from the start (INFLOW).  y sides: when a
 // level computes the first row, or reaches the row past the last, the value the rule gives
 // is put in the register the next level pulls from (for level 0, in the input ring).  Tile
-// columns and rows outside the domain are neither loaded nor computed; nx is even, so a pair
-// never straddles the domain's edge.
+// columns and rows outside the domain are neither loaded nor computed, except the second lane
+// of the pair that holds the last column of an odd nx (loaded from the row's padding,
+// computed, never stored, never pulled).
 template <int K, int COLS, int PF, bool STORE_W, bool L0R, bool PER = true, bool MRT = false, bool ODD = true,
           bool U3 = false>
 __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts<float>& Kc, float* smem, int x0, int w,
@@ -97,10 +98,10 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
   const bool py = PER || A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
   const bool col_live = col < w + 2 * K && (px || (gx_raw >= 0 && gx_raw < nx));
   const int gx = px ? ((gx_raw % nx) + nx) % nx : gx_raw;
-  // An odd nx (periodic x only) puts the pairs of the halo that wraps around at odd columns
-  // and one pair across the periodic seam: those land by two 4-byte copies, and the output
-  // pair at the last column stores its first lane only.  ODD = false: nx is even (no such
-  // pairs, and no test for them).
+  // An odd nx puts, with periodic x sides, the pairs of the halo that wraps around at odd
+  // columns and one pair across the periodic seam: those land by two 4-byte copies; with
+  // either kind of x side the output pair at the last column stores its first lane only.
+  // ODD = false: nx is even (no such pairs, and no test for them).
   const int gx2 = px ? (gx + 1 == nx ? 0 : gx + 1) : gx + 1;
   const bool split = ODD && ((gx & 1) || gx2 != gx + 1);
   const bool lane_y_out = ODD && gx_raw + 1 >= nx;

@@ -61,10 +61,10 @@ def temporal_kernel_name(k: int, cells: int = 4096 * 4096) -> str:
 # kernel sources it was taken on.
 NCU_TRAFFIC = {
     "step2d_temporal_periodic_x2<6, 256, 1, 0, 1>": {
-        "src_sha256": "ca5dffde26c5b5887f47cc4811488004ecb3405a167332589e8d2e80c301d017",
-        "sources": ("temporal.cu", "temporal.cuh", "temporal_pair.cuh", "scheme.cuh"), "bytes_per_launch": 1745.82e6,
+        "src_sha256": "a3d415b8e7c714ffc2f345720c1bce4855e2fc1465d9c61283fdade6f3da6895",
+        "sources": ("temporal.cu", "temporal.cuh", "temporal_pair.cuh", "scheme.cuh"), "bytes_per_launch": 1745.80e6,
         "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of the 5 launches of "
-                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.78 MB read + 824.04 MB "
+                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.76 MB read + 824.04 MB "
                 "written per launch (mean)"},
 }
 

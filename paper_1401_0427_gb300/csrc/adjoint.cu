@@ -333,6 +333,7 @@ struct lbm_sw_tape {
   double* ckpt = nullptr;  // checkpoints * 13 * plane doubles
   void* wstore = nullptr;  // wslots * 3 * plane of T
   int wslots = 0;           // interval, plus room for the last fused replay launch to run past it
+  bool last_w = false;      // the moment slots hold the last segment's W (left by the forward record)
   void* phi[2] = {nullptr, nullptr};
   void* rep[2] = {nullptr, nullptr};
   double* grad_staging = nullptr;  // 3 * nx * ny doubles (host transfers)
@@ -377,6 +378,35 @@ lbm::StepArgs<T> replay_args(const lbm_sw* h, const lbm_sw_tape* t, int from) {
   return a;
 }
 
+// The last segment of a forward record (len steps from the handle's state) run by the
+// kernels of a replay, which also keep W^{k0} .. W^{k0 + len} in the moment slots, so the
+// backward pass starts without replaying it.  The same updates as lbm_sw_step, so the same
+// state; FP32 handles that fuse steps only (their slots have room for the last launch).
+template <class T>
+int record_last_segment(lbm_sw* h, lbm_sw_tape* t, int len) {
+  cudaStream_t st = h->stream;
+  const lbm::ConstsD kd = lbm::handle_consts(h);
+  const long long P = h->plane;
+  T* W = static_cast<T*>(t->wstore);
+  TAPE_CUDA(t, lbm::launch_moments2d_planes<T>(lbm::handle_args<T>(h, h->cur), W, st), "record moments");
+  int from = h->cur, j = 1;
+  long long launches = 1;
+  if constexpr (sizeof(T) == 4) {
+    const int k = replay_k(h);
+    for (; j + k - 1 <= len; j += k, from ^= 1, ++launches)
+      TAPE_CUDA(t, lbm::launch_step2d_temporal_store_w(lbm::handle_args<T>(h, from), kd, k, W + 3 * P * j, 3 * P, st,
+                                                       h->sm_count),
+                "record launch");
+  }
+  for (; j <= len; ++j, from ^= 1, ++launches)
+    TAPE_CUDA(t, lbm::launch_step2d_store_w<T>(lbm::handle_args<T>(h, from), kd, W + 3 * P * j, st), "record step");
+  h->cur = from;
+  h->steps_done += len;
+  h->launches += launches;
+  t->last_w = true;
+  return LBM_SW_OK;
+}
+
 template <class T>
 int run_adjoint(lbm_sw* h, lbm_sw_tape* t, const double* gh, const double* gu, const double* gv, double* dh,
                 double* du, double* dv) {
@@ -393,7 +423,11 @@ int run_adjoint(lbm_sw* h, lbm_sw_tape* t, const double* gh, const double* gu, c
   for (int seg = t->checkpoints - 1; seg >= 0; --seg) {
     const int k0 = seg * t->interval;
     const int k1 = (k0 + t->interval < t->steps) ? k0 + t->interval : t->steps;
-    // replay the segment from its checkpoint, keeping W^{k0} .. W^{k1-1}
+    // replay the segment from its checkpoint, keeping W^{k0} .. W^{k1-1} (the forward record
+    // left them for the last segment)
+    if (seg == t->checkpoints - 1 && t->last_w) {
+      t->last_w = false;
+    } else {
     TAPE_CUDA(t, (lbm::launch_convert<double, T>(t->ckpt + static_cast<size_t>(seg) * t->state_elems,
                                                  static_cast<T*>(t->rep[0]), static_cast<long long>(t->state_elems), st)),
               "checkpoint restore");
@@ -412,6 +446,7 @@ int run_adjoint(lbm_sw* h, lbm_sw_tape* t, const double* gh, const double* gu, c
     }
     for (; j < k1 - k0; ++j, from ^= 1)
       TAPE_CUDA(t, lbm::launch_step2d_store_w<T>(replay_args<T>(h, t, from), kd, W + 3 * P * j, st), "replay step");
+    }
     // adjoint steps n = k1 .. k0 + 1 (FP32 periodic: k reverse steps per launch while the
     // segment's stored moments cover them)
     for (int n = k1; n > k0; --n) {
@@ -547,8 +582,15 @@ int lbm_sw_forward_record(lbm_sw* h, lbm_sw_tape* t) {
                                                              static_cast<long long>(t->state_elems), h->stream);
     TAPE_CUDA(t, e, "checkpoint store");
     const int len = std::min(t->interval, t->steps - k0);
-    const int rc = lbm_sw_step(h, len);
-    if (rc != LBM_SW_OK) return tfail(t, rc, "forward_record: %s", h->err.c_str());
+    if (seg == t->checkpoints - 1 && h->p.precision == LBM_SW_FP32 && replay_k(h) > 1 &&
+        lbm::temporal_store_w_supported(lbm::handle_args<float>(h, 0), replay_k(h))) {
+      const int rc = record_last_segment<float>(h, t, len);
+      if (rc != LBM_SW_OK) return rc;
+    } else {
+      t->last_w = false;
+      const int rc = lbm_sw_step(h, len);
+      if (rc != LBM_SW_OK) return tfail(t, rc, "forward_record: %s", h->err.c_str());
+    }
   }
   t->recorded = true;
   return LBM_SW_OK;

@@ -141,12 +141,20 @@ __global__ void __launch_bounds__(256)
 // rows are warp-uniform, so only the first and last row and the warps holding
 // x = 0 or x = nx - 1 take a boundary branch.
 // --------------------------------------------------------------------------
+//
+// Launched with programmatic dependent launch: the next step's CTAs may be placed while this
+// step's last CTAs run.  Each CTA first waits for the previous grid to have completed and
+// its writes to be visible (griddepcontrol.wait: before any read of src or write of dst, so
+// neither the previous step's output nor its input is touched early), and signals when its
+// own rows are done (griddepcontrol.launch_dependents).  Launched without it, both are no-ops.
 template <class T, int BY, bool MRT>
 __global__ void __launch_bounds__(32 * BY) step2d_vec(const StepArgs<T> A, const Consts<T> K) {
   constexpr int V = V16<T>::n;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int x0 = (blockIdx.x * 32 + threadIdx.x) * V;
   for (int y = blockIdx.y * BY + threadIdx.y; y < A.ny; y += gridDim.y * BY)  // warp-uniform
     vec_row<T, false, MRT>(A, K, y, x0, threadIdx.x, nullptr);
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // The same step, also writing the moments (h, hu, hv) of the new state to three planes
@@ -284,10 +292,17 @@ cudaError_t launch_step2d(const StepArgs<T>& a, const ConstsD& kd, int variant, 
     const dim3 block(32, BY);
     const dim3 grid((a.nx + 32 * V - 1) / (32 * V),
                     static_cast<unsigned>(std::min<long long>((a.ny + BY - 1) / BY, 65535)));
-    if (kd.mrt)
-      step2d_vec<T, BY, true><<<grid, block, 0, st>>>(a, K);
-    else
-      step2d_vec<T, BY, false><<<grid, block, 0, st>>>(a, K);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return kd.mrt ? cudaLaunchKernelEx(&cfg, step2d_vec<T, BY, true>, a, K)
+                  : cudaLaunchKernelEx(&cfg, step2d_vec<T, BY, false>, a, K);
   }
   return cudaGetLastError();
 }

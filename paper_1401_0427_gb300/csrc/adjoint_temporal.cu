@@ -464,9 +464,11 @@ __global__ void __launch_bounds__(COLS / 2, 2)
     adjoint_temporal_periodic_x2(const StepArgs<float> A, const float* __restrict__ w0, long long wslot,
                                  const Consts<float> Kc, const Partition P) {
   extern __shared__ __align__(16) float smem[];
+  pdl_wait();
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
     adjoint_pair_wave<K, COLS, PF>(A, w0, wslot, Kc, smem, strip * P.w, P.w, ys, ye);
   });
+  pdl_done();
 }
 
 // The same with the transposed rules of sides that are not periodic (even nx).
@@ -475,9 +477,11 @@ __global__ void __launch_bounds__(COLS / 2, 2)
     adjoint_temporal_x2(const StepArgs<float> A, const float* __restrict__ w0, long long wslot,
                         const Consts<float> Kc, const Partition P) {
   extern __shared__ __align__(16) float smem[];
+  pdl_wait();
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
     adjoint_pair_wave<K, COLS, PF, false>(A, w0, wslot, Kc, smem, strip * P.w, P.w, ys, ye);
   });
+  pdl_done();
 }
 
 namespace {
@@ -511,11 +515,11 @@ cudaError_t launch_adjoint_pairs(const StepArgs<float>& a, const float* w0, long
   P.strips = (a.nx + P.w - 1) / P.w;
   const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
   const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
+  const dim3 grid(Q.strips * Q.segments), block(COLS / 2);
   if constexpr (PER)
-    adjoint_temporal_periodic_x2<K, COLS, PF><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, w0, wslot, K_, Q);
+    return launch_pdl(adjoint_temporal_periodic_x2<K, COLS, PF>, grid, block, smem, st, a, w0, wslot, K_, Q);
   else
-    adjoint_temporal_x2<K, COLS, PF><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, w0, wslot, K_, Q);
-  return cudaGetLastError();
+    return launch_pdl(adjoint_temporal_x2<K, COLS, PF>, grid, block, smem, st, a, w0, wslot, K_, Q);
 }
 
 // Even widths at K <= 4 (the library's adjoint launches): two columns per thread, 192-column

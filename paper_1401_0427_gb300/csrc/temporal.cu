@@ -337,9 +337,11 @@ __global__ void __launch_bounds__(COLS / 2, 2)
     step2d_temporal_x2(const StepArgs<float> A, const Consts<float> Kc, const Partition P,
                        float* __restrict__ wout = nullptr, long long wslot = 0) {
   extern __shared__ __align__(16) float smem[];
+  pdl_wait();
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
     pair_wave<K, COLS, PF, STORE_W, L0R, false, false, STORE_W>(A, Kc, smem, strip * P.w, P.w, ys, ye, wout, wslot);
   });
+  pdl_done();
 }
 
 // Every side periodic.  The plain kernel runs even widths; the one that also stores the
@@ -349,20 +351,24 @@ __global__ void __launch_bounds__(COLS / 2, 2)
     step2d_temporal_periodic_x2(const StepArgs<float> A, const Consts<float> Kc, const Partition P,
                                 float* __restrict__ wout = nullptr, long long wslot = 0) {
   extern __shared__ __align__(16) float smem[];
+  pdl_wait();
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
     pair_wave<K, COLS, PF, STORE_W, L0R, true, false, STORE_W, !STORE_W && K <= 6>(A, Kc, smem, strip * P.w, P.w, ys,
                                                                                    ye, wout, wslot);
   });
+  pdl_done();
 }
 
 template <int K, int COLS, int PF, bool L0R, bool PER>
 __global__ void __launch_bounds__(COLS / 2, 2)
     step2d_temporal_x2_odd(const StepArgs<float> A, const Consts<float> Kc, const Partition P) {
   extern __shared__ __align__(16) float smem[];
+  pdl_wait();
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
     pair_wave<K, COLS, PF, false, L0R, PER, false, true, PER && K <= 6>(A, Kc, smem, strip * P.w, P.w, ys, ye, nullptr,
                                                                          0);
   });
+  pdl_done();
 }
 
 // Sides of a batch (shared by its instances) and the inflow equilibria of its INFLOW sides.
@@ -377,6 +383,7 @@ __global__ void __launch_bounds__(COLS / 2, 2)
     batch_temporal_pairs(const WaveUnit* __restrict__ units, const int* __restrict__ first,
                          const float* __restrict__ src, float* __restrict__ dst, const Consts<float> Kc) {
   extern __shared__ __align__(16) float smem[];
+  pdl_wait();
   for (int u = first[blockIdx.x]; u < first[blockIdx.x + 1]; ++u) {
     const WaveUnit U = units[u];
     StepArgs<float> A;
@@ -391,6 +398,7 @@ __global__ void __launch_bounds__(COLS / 2, 2)
     pair_wave<K, COLS, PF, false, L0R, true, false, true, K <= 6>(A, Kc, smem, U.x0, U.w, U.ys, U.ye, nullptr, 0);
     __syncthreads();  // the next unit reuses the rings
   }
+  pdl_done();
 }
 
 // The same with the boundary rules of sides that are not periodic (even K).
@@ -400,6 +408,7 @@ __global__ void __launch_bounds__(COLS / 2, 2)
                                  const float* __restrict__ src, float* __restrict__ dst, const Consts<float> Kc,
                                  const BatchSides sides) {
   extern __shared__ __align__(16) float smem[];
+  pdl_wait();
   for (int u = first[blockIdx.x]; u < first[blockIdx.x + 1]; ++u) {
     const WaveUnit U = units[u];
     StepArgs<float> A;
@@ -414,6 +423,7 @@ __global__ void __launch_bounds__(COLS / 2, 2)
     pair_wave<K, COLS, PF, false, L0R, false, false, true, false>(A, Kc, smem, U.x0, U.w, U.ys, U.ye, nullptr, 0);
     __syncthreads();  // the next unit reuses the rings
   }
+  pdl_done();
 }
 
 // Launch one kernel of K steps.  Column counts: 192 for the periodic kernel (its shared
@@ -457,13 +467,13 @@ cudaError_t launch_k_pairs(const StepArgs<float>& a, const ConstsD& kd, cudaStre
   P.strips = (a.nx + P.w - 1) / P.w;
   const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
   const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
-  if (odd)
-    step2d_temporal_x2_odd<K, COLS, PF, L0R, PER><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q);
-  else if constexpr (PER)
-    step2d_temporal_periodic_x2<K, COLS, PF, false, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q);
+  const dim3 grid(Q.strips * Q.segments), block(COLS / 2);
+  float* const no_w = nullptr;
+  if (odd) return launch_pdl(step2d_temporal_x2_odd<K, COLS, PF, L0R, PER>, grid, block, smem, st, a, K_, Q);
+  if constexpr (PER)
+    return launch_pdl(step2d_temporal_periodic_x2<K, COLS, PF, false, L0R>, grid, block, smem, st, a, K_, Q, no_w, 0LL);
   else
-    step2d_temporal_x2<K, COLS, PF, false, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q);
-  return cudaGetLastError();
+    return launch_pdl(step2d_temporal_x2<K, COLS, PF, false, L0R>, grid, block, smem, st, a, K_, Q, no_w, 0LL);
 }
 
 template <int K, bool PER, int COLS = K <= 6 ? 256 : 192>
@@ -483,12 +493,11 @@ cudaError_t launch_k_pairs_w(const StepArgs<float>& a, const ConstsD& kd, float*
   P.strips = (a.nx + P.w - 1) / P.w;
   const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
   const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
+  const dim3 grid(Q.strips * Q.segments), block(COLS / 2);
   if constexpr (PER)
-    step2d_temporal_periodic_x2<K, COLS, PF, true, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q, wout,
-                                                                                                    wslot);
+    return launch_pdl(step2d_temporal_periodic_x2<K, COLS, PF, true, L0R>, grid, block, smem, st, a, K_, Q, wout, wslot);
   else
-    step2d_temporal_x2<K, COLS, PF, true, L0R><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q, wout, wslot);
-  return cudaGetLastError();
+    return launch_pdl(step2d_temporal_x2<K, COLS, PF, true, L0R>, grid, block, smem, st, a, K_, Q, wout, wslot);
 }
 
 template <int K>
@@ -638,19 +647,24 @@ cudaError_t batch_prepare_k(int k, int* resident, int* resident_pairs) {
 }
 
 template <int K>
-void batch_launch(const BatchWaves& w, const float* src, float* dst, const Consts<float>& c, const BatchSides& sides,
-                  bool per, cudaStream_t st) {
-  if (w.count > 0) batch_temporal_periodic<K, 192><<<w.grid, 192, batch_smem<K>(), st>>>(w.units, w.first, src, dst, c);
+cudaError_t batch_launch(const BatchWaves& w, const float* src, float* dst, const Consts<float>& c,
+                         const BatchSides& sides, bool per, cudaStream_t st) {
+  if (w.count > 0) {
+    batch_temporal_periodic<K, 192><<<w.grid, 192, batch_smem<K>(), st>>>(w.units, w.first, src, dst, c);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   constexpr PairCfg pc = pair_cfg(K);
   if constexpr (pc.cols > 0)
     if (w.pcount > 0) {
       if (per)
-        batch_temporal_pairs<K, pc.cols, pc.pf, pc.l0r>
-            <<<w.pgrid, pc.cols / 2, batch_pair_smem<K>(), st>>>(w.punits, w.pfirst, src, dst, c);
+        return launch_pdl(batch_temporal_pairs<K, pc.cols, pc.pf, pc.l0r>, dim3(w.pgrid), dim3(pc.cols / 2),
+                          batch_pair_smem<K>(), st, w.punits, w.pfirst, src, dst, c);
       else
-        batch_temporal_pairs_bounded<K, pc.cols, pc.pf, pc.l0r>
-            <<<w.pgrid, pc.cols / 2, batch_pair_smem<K>(), st>>>(w.punits, w.pfirst, src, dst, c, sides);
+        return launch_pdl(batch_temporal_pairs_bounded<K, pc.cols, pc.pf, pc.l0r>, dim3(w.pgrid), dim3(pc.cols / 2),
+                          batch_pair_smem<K>(), st, w.punits, w.pfirst, src, dst, c, sides);
     }
+  return cudaGetLastError();
 }
 
 // Units of the given instances at strip width <= wmax (even widths when `even`), balanced
@@ -770,15 +784,14 @@ cudaError_t launch_batch_temporal(const BatchWaves& w, int k, const float* src, 
   if (e != cudaSuccess) return e;
   const Consts<float> c = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
   switch (k) {
-    case 2: batch_launch<2>(w, src, dst, c, sides, per, st); break;
-    case 3: batch_launch<3>(w, src, dst, c, sides, per, st); break;
-    case 5: batch_launch<5>(w, src, dst, c, sides, per, st); break;
-    case 6: batch_launch<6>(w, src, dst, c, sides, per, st); break;
-    case 7: batch_launch<7>(w, src, dst, c, sides, per, st); break;
-    case 8: batch_launch<8>(w, src, dst, c, sides, per, st); break;
-    default: batch_launch<4>(w, src, dst, c, sides, per, st);
+    case 2: return batch_launch<2>(w, src, dst, c, sides, per, st);
+    case 3: return batch_launch<3>(w, src, dst, c, sides, per, st);
+    case 5: return batch_launch<5>(w, src, dst, c, sides, per, st);
+    case 6: return batch_launch<6>(w, src, dst, c, sides, per, st);
+    case 7: return batch_launch<7>(w, src, dst, c, sides, per, st);
+    case 8: return batch_launch<8>(w, src, dst, c, sides, per, st);
+    default: return batch_launch<4>(w, src, dst, c, sides, per, st);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace lbm

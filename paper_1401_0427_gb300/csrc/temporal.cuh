@@ -13,6 +13,30 @@
 namespace lbm {
 namespace {
 
+// Programmatic dependent launch: a kernel launched by launch_pdl may have its CTAs placed
+// while the previous grid in the stream still runs.  It calls pdl_wait() before it touches
+// memory (the previous grid has then completed and its writes are visible, so neither its
+// output nor its input is used early) and pdl_done() when its own work is done.  Without
+// the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_done() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // All-periodic domains.  Row R of level t - 1 feeds level t in three ways: its -y movers
 // (planes 4, 8, 12) to row R - 1, f0 and the x movers to row R, its +y movers (2, 6, 10)
 // to row R + 1.  Only the x movers cross columns, so for t - 1 >= 1 only they go through

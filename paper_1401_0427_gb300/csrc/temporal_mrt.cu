@@ -18,9 +18,11 @@ template <int K, int COLS, int PF, bool L0R, bool PER>
 __global__ void __launch_bounds__(COLS / 2, 2)
     step2d_temporal_x2_mrt(const StepArgs<float> A, const Consts<float> Kc, const Partition P) {
   extern __shared__ __align__(16) float smem[];
+  pdl_wait();
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
     pair_wave<K, COLS, PF, false, L0R, PER, true, true>(A, Kc, smem, strip * P.w, P.w, ys, ye, nullptr, 0);
   });
+  pdl_done();
 }
 
 template <int K, int COLS, int PF, bool L0R, bool PER>
@@ -35,8 +37,8 @@ cudaError_t launch_pairs_mrt(const StepArgs<float>& a, const ConstsD& kd, cudaSt
   P.strips = (a.nx + P.w - 1) / P.w;
   const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
   const Consts<float> K_ = make_consts_mrt<float>(kd.g, kd.lambda, kd.s, kd.a, kd.rates, 10);
-  step2d_temporal_x2_mrt<K, COLS, PF, L0R, PER><<<Q.strips * Q.segments, COLS / 2, smem, st>>>(a, K_, Q);
-  return cudaGetLastError();
+  return launch_pdl(step2d_temporal_x2_mrt<K, COLS, PF, L0R, PER>, dim3(Q.strips * Q.segments), dim3(COLS / 2), smem,
+                    st, a, K_, Q);
 }
 
 // The shapes of the BGK kernel at each K.

@@ -100,9 +100,10 @@ typedef struct lbm_sw lbm_sw;
 #define LBM_SW_PRE_COLLISION 1  /* collided on the device first (moments, equilibria, relaxation) */
 
 /* step kernel variants */
-#define LBM_SW_KERNEL_AUTO 0    /* library choice: TEMPORAL for 2D FP32 grids of >= 2^20 cells with
-                                   every side periodic or an even temporal_steps, else VEC in 2D;
-                                   CLUSTER in 1D */
+#define LBM_SW_KERNEL_AUTO 0    /* library choice: TEMPORAL for 2D FP32 grids of >= 3 * 2^17 cells
+                                   (628^2 and up) with every side periodic or an even
+                                   temporal_steps (with MRT relaxation: >= 2^20 cells), else VEC in
+                                   2D; CLUSTER in 1D */
 #define LBM_SW_KERNEL_SIMPLE 1  /* one launch per step, one thread per cell, scalar loads */
 #define LBM_SW_KERNEL_VEC 2     /* 2D: 16-byte vectors along x (4 FP32 or 2 FP64 cells per thread),
                                    x-neighbours exchanged with warp shuffles */
@@ -128,7 +129,8 @@ typedef struct lbm_sw_params {
   void* stream;        /* cudaStream_t borrowed from the caller (NULL = legacy default) */
   int kernel;          /* LBM_SW_KERNEL_*: AUTO, SIMPLE, VEC or TEMPORAL (2D), CLUSTER (1D) */
   int graph_chunk;     /* steps per captured CUDA graph in lbm_sw_step; 0 = default, < 0 = off */
-  int temporal_steps;  /* steps fused per launch by the TEMPORAL kernel: 2 .. 8; 0 = default (6) */
+  int temporal_steps;  /* steps fused per launch by the TEMPORAL kernel: 2 .. 8; 0 = default (4 below
+                          2^20 cells, else 6) */
   int reserved[5];     /* must be zero */
 } lbm_sw_params;
 

@@ -12,6 +12,11 @@
 
 namespace {
 
+// Smallest 2D FP32 grid (cells) that AUTO steps with temporal blocking: 640^2 ran 10 .. 37 %
+// faster fused (K = 4) than one step per launch, 512^2 with a wall and an inflow side 19 %
+// slower.
+constexpr long long kAutoTemporalCells = 3LL << 17;
+
 int fail(lbm_sw* h, int code, const char* fmt, ...) {
   if (h) {
     char buf[512];
@@ -49,8 +54,13 @@ lbm::ConstsD consts(const lbm_sw* h) { return lbm::handle_consts(h); }
 // Whether lbm_sw_step fuses temporal_k steps per launch: FP32 2D TEMPORAL handles without
 // obstacles, with the BGK collision or with MRT where the two-column kernel applies.
 bool temporal_active(const lbm_sw* h) {
-  return h->p.dim == 2 && h->kernel == LBM_SW_KERNEL_TEMPORAL && h->p.precision == LBM_SW_FP32 &&
-         !h->has_obstacles && (!h->mrt || lbm::temporal_mrt_supported(h->p.bc, h->p.nx, h->temporal_k));
+  if (h->p.dim != 2 || h->kernel != LBM_SW_KERNEL_TEMPORAL || h->p.precision != LBM_SW_FP32 || h->has_obstacles)
+    return false;
+  if (!h->mrt) return true;
+  // MRT: the two-column kernel's K; under AUTO from 2^20 cells (on smaller grids the MRT
+  // form was measured no faster than one step per launch with walls and inflow)
+  const bool large = static_cast<long long>(h->p.nx) * h->p.ny >= (1LL << 20);
+  return lbm::temporal_mrt_supported(h->p.bc, h->p.nx, h->temporal_k) && (large || !h->auto_kernel);
 }
 
 // One step from buffer `from` into the other buffer, on stream st (the TEMPORAL choice
@@ -212,18 +222,20 @@ int lbm_sw_create(const lbm_sw_params* p, lbm_sw** out) {
   h->pitch = round_up(p->nx, 32);
   h->plane = round_up(h->pitch * p->ny, 64);  // 256-byte aligned planes in FP32 and FP64
   const bool all_periodic = p->bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC && p->bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
+  // default steps per fused launch: 4 below 2^20 cells (shorter wavefront fill), else 6
+  const long long cells = static_cast<long long>(p->nx) * p->ny;
+  h->temporal_k = p->temporal_steps ? p->temporal_steps : (cells < (1LL << 20) ? 4 : 6);
+  h->auto_kernel = p->kernel == LBM_SW_KERNEL_AUTO;
   if (p->dim == 2) {
-    // AUTO: temporal blocking where it was measured faster (FP32, at least 2^20 cells, all
-    // sides periodic or the two-column kernel: even K), otherwise one vectorised step per
-    // launch
-    const int k = p->temporal_steps ? p->temporal_steps : 6;
-    const bool temporal = p->precision == LBM_SW_FP32 && (all_periodic || k % 2 == 0) &&
-                          static_cast<long long>(p->nx) * p->ny >= (1LL << 20);
+    // AUTO: temporal blocking where it was measured faster (FP32, at least 3 * 2^17 cells,
+    // all sides periodic or the two-column kernel: even K), otherwise one vectorised step
+    // per launch
+    const int k = h->temporal_k;
+    const bool temporal = p->precision == LBM_SW_FP32 && (all_periodic || k % 2 == 0) && cells >= kAutoTemporalCells;
     h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? (temporal ? LBM_SW_KERNEL_TEMPORAL : LBM_SW_KERNEL_VEC) : p->kernel;
   } else {
     h->kernel = p->kernel == LBM_SW_KERNEL_AUTO ? LBM_SW_KERNEL_CLUSTER : p->kernel;
   }
-  h->temporal_k = p->temporal_steps ? p->temporal_steps : 6;
   h->graph_chunk = p->graph_chunk == 0 ? 64 : (p->graph_chunk < 0 ? 0 : p->graph_chunk + (p->graph_chunk & 1));
 
   auto bail = [&](int code) {

@@ -169,6 +169,7 @@ struct lbm_sw {
   double* diag_host = nullptr;        // pinned host, 8 doubles
   int kernel = LBM_SW_KERNEL_VEC;
   int temporal_k = 4;
+  bool auto_kernel = false;  // the kernel was the library's choice (LBM_SW_KERNEL_AUTO)
   int sm_count = 152;
   bool mrt = false;          // set by lbm_sw_set_relaxation
   double mrt_rates[10] = {};

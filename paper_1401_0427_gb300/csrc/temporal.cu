@@ -520,10 +520,16 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
   // and +y movers in registers (two CTAs per SM); at K = 8, 192 columns and one row of
   // prefetch.  Sides that are not periodic take the same shapes with their boundary rules.
   if constexpr (K % 2 == 0) {
-    // K = 6 below 2^23 cells: 128-column strips (four CTAs per SM), whose row segments are
-    // longer for the same number of CTAs, so less of the work is the wavefront's fill
-    // (measured +5 % at 1024^2, +3 % at 2048^2, -2 % at 4096^2)
-    const bool small = static_cast<long long>(a.nx) * a.ny < (1LL << 23);
+    // 128-column strips (four CTAs per SM) on small grids, whose row segments are longer for
+    // the same number of CTAs, so less of the work is the wavefront's fill: K = 6 below 2^23
+    // cells (+5 % at 1024^2, +3 % at 2048^2, -2 % at 4096^2), K = 4 below 2^21 cells (+13 %
+    // at 1024^2, +6 % at 868^2, +7 % at 724^2, +2 .. 4 % at 640^2)
+    const long long cells = static_cast<long long>(a.nx) * a.ny;
+    const bool small = cells < (1LL << 23);
+    if constexpr (K == 4)
+      if (cells < (1LL << 21))
+        return per ? launch_k_pairs<K, 128, 2>(a, kd, st, sm_count)
+                   : launch_k_pairs<K, 128, 2, false, false>(a, kd, st, sm_count);
     if (per) {
       if constexpr (K <= 4)
         return launch_k_pairs<K, 256, 2>(a, kd, st, sm_count);

@@ -63,10 +63,25 @@ def test_temporal_equals_single_steps_on_the_benchmark_workload():
     (1023, 1040, (P, P, W, O), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
     (1024, 1024, (P, P, P, P), lbm_sw.FP64, lbm_sw.KERNEL_VEC),
     (512, 512, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_VEC),
+    (512, 512, (I, W, P, P), lbm_sw.FP32, lbm_sw.KERNEL_VEC),
+    (627, 627, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_VEC),
+    (628, 628, (P, P, P, P), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
+    (724, 724, (I, W, P, P), lbm_sw.FP32, lbm_sw.KERNEL_TEMPORAL),
+    (640, 640, (P, P, P, P), lbm_sw.FP64, lbm_sw.KERNEL_VEC),
 ])
 def test_auto_kernel_choice(nx, ny, bc, precision, want):
+    """Temporal blocking from 3 * 2^17 cells (628^2 and up) for FP32; FP64 steps one per launch."""
     with lbm_sw.Simulation(nx, ny, precision=precision, bc=bc, inflow=INFLOW, stream=torch_stream()) as sim:
         assert sim.info().kernel == want
+
+
+@pytest.mark.parametrize("nx,ny,want", [(628, 628, 4), (1023, 1024, 4), (1024, 1024, 6), (4096, 256, 6)])
+def test_default_steps_per_launch(nx, ny, want):
+    """The default fused steps per launch: 4 below 2^20 cells, 6 from there."""
+    with lbm_sw.Simulation(nx, ny, stream=torch_stream()) as sim:
+        assert sim.info().steps_per_launch == want
+    with lbm_sw.Simulation(nx, ny, kernel=lbm_sw.KERNEL_TEMPORAL, bc=(W, W, W, W), stream=torch_stream()) as sim:
+        assert sim.info().steps_per_launch == want
 
 
 def test_auto_temporal_counts_launches_and_steps():

@@ -157,6 +157,21 @@ def test_dam_break_4096_d4_symmetry_and_conservation():
     assert abs(d1[1]) <= 1e-6 * d0[0] and abs(d1[2]) <= 1e-6 * d0[0]
 
 
+@pytest.mark.parametrize("bc", [(lbm_sw.PERIODIC,) * 4, (lbm_sw.WALL,) * 4], ids=["periodic", "walls"])
+def test_dam_break_fp64_d4_symmetry(bc):
+    """FP64 (the folded BGK form): mirror-image cells see mirror-image operations, so the
+    circular dam-break keeps the symmetries of the square bit for bit."""
+    n = 256
+    W0 = inputs.circular_dam_break_2d(n, seed=None)
+    with lbm_sw.Simulation(n, n, precision=lbm_sw.FP64, a=0.05, bc=bc, stream=torch_stream()) as sim:
+        sim.set_state(*W0)
+        sim.step(300)
+        h, hu, hv = sim.moments()
+    assert np.array_equal(h, h[::-1, :]) and np.array_equal(h, h[:, ::-1]) and np.array_equal(h, h.T)
+    assert np.array_equal(hu, -hu[:, ::-1]) and np.array_equal(hu, hu[::-1, :]) and np.array_equal(hu, hv.T)
+    assert not np.array_equal(h, W0[0])
+
+
 def test_grid_past_32_bit_indices():
     """16384 x 12288 cells in FP32: each population buffer holds 2.6e9 elements, past 32-bit
     indexing.  The temporal kernel (6 steps per launch) equals 6 single steps bit for bit,

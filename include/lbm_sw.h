@@ -102,7 +102,7 @@ typedef struct lbm_sw lbm_sw;
 /* step kernel variants */
 #define LBM_SW_KERNEL_AUTO 0    /* library choice: TEMPORAL for 2D FP32 grids of >= 3 * 2^17 cells
                                    (628^2 and up) with every side periodic or an even
-                                   temporal_steps (with MRT relaxation: >= 2^20 cells), else VEC in
+                                   temporal_steps (with MRT relaxation: >= 2^19 cells), else VEC in
                                    2D; CLUSTER in 1D */
 #define LBM_SW_KERNEL_SIMPLE 1  /* one launch per step, one thread per cell, scalar loads */
 #define LBM_SW_KERNEL_VEC 2     /* 2D: 16-byte vectors along x (4 FP32 or 2 FP64 cells per thread),

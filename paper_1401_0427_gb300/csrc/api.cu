@@ -57,9 +57,9 @@ bool temporal_active(const lbm_sw* h) {
   if (h->p.dim != 2 || h->kernel != LBM_SW_KERNEL_TEMPORAL || h->p.precision != LBM_SW_FP32 || h->has_obstacles)
     return false;
   if (!h->mrt) return true;
-  // MRT: the two-column kernel's K; under AUTO from 2^20 cells (on smaller grids the MRT
-  // form was measured no faster than one step per launch with walls and inflow)
-  const bool large = static_cast<long long>(h->p.nx) * h->p.ny >= (1LL << 20);
+  // MRT: the two-column kernel's K; under AUTO from 2^19 cells (868^2 with walls and inflow:
+  // +14 % fused at K = 4; 724^2 even, 628^2 -12 %)
+  const bool large = static_cast<long long>(h->p.nx) * h->p.ny >= (1LL << 19);
   return lbm::temporal_mrt_supported(h->p.bc, h->p.nx, h->temporal_k) && (large || !h->auto_kernel);
 }
 

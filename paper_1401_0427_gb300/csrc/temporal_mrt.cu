@@ -45,9 +45,14 @@ cudaError_t launch_pairs_mrt(const StepArgs<float>& a, const ConstsD& kd, cudaSt
 template <int K>
 cudaError_t launch_mrt_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t st, int sm_count) {
   const bool per = a.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC && a.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
-  if constexpr (K <= 4)
+  if constexpr (K <= 4) {
+    // 128-column strips below 2^21 cells at K = 4, as the BGK kernel
+    if (K == 4 && static_cast<long long>(a.nx) * a.ny < (1LL << 21))
+      return per ? launch_pairs_mrt<K, 128, 2, false, true>(a, kd, st, sm_count)
+                 : launch_pairs_mrt<K, 128, 2, false, false>(a, kd, st, sm_count);
     return per ? launch_pairs_mrt<K, 256, 2, false, true>(a, kd, st, sm_count)
                : launch_pairs_mrt<K, 256, 2, false, false>(a, kd, st, sm_count);
+  }
   else if constexpr (K == 6) {
     // 128-column strips below 2^23 cells, as the BGK kernel (measured with MRT: +7 % at
     // 1024^2, +2 % at 2048^2, -3.5 % at 4096^2)

@@ -126,17 +126,17 @@ def test_mrt_temporal_choice():
             assert sim.info().steps_per_launch == want, (nx, bc)
 
 
-def test_mrt_small_grid_choice():
-    """Below 2^20 cells AUTO steps MRT one step per launch (the BGK collision keeps K = 4),
+@pytest.mark.parametrize("n,kernel,bgk,mrt", [(724, lbm_sw.KERNEL_AUTO, 4, 1), (724, lbm_sw.KERNEL_TEMPORAL, 4, 4),
+                                               (868, lbm_sw.KERNEL_AUTO, 4, 4)])
+def test_mrt_small_grid_choice(n, kernel, bgk, mrt):
+    """Below 2^19 cells AUTO steps MRT one step per launch (the BGK collision keeps K = 4),
     while an explicit TEMPORAL choice keeps its fused launches."""
-    for kernel, bgk, mrt in ((lbm_sw.KERNEL_AUTO, 4, 1), (lbm_sw.KERNEL_TEMPORAL, 4, 4)):
-        with lbm_sw.Simulation(724, 724, a=0.05, bc=(I, W, P, P), inflow=INFLOW, kernel=kernel,
-                               stream=torch_stream()) as sim:
-            assert sim.info().steps_per_launch == bgk
-            sim.set_relaxation(RATES_2D)
-            assert sim.info().steps_per_launch == mrt
-            sim.set_relaxation(None)
-            assert sim.info().steps_per_launch == bgk
+    with lbm_sw.Simulation(n, n, a=0.05, bc=(I, W, P, P), inflow=INFLOW, kernel=kernel, stream=torch_stream()) as sim:
+        assert sim.info().steps_per_launch == bgk
+        sim.set_relaxation(RATES_2D)
+        assert sim.info().steps_per_launch == mrt
+        sim.set_relaxation(None)
+        assert sim.info().steps_per_launch == bgk
 
 
 def test_mrt_temporal_matches_oracle():

@@ -47,78 +47,120 @@ __global__ void __launch_bounds__(256) step1d(const StepArgs<T> A, const Consts<
   }
 }
 
+// Steps per cluster barrier in step1d_cluster.
+constexpr int kCluster1dBlock = 8;
+
 // All n steps of a line of up to 16 * 1024 cells in one launch: one thread-block cluster,
-// CTA r holds cells [r * chunk, (r + 1) * chunk) in shared memory (two buffers of five
-// planes); the cells next to a CTA's ends are read from the neighbouring CTAs' shared
-// memory (distributed shared memory), and one cluster barrier per step separates the
-// reads of one buffer from the writes of the next step.
+// CTA r owns cells [r * chunk, (r + 1) * chunk) and keeps them in shared memory.  The steps
+// go in blocks of up to kCluster1dBlock (KB): at the start of a block a CTA copies its own
+// cells and KB cells on each side (from the neighbouring CTAs' shared memory, distributed
+// shared memory, wrapping around on periodic sides) into a local window, advances the window
+// KB steps on its own, and writes its own cells back.  After step s the window is exact
+// except for s cells at each end that is not a physical boundary, which never reaches the
+// owned cells.  One cluster barrier per block orders the write-back before the neighbours'
+// next reads; the owned copies alternate between two buffers, so a block's writes never
+// meet the same block's reads.  Every cell update is the pull + collide of the per-step
+// kernel on the same values, so the results are equal bit for bit.
 template <class T, bool MRT>
 __global__ void __launch_bounds__(1024) step1d_cluster(const StepArgs<T> A, const Consts<T> K, int nsteps,
                                                        int chunk) {
+  constexpr int KB = kCluster1dBlock;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = static_cast<int>(cluster.block_rank());
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* buf0 = reinterpret_cast<T*>(smem_raw);
-  T* buf1 = buf0 + 5 * chunk;
+  const int wcap = chunk + 2 * KB;  // window capacity
+  T* home = reinterpret_cast<T*>(smem_raw);
+  T* other = home + 5 * chunk;
+  T* const win0 = other + 5 * chunk;
+  T* const win1 = win0 + 5 * wcap;
   const int nx = A.nx;
   const int i0 = rank * chunk;
   const int ncell = nx - i0 < chunk ? nx - i0 : chunk;  // <= 0 for idle trailing CTAs
+  const bool per = A.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC;  // periodic sides come in pairs
   for (int c = threadIdx.x; c < ncell; c += blockDim.x)
 #pragma unroll
-    for (int p = 0; p < 5; ++p) buf0[p * chunk + c] = A.src[p * A.plane + i0 + c];
-  const int last_rank = (nx - 1) / chunk, last_c = (nx - 1) - last_rank * chunk;
+    for (int p = 0; p < 5; ++p) home[p * chunk + c] = A.src[p * A.plane + i0 + c];
   cluster.sync();
-  T* cur = buf0;
-  T* nxt = buf1;
-  for (int n = 0; n < nsteps; ++n) {
-    const T* left = rank > 0 ? cluster.map_shared_rank(cur, rank - 1) : nullptr;
-    const T* right = rank + 1 <= last_rank ? cluster.map_shared_rank(cur, rank + 1) : nullptr;
-    const T* first = cluster.map_shared_rank(cur, 0);
-    const T* last = cluster.map_shared_rank(cur, last_rank);
-    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-      const int i = i0 + c;
-      T f[5];
-      f[0] = cur[c];
-#pragma unroll
-      for (int p = 1; p < 5; ++p) {
-        const bool plus = (p == 1 || p == 3);
-        if (plus ? i > 0 : i < nx - 1) {  // interior pull
-          if (plus)
-            f[p] = c > 0 ? cur[p * chunk + c - 1] : left[p * chunk + chunk - 1];
-          else
-            f[p] = c < ncell - 1 ? cur[p * chunk + c + 1] : right[p * chunk];
-        } else {
-          const int side = plus ? LBM_SW_SIDE_XM : LBM_SW_SIDE_XP;
-          switch (A.bc[side]) {
-            case LBM_SW_BC_PERIODIC:
-              f[p] = plus ? last[p * chunk + last_c] : first[p * chunk];
-              break;
-            case LBM_SW_BC_WALL: {
-              const int m = (p == 1) ? 2 : (p == 2) ? 1 : (p == 3) ? 4 : 3;
-              const T v = cur[m * chunk + c];
-              f[p] = p >= 3 ? -v : v;
-              break;
-            }
-            case LBM_SW_BC_OUTFLOW:
-              f[p] = cur[p * chunk + c];
-              break;
-            default:
-              f[p] = A.inflow_feq[side * 5 + p];
-          }
+  for (int done = 0; done < nsteps; done += KB) {
+    const int kb = nsteps - done < KB ? nsteps - done : KB;
+    if (ncell > 0) {
+      // the window holds cells [i0 - L, i0 + ncell + R)
+      const int L = per ? kb : min(kb, i0);
+      const int R = per ? kb : min(kb, nx - i0 - ncell);
+      const int wn = L + ncell + R;
+      const bool left_end = !per && i0 - L == 0;  // the window starts at the x- side
+      const bool right_end = !per && i0 + ncell + R == nx;
+      for (int w = threadIdx.x; w < wn; w += blockDim.x) {
+        int g = i0 - L + w;
+        if (per) {
+          g %= nx;
+          if (g < 0) g += nx;
         }
-      }
-      collide5_any<T, MRT>(f, K);
+        const int r = g / chunk;
+        const int c = g - r * chunk;
+        const T* src = r == rank ? home : cluster.map_shared_rank(home, r);
 #pragma unroll
-      for (int p = 0; p < 5; ++p) nxt[p * chunk + c] = f[p];
+        for (int p = 0; p < 5; ++p) win0[p * wcap + w] = src[p * chunk + c];
+      }
+      __syncthreads();
+      T* cur = win0;
+      T* nxt = win1;
+      for (int s = 1; s <= kb; ++s) {
+        const int lo = left_end ? 0 : s;
+        const int hi = right_end ? wn : wn - s;
+        for (int w = lo + threadIdx.x; w < hi; w += blockDim.x) {
+          const int g = i0 - L + w;  // the cell (sides that are not periodic)
+          T f[5];
+          f[0] = cur[w];
+#pragma unroll
+          for (int p = 1; p < 5; ++p) {
+            const bool plus = (p == 1 || p == 3);  // moves +lambda: comes from w - 1
+            if (per || (plus ? g > 0 : g < nx - 1)) {
+              f[p] = cur[p * wcap + (plus ? w - 1 : w + 1)];
+            } else {
+              const int side = plus ? LBM_SW_SIDE_XM : LBM_SW_SIDE_XP;
+              switch (A.bc[side]) {
+                case LBM_SW_BC_WALL: {  // mirror of the boundary cell: f+ <-> f-, g+ <-> -g-
+                  const int m = (p == 1) ? 2 : (p == 2) ? 1 : (p == 3) ? 4 : 3;
+                  const T v = cur[m * wcap + w];
+                  f[p] = p >= 3 ? -v : v;
+                  break;
+                }
+                case LBM_SW_BC_OUTFLOW:
+                  f[p] = cur[p * wcap + w];
+                  break;
+                default:
+                  f[p] = A.inflow_feq[side * 5 + p];
+              }
+            }
+          }
+          collide5_any<T, MRT>(f, K);
+#pragma unroll
+          for (int p = 0; p < 5; ++p) nxt[p * wcap + w] = f[p];
+        }
+        __syncthreads();
+        T* t = cur;
+        cur = nxt;
+        nxt = t;
+      }
+      for (int c = threadIdx.x; c < ncell; c += blockDim.x)
+#pragma unroll
+        for (int p = 0; p < 5; ++p) other[p * chunk + c] = cur[p * wcap + L + c];
     }
     cluster.sync();
-    T* t = cur;
-    cur = nxt;
-    nxt = t;
+    T* t = home;
+    home = other;
+    other = t;
   }
   for (int c = threadIdx.x; c < ncell; c += blockDim.x)
 #pragma unroll
-    for (int p = 0; p < 5; ++p) A.dst[p * A.plane + i0 + c] = cur[p * chunk + c];
+    for (int p = 0; p < 5; ++p) A.dst[p * A.plane + i0 + c] = home[p * chunk + c];
+}
+
+// Dynamic shared memory of step1d_cluster at `chunk` cells per CTA.
+template <class T>
+size_t cluster1d_smem(int chunk) {
+  return (2 * 5 * static_cast<size_t>(chunk) + 2 * 5 * static_cast<size_t>(chunk + 2 * kCluster1dBlock)) * sizeof(T);
 }
 
 template <class T>
@@ -202,11 +244,11 @@ int cluster1d_max_cells() {
     max_blocks = 8;
     if (cudaFuncSetAttribute(step1d_cluster<T, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
         cudaFuncSetAttribute(step1d_cluster<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(2 * 5 * 1024 * sizeof(T))) == cudaSuccess) {
+                             static_cast<int>(cluster1d_smem<T>(1024))) == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(16);
       cfg.blockDim = dim3(1024);
-      cfg.dynamicSmemBytes = 2 * 5 * 1024 * sizeof(T);
+      cfg.dynamicSmemBytes = cluster1d_smem<T>(1024);
       cudaLaunchAttribute attr;
       attr.id = cudaLaunchAttributeClusterDimension;
       attr.val.clusterDim.x = 16;
@@ -231,10 +273,11 @@ cudaError_t launch_cluster_t(const StepArgs<T>& a, const ConstsD& kd, int nsteps
   if (blocks > max_blocks) blocks = max_blocks;
   if (blocks < 1) blocks = 1;
   const int chunk = (a.nx + blocks - 1) / blocks;
-  const int threads = ((chunk + 31) / 32) * 32;
-  const size_t smem = 2 * 5 * static_cast<size_t>(chunk) * sizeof(T);
+  const int window = chunk + 2 * kCluster1dBlock;
+  const int threads = window < 1024 ? ((window + 31) / 32) * 32 : 1024;
+  const size_t smem = cluster1d_smem<T>(chunk);
   cudaError_t e = cudaFuncSetAttribute(step1d_cluster<T, MRT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(2 * 5 * 1024 * sizeof(T)));
+                                       static_cast<int>(cluster1d_smem<T>(1024)));
   if (e != cudaSuccess) return e;
   if (blocks > 8) {
     e = cudaFuncSetAttribute(step1d_cluster<T, MRT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

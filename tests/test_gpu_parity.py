@@ -69,15 +69,16 @@ def test_1d_matches_oracle(n, bc, precision):
 
 @pytest.mark.parametrize("precision", [lbm_sw.FP64, lbm_sw.FP32])
 @pytest.mark.parametrize("bc", [(P, P), (W, W), (O, I), (I, W)], ids=str)
-@pytest.mark.parametrize("n", [1, 5, 64, 65, 1000, 4097, 16384, 16385])
-def test_1d_cluster_kernel_equals_per_step_kernel(n, bc, precision):
-    """All steps in one cluster launch (the line in shared memory) against one launch per
-    step: the same arithmetic, so the same bits; lines longer than the cluster holds fall
-    back to the per-step kernel."""
+@pytest.mark.parametrize("n", [1, 2, 5, 17, 64, 65, 130, 1000, 4097, 16384, 16385])
+@pytest.mark.parametrize("steps", [1, 8, 23])
+def test_1d_cluster_kernel_equals_per_step_kernel(n, bc, precision, steps):
+    """All steps in one cluster launch (the line in shared memory, blocks of 8 steps per
+    cluster barrier) against one launch per step: the same arithmetic, so the same bits;
+    lines longer than the cluster holds fall back to the per-step kernel."""
     inflow = [(1.3, 0.2, 0.0), (0.9, -0.15, 0.0), None, None]
     F0 = inputs.random_populations(5, 1, n, seed=3500 + n)
-    a = gpu_post(F0, 23, dim=1, precision=precision, bc=bc, inflow=inflow, a=0.15, kernel=lbm_sw.KERNEL_SIMPLE)
-    b = gpu_post(F0, 23, dim=1, precision=precision, bc=bc, inflow=inflow, a=0.15, kernel=lbm_sw.KERNEL_CLUSTER)
+    a = gpu_post(F0, steps, dim=1, precision=precision, bc=bc, inflow=inflow, a=0.15, kernel=lbm_sw.KERNEL_SIMPLE)
+    b = gpu_post(F0, steps, dim=1, precision=precision, bc=bc, inflow=inflow, a=0.15, kernel=lbm_sw.KERNEL_CLUSTER)
     assert np.array_equal(a, b)
 
 

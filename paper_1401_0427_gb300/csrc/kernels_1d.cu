@@ -236,32 +236,36 @@ cudaError_t launch_step1d(const StepArgs<T>& a, const ConstsD& kd, cudaStream_t 
   return cudaGetLastError();
 }
 
+// CTAs of the largest cluster the device places for step1d_cluster: 16 where it allows
+// that non-portable size with the shared memory of 1024-cell chunks, else the portable 8.
+template <class T>
+int cluster1d_probe_blocks() {
+  int blocks = 8;
+  if (cudaFuncSetAttribute(step1d_cluster<T, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+      cudaFuncSetAttribute(step1d_cluster<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(cluster1d_smem<T>(1024))) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = cluster1d_smem<T>(1024);
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 16;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, step1d_cluster<T, false>, &cfg) == cudaSuccess && clusters > 0)
+      blocks = 16;
+  }
+  cudaGetLastError();  // a refused attribute or probe leaves no error behind
+  return blocks;
+}
+
 template <class T>
 int cluster1d_max_cells() {
-  static int max_blocks = 0;
-  if (max_blocks == 0) {
-    // a 16-CTA cluster where the device allows it, else the portable 8
-    max_blocks = 8;
-    if (cudaFuncSetAttribute(step1d_cluster<T, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-        cudaFuncSetAttribute(step1d_cluster<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(cluster1d_smem<T>(1024))) == cudaSuccess) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(16);
-      cfg.blockDim = dim3(1024);
-      cfg.dynamicSmemBytes = cluster1d_smem<T>(1024);
-      cudaLaunchAttribute attr;
-      attr.id = cudaLaunchAttributeClusterDimension;
-      attr.val.clusterDim.x = 16;
-      attr.val.clusterDim.y = 1;
-      attr.val.clusterDim.z = 1;
-      cfg.attrs = &attr;
-      cfg.numAttrs = 1;
-      int clusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&clusters, step1d_cluster<T, false>, &cfg) == cudaSuccess && clusters > 0)
-        max_blocks = 16;
-    }
-    cudaGetLastError();
-  }
+  static const int max_blocks = cluster1d_probe_blocks<T>();  // probed once (thread-safe initialisation)
   return max_blocks * 1024;
 }
 

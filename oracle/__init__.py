@@ -99,10 +99,12 @@ def build(force: bool = False) -> str:
 
 
 def lib() -> ctypes.CDLL:
+    """The compiled oracle; ``LBM_ORACLE_LIB`` names another build of this source to load
+    instead (the planted-mistake tests point the pins at mutated copies this way)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
+            path = os.environ.get("LBM_ORACLE_LIB") or build()
             _lib = ctypes.CDLL(path)
             dp = ctypes.POINTER(ctypes.c_double)
             pp = ctypes.POINTER(OracleParams)

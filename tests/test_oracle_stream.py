@@ -117,6 +117,33 @@ def test_inflow_injects_equilibrium(side):
     assert np.array_equal(out, want)
 
 
+@pytest.mark.parametrize("side", range(2))
+def test_inflow_injects_equilibrium_1d(side):
+    """1D: with s = 0 the populations entering through an INFLOW side (f+ and g+ at x-,
+    f- and g- at x+) are the equilibrium of the prescribed state W_in = (h, q), whose
+    closed form (section 2) is written out here: f+- = (h - a kappa)/2 +- q/(2 lam),
+    g+- = q/2 +- (q u + g h^2/2)/(2 lam), kappa = h/2 - u^2/(4g)."""
+    n, lam, a, g = 5, 8.0, 0.15, 1.0
+    bc = [OUTFLOW, OUTFLOW]
+    bc[side] = INFLOW
+    h, q = 1.7, 0.3
+    inflow = [None] * 4
+    inflow[side] = (h, q, 0.0)
+    B = oracle.equilibrium_1d(np.ones(n), np.zeros(n), oracle.params(n, a=a))  # a lake of depth 1
+    out = oracle.run_1d(B, 1, oracle.params(n, a=a, s=0.0, bc=bc, inflow=inflow))
+    u = q / h
+    kap = h / 2 - u * u / (4 * g)
+    feq = [a * kap, (h - a * kap) / 2 + q / (2 * lam), (h - a * kap) / 2 - q / (2 * lam),
+           q / 2 + (q * u + g * h * h / 2) / (2 * lam), q / 2 - (q * u + g * h * h / 2) / (2 * lam)]
+    cell, incoming = (0, (1, 3)) if side == 0 else (n - 1, (2, 4))
+    for pop in incoming:
+        assert out[pop, cell] == pytest.approx(feq[pop], rel=1e-14, abs=1e-15)
+    want = B.copy()
+    for pop in incoming:
+        want[pop, cell] = out[pop, cell]
+    assert np.array_equal(out, want)  # every other population streamed onto the lake's own values
+
+
 def test_pure_streaming_periodic_returns_after_n_steps():
     nx, ny = 7, 5
     F = inputs.random_populations(13, ny, nx, seed=41)

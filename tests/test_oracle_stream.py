@@ -176,6 +176,25 @@ def test_pure_streaming_1d_walls_and_periodic():
     assert np.array_equal(out, want)
 
 
+@pytest.mark.parametrize("side", range(2))
+def test_outflow_copies_boundary_cell_1d(side):
+    """1D, s = 0: a population entering through an OUTFLOW side is the boundary cell's own
+    value of it (the ghost is a copy of that cell), here a spike of 0.25 on f+ or g+ at x-
+    and on f- or g- at x+, which also moves on inside."""
+    n = 6
+    B = np.zeros((5, n))
+    B[1:3] = 0.5  # depth-1 background so that the (identity) collision is defined
+    cell, step, incoming = (0, 1, (1, 3)) if side == 0 else (n - 1, -1, (2, 4))
+    for pop in incoming:
+        G = np.zeros((5, n))
+        G[pop, cell] = 0.25
+        out = oracle.run_1d(B + G, 1, oracle.params(n, s=0.0, bc=(OUTFLOW, OUTFLOW))) - B
+        want = np.zeros((5, n))
+        want[pop, cell] = 0.25  # the ghost copy comes back in
+        want[pop, cell + step] = 0.25  # and the spike moves on
+        assert np.array_equal(out, want), (side, pop)
+
+
 @pytest.mark.parametrize("h0", [1.0, 2.0, 0.5])
 @pytest.mark.parametrize("bcs", [(PERIODIC,) * 4, (WALL,) * 4, (OUTFLOW,) * 4, (WALL, OUTFLOW, PERIODIC, PERIODIC)])
 def test_lake_at_rest_stays_exactly_at_rest(h0, bcs):

@@ -36,6 +36,13 @@ MUTANTS = [
      "m[2] = lam * (f[1] + f[2] - 2.0 * f[0]);"),
     ("1d_inflow_discharge_sign", "equilibrium_1d<T>(pr.inflow[side][0], pr.inflow[side][1], pr, win)",
      "equilibrium_1d<T>(pr.inflow[side][0], -pr.inflow[side][1], pr, win)"),
+    ("1d_periodic_copies_own_edge", "case BC_PERIODIC: g(j, ghost) = g(j, opposite); break;",
+     "case BC_PERIODIC: g(j, ghost) = g(j, edge); break;"),
+    ("1d_outflow_copies_far_side", "case BC_OUTFLOW: g(j, ghost) = g(j, edge); break;",
+     "case BC_OUTFLOW: g(j, ghost) = g(j, opposite); break;"),
+    ("1d_mrt_inverse_f0_sign", "f[0] = m[0] - sum_pm;", "f[0] = m[0] + sum_pm;"),
+    ("1d_mrt_skips_j_q_not_q", "if (l != 0 && l != 3) m[l] = m[l] + pr.s_moments[l] * (meq[l] - m[l]);",
+     "if (l != 0 && l != 4) m[l] = m[l] + pr.s_moments[l] * (meq[l] - m[l]);"),
     # section 3, D2Q5Q4Q4
     ("2d_theta_half_dropped", "const T theta = pr.g * rho - uu / 2.0;", "const T theta = pr.g * rho - uu;"),
     ("2d_rest_potential_without_K", "const T h0_t = pr.a * K * theta;", "const T h0_t = pr.a * theta;"),
@@ -60,6 +67,14 @@ MUTANTS = [
     ("2d_inflow_velocity_transposed",
      "equilibrium_2d<T>(pr.inflow[side][0], pr.inflow[side][1], pr.inflow[side][2], pr, win);",
      "equilibrium_2d<T>(pr.inflow[side][0], pr.inflow[side][2], pr.inflow[side][1], pr, win);"),
+    ("2d_pressure_linear_in_w", "const T p = K * w * w;", "const T p = K * w;"),
+    ("2d_mrt_relaxes_qy", "if (l != 0 && l != 5 && l != 9) m[l] = m[l] + pr.s_moments[l] * (meq[l] - m[l]);",
+     "if (l != 0 && l != 5 && l != 10) m[l] = m[l] + pr.s_moments[l] * (meq[l] - m[l]);"),
+    ("2d_mrt_xx_rho_basis", "m[4] = f[1] - f[2] + f[3] - f[4];", "m[4] = f[1] + f[2] - f[3] - f[4];"),
+    ("2d_x_wall_gy_not_mirrored", "const int kMirrorX[13] = {0, 3, 2, 1, 4, 7, 6, 5, 8, 11, 10, 9, 12};",
+     "const int kMirrorX[13] = {0, 3, 2, 1, 4, 7, 6, 5, 8, 9, 10, 11, 12};"),
+    ("2d_solid_cells_collide", "if (pr.solid && pr.solid[c]) continue;  // no fluid to relax",
+     "if (false) continue;  // no fluid to relax"),
     ("2d_obstacle_face_without_sign",
      "f[p * plane + c] = kEx2[p] != 0 ? kSignX[p] * g(kMirrorX[p], i, j) : kSignY[p] * g(kMirrorY[p], i, j);",
      "f[p * plane + c] = kEx2[p] != 0 ? g(kMirrorX[p], i, j) : g(kMirrorY[p], i, j);"),

@@ -178,3 +178,21 @@ def test_batch_rejects_a_zero_width_instance(lib):
     with pytest.raises(lbm_sw.LbmSwError) as ei:
         lbm_sw.lbm_sw_batch_create(p)
     assert "instance 1" in str(ei.value)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the compiled CUDA library the binding raises: there is no CPU fallback."""
+    monkeypatch.setattr(lbm_sw, "_lib", None)
+    with pytest.raises(ImportError, match="no CPU fallback"):
+        lbm_sw.load(str(tmp_path / "liblbm_sw.so"))
+
+
+def test_no_gpu_means_an_error_not_a_fallback(lib):
+    """On a machine without a GPU, creating a handle fails with the CUDA status instead of
+    computing anywhere else."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lbm_sw.LbmSwError) as err:
+        lbm_sw.Simulation(16, 16)
+    assert err.value.status == lbm_sw.E_CUDA

@@ -405,15 +405,27 @@ def make_params(nx: int, ny: int = 1, *, dim: int | None = None, precision: int 
     return p
 
 
-def _ptr(x, on_device: bool):
-    """Address of a contiguous numpy array or torch tensor (and whether it is on the GPU)."""
+def _ptr(x, on_device: bool, dtype: str | None = None, count: int | None = None, what: str = "buffer"):
+    """Address of a contiguous numpy array or torch tensor (and whether it is on the GPU).
+
+    With ``dtype`` ("float64", "float32", "uint8") and ``count`` the buffer is checked first:
+    the C library reads or writes exactly ``count`` elements of that type through the pointer,
+    so a buffer of another type or size is refused here, before any copy."""
     if x is None:
         return None
     if hasattr(x, "data_ptr"):
-        assert x.is_contiguous()
-        return x.data_ptr()
-    assert isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]
-    return x.ctypes.data
+        if not x.is_contiguous():
+            raise ValueError(f"{what}: tensor must be contiguous")
+        name, n = str(x.dtype).replace("torch.", ""), x.numel()
+    else:
+        if not (isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]):
+            raise ValueError(f"{what}: expected a C-contiguous numpy array or a torch tensor")
+        name, n = x.dtype.name, x.size
+    if dtype is not None and name != dtype:
+        raise ValueError(f"{what}: dtype {name}, expected {dtype}")
+    if count is not None and n != count:
+        raise ValueError(f"{what}: {n} elements, expected {count}")
+    return x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
 
 
 class Simulation:
@@ -454,7 +466,9 @@ class Simulation:
         if not dev:
             h, hu = (np.ascontiguousarray(x, dtype=np.float64) for x in (h, hu))
             hv = None if hv is None else np.ascontiguousarray(hv, dtype=np.float64)
-        lbm_sw_set_state(self.handle, _ptr(h, dev), _ptr(hu, dev), _ptr(hv, dev), dev)
+        n = self.nx * self.ny
+        lbm_sw_set_state(self.handle, _ptr(h, dev, "float64", n, "h"), _ptr(hu, dev, "float64", n, "hu"),
+                         _ptr(hv, dev, "float64", n, "hv"), dev)
 
     def step(self, n: int = 1):
         lbm_sw_step(self.handle, n)
@@ -473,7 +487,7 @@ class Simulation:
             solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
         if tuple(solid.shape) != (self.ny, self.nx):
             raise ValueError(f"solid must have shape ({self.ny}, {self.nx})")
-        lbm_sw_set_obstacle(self.handle, _ptr(solid, dev), dev)
+        lbm_sw_set_obstacle(self.handle, _ptr(solid, dev, "uint8", self.nx * self.ny, "solid"), dev)
 
     def moments(self):
         h = np.empty((self.ny, self.nx))
@@ -484,7 +498,9 @@ class Simulation:
 
     def moments_into(self, h, hu, hv=None):
         dev = self._on_device(h)
-        lbm_sw_get_moments(self.handle, _ptr(h, dev), _ptr(hu, dev), _ptr(hv, dev), dev)
+        n = self.nx * self.ny
+        lbm_sw_get_moments(self.handle, _ptr(h, dev, "float64", n, "h"), _ptr(hu, dev, "float64", n, "hu"),
+                           _ptr(hv, dev, "float64", n, "hv"), dev)
 
     def populations(self) -> np.ndarray:
         out = np.empty((self.q, self.ny, self.nx), dtype=self.dtype)
@@ -493,13 +509,15 @@ class Simulation:
 
     def populations_into(self, out):
         dev = self._on_device(out)
-        lbm_sw_get_populations(self.handle, _ptr(out, dev), dev)
+        lbm_sw_get_populations(self.handle, _ptr(out, dev, np.dtype(self.dtype).name, self.q * self.nx * self.ny,
+                                                 "populations"), dev)
 
     def set_populations(self, F, form: int = POST_COLLISION):
         dev = self._on_device(F)
         if not dev:
             F = np.ascontiguousarray(F, dtype=self.dtype).reshape(self.q, self.ny, self.nx)
-        lbm_sw_set_populations(self.handle, _ptr(F, dev), dev, form)
+        lbm_sw_set_populations(self.handle, _ptr(F, dev, np.dtype(self.dtype).name, self.q * self.nx * self.ny,
+                                                 "populations"), dev, form)
 
     def diagnostics(self, raise_unstable: bool = True):
         return lbm_sw_diagnostics(self.handle, raise_unstable)
@@ -559,7 +577,10 @@ class Batch:
         if not dev:
             h, hu = (np.ascontiguousarray(x, dtype=np.float64) for x in (h, hu))
             hv = None if hv is None else np.ascontiguousarray(hv, dtype=np.float64)
-        lbm_sw_batch_set_state(self.handle, i, _ptr(h, dev), _ptr(hu, dev), _ptr(hv, dev), dev)
+        # an index out of range is the library's to refuse (LBM_SW_E_ARG)
+        n = self.sizes[i][0] * self.sizes[i][1] if 0 <= i < len(self.sizes) else None
+        lbm_sw_batch_set_state(self.handle, i, _ptr(h, dev, "float64", n, "h"), _ptr(hu, dev, "float64", n, "hu"),
+                               _ptr(hv, dev, "float64", n, "hv"), dev)
 
     def step(self, n: int = 1):
         lbm_sw_batch_step(self.handle, n)
@@ -628,8 +649,9 @@ class Tape:
             g_hv = None if g_hv is None else np.ascontiguousarray(g_hv, dtype=np.float64)
             outs = [np.empty((ny, nx)) for _ in range(3 if want_momentum else 1)]
         d = [outs[0], outs[1] if want_momentum else None, outs[2] if want_momentum else None]
-        lbm_sw_adjoint(self.sim.handle, self.handle, _ptr(g_h, dev), _ptr(g_hu, dev), _ptr(g_hv, dev),
-                       _ptr(d[0], dev), _ptr(d[1], dev), _ptr(d[2], dev), dev)
+        n = nx * ny
+        g = [_ptr(x, dev, "float64", n, w) for x, w in ((g_h, "g_h"), (g_hu, "g_hu"), (g_hv, "g_hv"))]
+        lbm_sw_adjoint(self.sim.handle, self.handle, *g, _ptr(d[0], dev), _ptr(d[1], dev), _ptr(d[2], dev), dev)
         return tuple(outs) if want_momentum else outs[0]
 
     def info(self) -> lbm_sw_tape_info:

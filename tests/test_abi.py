@@ -7,6 +7,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_1401_0427_gb300 import build as libbuild
@@ -196,3 +197,42 @@ def test_no_gpu_means_an_error_not_a_fallback(lib):
     with pytest.raises(lbm_sw.LbmSwError) as err:
         lbm_sw.Simulation(16, 16)
     assert err.value.status == lbm_sw.E_CUDA
+
+
+def _handleless(nx, ny, precision=lbm_sw.FP32, dim=2):
+    """A Simulation object without a handle: enough to exercise the binding's own checks,
+    which run before any call into the library."""
+    sim = object.__new__(lbm_sw.Simulation)
+    sim.handle, sim.nx, sim.ny, sim.dim = None, nx, ny, dim
+    sim.q = 13 if dim == 2 else 5
+    sim.dtype = np.float64 if precision == lbm_sw.FP64 else np.float32
+    return sim
+
+
+def test_binding_refuses_buffers_of_another_type_or_size():
+    """The C library reads or writes a fixed number of elements of a fixed type through each
+    pointer: the binding refuses any other buffer before the call."""
+    sim = _handleless(6, 4)
+    ok = [np.empty((4, 6)) for _ in range(3)]
+    with pytest.raises(ValueError, match="dtype float32, expected float64"):
+        sim.moments_into(np.empty((4, 6), np.float32), *ok[1:])
+    with pytest.raises(ValueError, match="23 elements, expected 24"):
+        sim.moments_into(ok[0], np.empty(23), ok[2])
+    with pytest.raises(ValueError, match="contiguous"):
+        sim.moments_into(np.empty((4, 12))[:, ::2], *ok[1:])
+    with pytest.raises(ValueError, match="dtype float64, expected float32"):
+        sim.populations_into(np.empty((13, 4, 6)))
+    with pytest.raises(ValueError, match="expected 312"):
+        sim.populations_into(np.empty((13, 4, 5), np.float32))
+    with pytest.raises(ValueError, match="expected 24"):
+        sim.set_state(np.ones((4, 5)), np.zeros((4, 6)), np.zeros((4, 6)))
+    with pytest.raises(ValueError, match="solid must have shape"):
+        sim.set_obstacle(np.zeros((4, 5), np.uint8))
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError, match="dtype float32, expected float64"):
+        sim.moments_into(torch.empty((4, 6), dtype=torch.float32), *ok[1:])
+    with pytest.raises(ValueError, match="dtype float64, expected float32"):
+        sim.populations_into(torch.empty((13, 4, 6), dtype=torch.float64))
+    one_d = _handleless(10, 1, lbm_sw.FP64, dim=1)
+    with pytest.raises(ValueError, match="expected 50"):
+        one_d.populations_into(np.empty((5, 9)))

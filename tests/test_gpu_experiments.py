@@ -16,7 +16,7 @@ import pytest
 
 import oracle
 from paper_1401_0427_gb300 import experiments as ex
-from paper_1401_0427_gb300 import inputs, lbm_sw
+from paper_1401_0427_gb300 import inputs
 
 from gpu_helpers import FP64_TOL, rel_max, torch_stream
 

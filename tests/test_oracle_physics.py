@@ -187,23 +187,54 @@ def test_1d_mass_conservation_walls():
     assert abs(oracle.moments_1d(F, p)[0].sum() - h.sum()) <= 1e-13 * h.sum()
 
 
-def test_complex_step_matches_central_differences():
+@pytest.mark.parametrize("perturb", [0, 1, 2], ids=["h", "hu", "hv"])
+def test_complex_step_matches_central_differences(perturb):
+    """The derivative of a 2D run along a perturbation of h, hu or hv: complex step equals
+    central differences, and the real part of the complex run is the real run."""
     nx, ny, steps = 8, 6, 12
     p = oracle.params(nx, ny, a=0.05, bc=(WALL, PERIODIC, OUTFLOW, INFLOW), inflow=[(1.2, 0.1, 0.05)] * 4)
-    h, hu, hv = inputs.random_states(nx * ny, seed=51, h=(0.8, 1.6), speed=0.3)
-    dh = inputs.uniform(52, nx * ny, -1, 1)
+    W0 = inputs.random_states(nx * ny, seed=51, h=(0.8, 1.6), speed=0.3)
+    d = inputs.uniform(52, nx * ny, -1, 1)
     probe = inputs.uniform(53, 13 * nx * ny, -1, 1).reshape(13, ny, nx)
 
-    def J(hh):
-        return float((oracle.run_2d(oracle.equilibrium_2d(hh, hu, hv, p), steps, p) * probe).sum())
+    def W(t):
+        return [w + t * d if k == perturb else w for k, w in enumerate(W0)]
+
+    def J(t):
+        return float((oracle.run_2d(oracle.equilibrium_2d(*W(t), p), steps, p) * probe).sum())
 
     eps = 1e-6
-    fd = (J(h + eps * dh) - J(h - eps * dh)) / (2 * eps)
-    Fc = oracle.run_2d_cplx(oracle.equilibrium_2d_cplx(h + 1e-30j * dh, hu, hv, p), steps, p)
+    fd = (J(eps) - J(-eps)) / (2 * eps)
+    Fc = oracle.run_2d_cplx(oracle.equilibrium_2d_cplx(*W(1e-30j), p), steps, p)
     cs = float((Fc.imag * probe).sum()) / 1e-30
     assert abs(cs - fd) <= 1e-7 * max(1.0, abs(cs))
     # the complex run's real part is the real run
-    assert np.allclose(Fc.real, oracle.run_2d(oracle.equilibrium_2d(h, hu, hv, p), steps, p), rtol=0, atol=1e-15)
+    assert np.allclose(Fc.real, oracle.run_2d(oracle.equilibrium_2d(*W(0.0), p), steps, p), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("perturb", ["h", "q"])
+def test_complex_step_matches_central_differences_1d(perturb):
+    """The 1D complex-step entry points: the derivative of a 1D run (walls on one side,
+    inflow on the other) along a perturbation of h or q equals central differences, and the
+    real part of the complex run is the real run."""
+    n, steps = 24, 15
+    p = oracle.params(n, a=0.15, bc=(WALL, INFLOW), inflow=[None, (1.1, -0.05, 0.0), None, None])
+    h, q, _ = inputs.random_states(n, seed=61, h=(0.8, 1.6), speed=0.3)
+    d = inputs.uniform(62, n, -1, 1)
+    probe = inputs.uniform(63, 5 * n, -1, 1).reshape(5, n)
+
+    def W(t):
+        return (h + t * d, q) if perturb == "h" else (h, q + t * d)
+
+    def J(t):
+        return float((oracle.run_1d(oracle.equilibrium_1d(*W(t), p), steps, p) * probe).sum())
+
+    eps = 1e-6
+    fd = (J(eps) - J(-eps)) / (2 * eps)
+    Fc = oracle.run_1d_cplx(oracle.equilibrium_1d_cplx(*W(1e-30j), p), steps, p)
+    cs = float((Fc.imag * probe).sum()) / 1e-30
+    assert abs(cs - fd) <= 1e-7 * max(1.0, abs(cs))
+    assert np.allclose(Fc.real, oracle.run_1d(oracle.equilibrium_1d(*W(0.0), p), steps, p), rtol=0, atol=1e-15)
 
 
 def _golden_states():

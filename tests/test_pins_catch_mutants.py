@@ -75,6 +75,13 @@ MUTANTS = [
      "const int kMirrorX[13] = {0, 3, 2, 1, 4, 7, 6, 5, 8, 9, 10, 11, 12};"),
     ("2d_solid_cells_collide", "if (pr.solid && pr.solid[c]) continue;  // no fluid to relax",
      "if (false) continue;  // no fluid to relax"),
+    # complex-step entry points
+    ("1d_cplx_run_one_step_short", "run_1d<cplx>(z.data(), nsteps, *pr);",
+     "run_1d<cplx>(z.data(), nsteps > 0 ? nsteps - 1 : 0, *pr);"),
+    ("1d_cplx_equilibrium_drops_q_im",
+     "equilibrium_1d<cplx>(cplx(rho_re[i], rho_im[i]), cplx(q_re[i], q_im[i]), *pr, f);",
+     "equilibrium_1d<cplx>(cplx(rho_re[i], rho_im[i]), cplx(q_re[i], 0.0), *pr, f);"),
+    ("2d_cplx_equilibrium_qx_im_from_qy", "cplx(qx_re[c], qx_im[c])", "cplx(qx_re[c], qy_im[c])"),
     ("2d_obstacle_face_without_sign",
      "f[p * plane + c] = kEx2[p] != 0 ? kSignX[p] * g(kMirrorX[p], i, j) : kSignY[p] * g(kMirrorY[p], i, j);",
      "f[p * plane + c] = kEx2[p] != 0 ? g(kMirrorX[p], i, j) : g(kMirrorY[p], i, j);"),

@@ -75,6 +75,12 @@ MUTANTS = [
      "const int kMirrorX[13] = {0, 3, 2, 1, 4, 7, 6, 5, 8, 9, 10, 11, 12};"),
     ("2d_solid_cells_collide", "if (pr.solid && pr.solid[c]) continue;  // no fluid to relax",
      "if (false) continue;  // no fluid to relax"),
+    # stand-alone entry points
+    ("2d_moments_entry_transposed", "moments_2d(f, rho[c], qx[c], qy[c]);", "moments_2d(f, rho[c], qy[c], qx[c]);"),
+    ("1d_moments_entry_swapped", "moments_1d(f, rho[i], q[i]);", "moments_1d(f, q[i], rho[i]);"),
+    ("2d_stream_entry_skips_ghosts", "stream_2d<double>(Fs, F, *pr, ghosts);",
+     "{ oracle_params open = *pr; for (int k = 0; k < 4; ++k) open.bc[k] = BC_OUTFLOW; "
+     "stream_2d<double>(Fs, F, open, ghosts); }"),
     # complex-step entry points
     ("1d_cplx_run_one_step_short", "run_1d<cplx>(z.data(), nsteps, *pr);",
      "run_1d<cplx>(z.data(), nsteps > 0 ? nsteps - 1 : 0, *pr);"),

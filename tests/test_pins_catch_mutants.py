@@ -30,6 +30,7 @@ MUTANTS = [
      "feq[3] = K * w * beta * (1.0 + beta / pr.lam);"),
     ("1d_rho_without_f0", "rho = f[0] + (f[1] + f[2]);  // rho", "rho = (f[1] + f[2]);  // rho"),
     ("1d_g_velocities_swapped", "const int kEx1[5] = {0, 1, -1, 1, -1};", "const int kEx1[5] = {0, 1, -1, -1, 1};"),
+    ("1d_wall_without_partner", "const int kMirror1[5] = {0, 2, 1, 4, 3};", "const int kMirror1[5] = {0, 1, 2, 3, 4};"),
     ("1d_wall_keeps_momentum_sign", "const double kMirrorSign1[5] = {1, 1, 1, -1, -1};",
      "const double kMirrorSign1[5] = {1, 1, 1, 1, 1};"),
     ("1d_mrt_eps_without_lambda2", "m[2] = lam * lam * (f[1] + f[2] - 2.0 * f[0]);",
@@ -54,6 +55,8 @@ MUTANTS = [
     ("2d_relaxation_sign", "for (int j = 0; j < 13; ++j) f[j] = f[j] + pr.s * (feq[j] - f[j]);",
      "for (int j = 0; j < 13; ++j) f[j] = f[j] + pr.s * (f[j] - feq[j]);"),
     ("2d_mrt_inverse_sign", "f[2] = (s24 + m[2] / lam) / 2.0;", "f[2] = (s24 - m[2] / lam) / 2.0;"),
+    ("2d_gx_moves_along_y", "const int kEx2[13] = {0, 1, 0, -1, 0, 1, 0, -1, 0, 1, 0, -1, 0};",
+     "const int kEx2[13] = {0, 1, 0, -1, 0, 0, 1, 0, -1, 1, 0, -1, 0};"),
     ("2d_gy_directions_swapped", "const int kEy2[13] = {0, 0, 1, 0, -1, 0, 1, 0, -1, 0, 1, 0, -1};",
      "const int kEy2[13] = {0, 0, 1, 0, -1, 0, 1, 0, -1, 0, -1, 0, 1};"),
     ("2d_x_wall_keeps_normal_momentum", "const double kSignX[13] = {1, 1, 1, 1, 1, -1, -1, -1, -1, 1, 1, 1, 1};",

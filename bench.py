@@ -208,11 +208,26 @@ def cpu_oracle_mlups(W0, target_seconds: float = 15.0, max_steps: int = 120):
     t1 = time.perf_counter() - t
     steps = int(max(1, min(max_steps, math.ceil(target_seconds / max(t1, 1e-3)))))
     t = time.perf_counter()
-    oracle.run_2d(F, steps, p)
+    F = oracle.run_2d(F, steps, p)
     dt = time.perf_counter() - t
+    h = oracle.moments_2d(F, p)[0]
     return {"value": N * N * steps / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle, the full 4096x4096 grid of the workload for {steps} steps "
-                      f"({dt:.1f} s, OpenMP over rows)"}
+                      f"({dt:.1f} s, OpenMP over rows)"}, (steps + 2, h)
+
+
+def fp32_error_against_oracle(W0, oracle_run, stream, lbm_sw, torch):
+    """Relative L1 of h between the library's FP32 run (default kernel) and the FP64
+    oracle's run of the same steps on the full grid (the oracle state timed for the CPU
+    baseline)."""
+    steps, oh = oracle_run
+    with lbm_sw.Simulation(N, N, precision=lbm_sw.FP32, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream) as sim:
+        sim.set_state(*W0)
+        sim.step(steps)
+        gh = sim.moments()[0]
+    return {"relative_l1_h": float(np.abs(gh - oh).sum() / np.abs(oh).sum()), "steps": steps,
+            "against": f"the FP64 oracle run of the same {steps} steps on the full 4096x4096 grid "
+                       "(the state timed for cpu_baseline)", "bar": 1e-5}
 
 
 def _time_oracle(fn, min_seconds: float = 0.5):
@@ -332,9 +347,13 @@ def run_ours(args, world, rank, local):
     info = sim.info()
     unit = max(1, info.steps_per_launch)  # steps per launch of the step kernel
     kname = temporal_kernel_name(unit, cells) if unit > 1 else KERNEL_NAMES[(lbm_sw.KERNEL_VEC, dt_name)]
-    # The timed region is exactly --steps time steps: full launches of `unit` steps, then
-    # the remainder (one step per launch, bit-identical results).
-    nfull, rem = divmod(args.steps, unit)
+    # The timed region is exactly --steps time steps, launched as lbm_sw_step(steps) does
+    # (lbm_sw_step_plan: launches of `unit` steps, the tail split into shorter fused
+    # launches; bit-identical results).  Each planned launch is issued by its own call, with
+    # an event after it, so the launches of the dominant kernel are timed one by one.
+    plan = sim.step_plan(args.steps)
+    if any(sim.step_plan(k) != [k] for k in set(plan)):
+        plan = [args.steps]  # a size that one call would split: time the whole call instead
     launches0 = sim.info().kernel_launches
     sim.step(max(args.warmup, 3) * unit)  # warm-up: at least 3 launches of the timed kernel
     sim.synchronize()
@@ -346,16 +365,14 @@ def run_ours(args, world, rank, local):
     clocks.start()
     time.sleep(0.3)
 
-    events = [torch.cuda.Event(enable_timing=True) for _ in range(nfull + 2)]
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(len(plan) + 1)]
     barrier(world)
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
     events[0].record(stream)
-    for i in range(nfull):
-        sim.step(unit)
+    for i, k in enumerate(plan):
+        sim.step(k)
         events[i + 1].record(stream)
-    sim.step(rem)
-    events[nfull + 1].record(stream)
     torch.cuda.synchronize()
     t_wall1 = time.perf_counter()
     barrier(world)
@@ -363,7 +380,9 @@ def run_ours(args, world, rank, local):
     clocks.stop()
 
     total_ms = events[0].elapsed_time(events[-1])
-    per_launch = [events[i].elapsed_time(events[i + 1]) for i in range(nfull)]
+    per_launch = [events[i].elapsed_time(events[i + 1]) for i, k in enumerate(plan) if k == unit]
+    if not per_launch:
+        per_launch = [total_ms * unit / args.steps]
     launches = sim.info().kernel_launches - launches0 - warm_launches
     value, total_ms = job_throughput(world, cells * args.steps, total_ms)
     diag = sim.diagnostics()
@@ -382,7 +401,8 @@ def run_ours(args, world, rank, local):
                 "algorithmic_bytes_per_update": BYTES_PER_LUP[dt_name] / unit,
                 "median_launch_ms": float(np.median(per_launch)) if per_launch else None,
                 "one_step_per_launch_ceiling_MLUPS": per_step_ceiling,
-                "value_over_one_step_ceiling": value / world / per_step_ceiling}
+                "value_over_one_step_ceiling": value / world / per_step_ceiling,
+                "timed_launches_by_steps": {str(k): plan.count(k) for k in sorted(set(plan), reverse=True)}}
     sim.close()
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -401,7 +421,9 @@ def run_ours(args, world, rank, local):
         result["variants"] = variants(args, W0, stream, lbm_sw, torch)
         result["l1_error"] = result["variants"].pop("_l1")
     if rank == 0 and not args.quick and not args.skip_cpu:
-        result["cpu_baseline"] = cpu_oracle_mlups(W0)
+        result["cpu_baseline"], oracle_run = cpu_oracle_mlups(W0)
+        result["l1_error"] = {"vs_oracle": fp32_error_against_oracle(W0, oracle_run, stream, lbm_sw, torch),
+                              "vs_fp64_gpu": result.get("l1_error")}
         import oracle
 
         threads = oracle.set_threads(1)
@@ -455,8 +477,9 @@ def variants(args, W0, stream, lbm_sw, torch):
                      "HBM_GB_per_s": bpl * N * N / spl / (ms * 1e-3) / 1e9,
                      "frac_of_hbm_peak": bpl * N * N / spl / (ms * 1e-3) / 1e9 / peak}
     out["_l1"] = {"relative_l1_h": float(np.abs(hs["fp32"] - hs["fp64"]).sum() / np.abs(hs["fp64"]).sum()),
-                  "steps": JOB_STEPS, "against": "FP64 run of the same workload (equal to the FP64 oracle "
-                                                 "within 1e-12 in the parity tests)"}
+                  "steps": JOB_STEPS, "against": "the library's FP64 run of the same 1000 steps, which equals the "
+                                                 "FP64 oracle's whole run within 1e-12 (tests/test_gpu_configs.py::"
+                                                 "test_dam_break_4096_whole_run_matches_oracle)"}
     out["fp32_temporal_k"] = temporal_sweep(W0, stream, lbm_sw, torch)
     out["fp32_closed_basin"] = bounded_variant(W0, stream, lbm_sw, torch)
     out["fp32_mrt"] = mrt_variant(W0, stream, lbm_sw, torch)

@@ -67,7 +67,7 @@ typedef struct lbm_sw lbm_sw;
 #define LBM_SW_E_ARG (-1)      /* invalid argument (NULL, size, parameter out of range) */
 #define LBM_SW_E_CUDA (-2)     /* a CUDA call failed; see lbm_sw_last_error */
 #define LBM_SW_E_UNSTABLE (-3) /* a diagnostic found NaN/Inf or a depth h <= 0 */
-#define LBM_SW_E_TIMEOUT (-4)  /* a bounded device-side wait gave up */
+/* (-4 is not used: no kernel of this library waits on a flag or on another grid) */
 #define LBM_SW_E_STATE (-5)    /* call not valid in the handle's state (e.g. no state set) */
 #define LBM_SW_E_NOMEM (-6)    /* device allocation failed */
 
@@ -113,8 +113,9 @@ typedef struct lbm_sw lbm_sw;
 #define LBM_SW_KERNEL_TEMPORAL 4 /* 2D FP32: temporal_steps steps per launch (temporal
                                     blocking: a row wavefront through shared memory, 104/k bytes of
                                     HBM traffic per cell update plus halos), BGK, or MRT with an even
-                                    temporal_steps; the remainder of n, obstacles and other cases
-                                    use VEC; results equal VEC bit for bit */
+                                    temporal_steps; the tail of n runs as shorter fused launches
+                                    (lbm_sw_step), obstacles use their own kernel; results equal
+                                    VEC bit for bit */
 
 typedef struct lbm_sw_params {
   int dim;             /* 1 (D1Q3Q2) or 2 (D2Q5Q4Q4) */
@@ -159,7 +160,8 @@ LBM_SW_API int lbm_sw_params_init(lbm_sw_params* p);
  * nonzero reserved fields), LBM_SW_E_NOMEM, LBM_SW_E_CUDA; *out is then NULL. */
 LBM_SW_API int lbm_sw_create(const lbm_sw_params* p, lbm_sw** out);
 
-/* Release the handle and its device memory (synchronises its stream). NULL-safe. */
+/* Release the handle and its device memory (synchronises its stream). NULL-safe.
+ * A utility of the library: no passage of the paper corresponds to it. */
 LBM_SW_API void lbm_sw_destroy(lbm_sw* h);
 
 /* Set the populations to the equilibrium of W = (h, hu, hv) (paper: the state at
@@ -168,12 +170,29 @@ LBM_SW_API void lbm_sw_destroy(lbm_sw* h);
  * stream reaches this work.  Errors: LBM_SW_E_ARG, LBM_SW_E_CUDA. */
 LBM_SW_API int lbm_sw_set_state(lbm_sw* h, const double* depth, const double* hu, const double* hv, int on_device);
 
-/* Advance n >= 0 time steps, each one fused pull-stream + collide kernel (streaming
- * with the boundary rules, moments, equilibria, relaxation), asynchronously on the
- * handle's stream; long runs replay a captured CUDA graph of graph_chunk steps.
- * Errors: LBM_SW_E_ARG (n < 0), LBM_SW_E_STATE (no state set), LBM_SW_E_CUDA
- * (launch failure; kernel faults surface at the next synchronising call). */
+/* Advance n >= 0 time steps (each: streaming with the boundary rules, moments,
+ * equilibria, relaxation), asynchronously on the handle's stream.  How the steps map to
+ * kernel launches depends on the kernel in use (lbm_sw_get_info):
+ *   TEMPORAL: fused launches of up to temporal_steps = K steps each (temporal blocking):
+ *             launches of K while more than K + 8 steps remain, then the cheapest split of
+ *             the rest into launches of at most K steps (even counts always; odd counts
+ *             above one only on BGK grids with every side periodic; one step per launch
+ *             only where no fused launch fits), e.g. 20 = 6 + 6 + 4 + 4 at K = 6;
+ *             lbm_sw_step_plan lists the launches;
+ *   CLUSTER:  one launch for all n steps (1D lines up to 16384 cells);
+ *   VEC, SIMPLE, obstacles: one launch per step; long runs replay a captured CUDA graph of
+ *             graph_chunk steps.
+ * Every mapping gives the same bits.  Errors: LBM_SW_E_ARG (n < 0), LBM_SW_E_STATE (no
+ * state set), LBM_SW_E_CUDA (launch failure; kernel faults surface at the next
+ * synchronising call). */
 LBM_SW_API int lbm_sw_step(lbm_sw* h, int n);
+
+/* The kernel launches lbm_sw_step(h, n) would make now: writes the steps each launch
+ * advances, in order, to sizes[0 .. min(count, max_sizes) - 1] and returns count (the
+ * number of launches; 0 for n = 0).  A utility of the library (no passage of the paper
+ * corresponds to it); launches nothing.  Errors: LBM_SW_E_ARG (NULL handle, n < 0,
+ * max_sizes < 0, or sizes NULL with max_sizes > 0). */
+LBM_SW_API int lbm_sw_step_plan(const lbm_sw* h, int n, int* sizes, int max_sizes);
 
 /* Relax each moment at its own rate: the MRT form of Eq. 2-relaxation,
  * m*_l = m_l + s_l (m_l^eq - m_l), on the moment bases the paper gives.  rates[count]:
@@ -215,13 +234,18 @@ LBM_SW_API int lbm_sw_diagnostics(lbm_sw* h, double out[4]);
 
 /* Copy the stored (post-collision) populations out as dense planes [q][ny][nx] of
  * the handle's precision; lbm_sw_get_info gives the byte count.  Synchronises for
- * host memory. */
+ * host memory.  A utility of the library (checkpoints, parity checks): no passage of the
+ * paper corresponds to it. */
 LBM_SW_API int lbm_sw_get_populations(lbm_sw* h, void* dst, int on_device);
 
 /* Load dense planes [q][ny][nx] of the handle's precision.  form =
  * LBM_SW_POST_COLLISION stores them as they are (a checkpoint written by
- * lbm_sw_get_populations); LBM_SW_PRE_COLLISION collides them on the device first,
- * so that the next step streams their post-collision values. */
+ * lbm_sw_get_populations); LBM_SW_PRE_COLLISION collides them on the device first
+ * (Eq. 2-relaxation with the equilibria of sections 2-3), so that the next step streams
+ * their post-collision values.  The `form` argument extends the population exchange of
+ * the plain set/get pair: it lets a caller start from arbitrary (non-equilibrium)
+ * populations as the oracle does.  A utility of the library otherwise: no passage of the
+ * paper corresponds to loading raw populations. */
 LBM_SW_API int lbm_sw_set_populations(lbm_sw* h, const void* src, int on_device, int form);
 
 /* ---- Batched instances ----
@@ -382,8 +406,10 @@ LBM_SW_API const char* lbm_sw_tape_last_error(const lbm_sw_tape* t);
  * process exits).  Larger ny, NULL pointers, bad sizes or pitches return LBM_SW_E_ARG without
  * launching anything; a failed CUDA call returns LBM_SW_E_CUDA.
  *
- * The first call on a device (with that device current) looks up the device address of the
- * static array; make that first call before any stream capture.  All calls share the array
+ * Every call looks up the device address of the static array in the current context
+ * (cudaGetSymbolAddress; not cached, so a device reset or a second context of the device
+ * gets the address of its own copy).  The first call in a context loads the library's
+ * device code there: make that first call before any stream capture.  All calls share the array
  * and each call fully rewrites the part it reads, so nothing needs clearing between calls;
  * calls whose work overlaps on the GPU (different streams, or different threads) race on the
  * array and must be serialised by the caller. */
@@ -397,7 +423,8 @@ LBM_SW_API int lbm_sw_synchronize(lbm_sw* h);
 /* Sizes and counters of the handle. */
 LBM_SW_API int lbm_sw_get_info(const lbm_sw* h, lbm_sw_info* out);
 
-/* Message of the last failure on this handle ("" if none); valid until the next call. */
+/* Message of the last failure on this handle ("" if none); valid until the next call.
+ * Utilities from here on: no passage of the paper corresponds to them. */
 LBM_SW_API const char* lbm_sw_last_error(const lbm_sw* h);
 
 /* Message of the last failed lbm_sw_create on the calling thread ("" if it succeeded). */

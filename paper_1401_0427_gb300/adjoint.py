@@ -14,7 +14,13 @@ from . import lbm_sw
 
 
 class ShallowWaterRun(torch.autograd.Function):
-    """h_T = run(h0): depth after `steps` steps from rest (discharge zero)."""
+    """h_T = run(h0): depth after `steps` steps from rest (discharge zero).
+
+    The forward pass runs on the caller's Simulation: it overwrites that handle's state
+    (set_state(h0, 0, 0), then `steps` steps), so afterwards `sim` holds the state at step T.
+    Its checkpoint tape owns its own device memory and is released when the autograd graph
+    that holds it is freed, so backward may run more than once (retain_graph=True); each
+    backward replays the tape's checkpoints and leaves the handle's state alone."""
 
     @staticmethod
     def forward(ctx, h0: torch.Tensor, sim: lbm_sw.Simulation, steps: int, interval: int = 0):
@@ -34,7 +40,6 @@ class ShallowWaterRun(torch.autograd.Function):
     def backward(ctx, g_hT: torch.Tensor):
         g = g_hT.contiguous().to(torch.float64)
         d_h0 = ctx.tape.adjoint(g)
-        ctx.tape.close()
         return d_h0, None, None, None
 
 

@@ -1,6 +1,7 @@
 // C ABI of the library (declarations and contracts in include/lbm_sw.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -61,6 +62,54 @@ bool temporal_active(const lbm_sw* h) {
   // +14 % fused at K = 4; 724^2 even, 628^2 -12 %)
   const bool large = static_cast<long long>(h->p.nx) * h->p.ny >= (1LL << 19);
   return lbm::temporal_mrt_supported(h->p.bc, h->p.nx, h->temporal_k) && (large || !h->auto_kernel);
+}
+
+// Relative cost of one launch of k fused steps (k = 1: one step per launch), measured as
+// ms per launch on the 4096^2 FP32 periodic dam-break: 0.257 (one step), 0.387, 0.386,
+// 0.338, 0.515, 0.437, 0.637, 0.751 (k = 2 .. 8).  Used only to split the tail of a call
+// into launches; every split gives the same bits.
+constexpr double kLaunchCost[9] = {0.0, 0.257, 0.387, 0.386, 0.338, 0.515, 0.437, 0.637, 0.751};
+
+// Steps per launch for lbm_sw_step(n) on a fused handle, into plan[] (returns the count of
+// launches, at most max_plan).  Launches of the handle's K while more than K + 8 steps
+// remain, then the cheapest split of the rest (at most K + 8 steps) into launches of at
+// most K steps: even sizes always (the two-column kernels), odd sizes above one only where
+// the one-column periodic kernel runs (BGK, every side periodic).  At K = 6 a call of 20
+// steps runs 6 + 6 + 4 + 4, one of 8 runs 4 + 4; a single step is left only where no fused
+// size fits.
+int plan_fused_launches(const lbm_sw* h, int n, int* plan, int max_plan) {
+  const int K = h->temporal_k;
+  const bool odd_ok = !h->mrt && h->p.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC &&
+                      h->p.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
+  auto allowed = [&](int k) { return k == 1 || (k <= K && (k % 2 == 0 || odd_ok)); };
+  int count = 0;
+  while (n > K + 8 && count < max_plan) {
+    plan[count++] = K;
+    n -= K;
+  }
+  // cheapest split of the remaining n <= K + 8 steps (n <= 16)
+  double best[17];
+  int first[17];
+  best[0] = 0.0;
+  first[0] = 0;
+  for (int m = 1; m <= n; ++m) {
+    best[m] = 1e300;
+    first[m] = 1;
+    for (int k = 1; k <= 8 && k <= m; ++k) {
+      if (!allowed(k)) continue;
+      const double c = kLaunchCost[k] + best[m - k];
+      if (c < best[m]) {
+        best[m] = c;
+        first[m] = k;
+      }
+    }
+  }
+  // larger launches first
+  int tail[16], nt = 0;
+  for (int m = n; m > 0; m -= first[m]) tail[nt++] = first[m];
+  std::sort(tail, tail + nt, [](int a, int b) { return a > b; });
+  for (int i = 0; i < nt && count < max_plan; ++i) plan[count++] = tail[i];
+  return count;
 }
 
 // One step from buffer `from` into the other buffer, on stream st (the TEMPORAL choice
@@ -156,7 +205,6 @@ const char* lbm_sw_status_string(int status) {
     case LBM_SW_E_ARG: return "invalid argument";
     case LBM_SW_E_CUDA: return "CUDA error";
     case LBM_SW_E_UNSTABLE: return "unstable state (NaN/Inf or depth <= 0)";
-    case LBM_SW_E_TIMEOUT: return "bounded device wait timed out";
     case LBM_SW_E_STATE: return "call not valid in the current state";
     case LBM_SW_E_NOMEM: return "out of device memory";
     default: return "unknown status";
@@ -328,31 +376,25 @@ int lbm_sw_step(lbm_sw* h, int n) {
     }
   }
   if (temporal_active(h)) {
-    const int K = h->temporal_k;
-    while (n >= K) {
-      cudaError_t e = h->mrt ? lbm::launch_step2d_temporal_mrt(args<float>(h, h->cur), consts(h), K, h->stream,
-                                                               h->sm_count)
-                             : lbm::launch_step2d_temporal(args<float>(h, h->cur), consts(h), K, h->stream, h->sm_count);
-      if (e != cudaSuccess) return cuda_fail(h, e, "temporal step launch");
-      h->cur ^= 1;
-      n -= K;
-      h->steps_done += K;
-      h->launches += 1;
-    }
-    const int saved = h->kernel;
-    h->kernel = LBM_SW_KERNEL_VEC;  // the remainder, one step per launch
+    int plan[64];
     while (n > 0) {
-      cudaError_t e = launch_one_step(h, h->cur, h->stream);
-      if (e != cudaSuccess) {
-        h->kernel = saved;
-        return cuda_fail(h, e, "step kernel launch");
+      const int count = plan_fused_launches(h, n, plan, 64);
+      for (int i = 0; i < count; ++i) {
+        const int k = plan[i];
+        cudaError_t e;
+        if (k == 1) {  // one step per launch (the vectorised kernel; FP32 here)
+          e = lbm::launch_step2d<float>(args<float>(h, h->cur), consts(h), LBM_SW_KERNEL_VEC, h->stream);
+        } else {
+          e = h->mrt ? lbm::launch_step2d_temporal_mrt(args<float>(h, h->cur), consts(h), k, h->stream, h->sm_count)
+                     : lbm::launch_step2d_temporal(args<float>(h, h->cur), consts(h), k, h->stream, h->sm_count);
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, k == 1 ? "step kernel launch" : "temporal step launch");
+        h->cur ^= 1;
+        n -= k;
+        h->steps_done += k;
+        h->launches += 1;
       }
-      h->cur ^= 1;
-      n -= 1;
-      h->steps_done += 1;
-      h->launches += 1;
     }
-    h->kernel = saved;
     return LBM_SW_OK;
   }
   while (n > 0) {
@@ -375,6 +417,37 @@ int lbm_sw_step(lbm_sw* h, int n) {
     }
   }
   return LBM_SW_OK;
+}
+
+int lbm_sw_step_plan(const lbm_sw* h, int n, int* sizes, int max_sizes) {
+  if (!h || n < 0 || max_sizes < 0 || (max_sizes > 0 && !sizes)) return LBM_SW_E_ARG;
+  int count = 0;
+  auto put = [&](int k) {
+    if (count < max_sizes) sizes[count] = k;
+    ++count;
+  };
+  if (n == 0) return 0;
+  if (h->p.dim == 1 && h->kernel == LBM_SW_KERNEL_CLUSTER) {
+    const int max_cells = h->p.precision == LBM_SW_FP64 ? lbm::cluster1d_max_cells<double>()
+                                                        : lbm::cluster1d_max_cells<float>();
+    if (h->p.nx <= max_cells) {
+      put(n);
+      return count;
+    }
+  }
+  if (temporal_active(h)) {
+    int plan[64];
+    while (n > 0) {
+      const int c = plan_fused_launches(h, n, plan, 64);
+      for (int i = 0; i < c; ++i) {
+        put(plan[i]);
+        n -= plan[i];
+      }
+    }
+    return count;
+  }
+  for (int i = 0; i < n; ++i) put(1);
+  return count;
 }
 
 int lbm_sw_get_moments(lbm_sw* h, double* depth, double* hu, double* hv, int on_device) {

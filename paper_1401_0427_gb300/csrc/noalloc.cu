@@ -3,18 +3,17 @@
 //
 // The pass-1 partials live in a file-scope device array instead of memory the caller
 // or the library allocates.  In host code `g_noalloc_partials` names a host-side
-// stand-in, not a device address, so its device address is looked up once per
-// device (with that device current) and handed to the kernels.
+// stand-in, not a device address, so every call looks up its device address in the
+// current context (cudaGetSymbolAddress) and hands that to the kernels.  The lookup is not
+// cached: after a device reset, or in another context of the same device, the runtime loads
+// the module again at another address, and a cached pointer would go stale.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "internal.h"
 
 namespace {
 
 constexpr int kMaxRows = LBM_SW_NOALLOC_MAX_ROWS;  // one pass-1 partial per row
-constexpr int kMaxDevices = 64;
 
 // 5 doubles (sum h, sum hu, sum hv, min h, bad cells) per row: 8192 * 5 * 8 = 327,680
 // bytes.  Every device that loads the library holds this array until the process
@@ -23,24 +22,13 @@ constexpr int kMaxDevices = 64;
 // overlap on the GPU share the array and race.
 static __device__ __align__(256) double g_noalloc_partials[kMaxRows * 5];
 
-std::mutex g_setup_mutex;
-double* g_partials_on_device[kMaxDevices] = {};
-
-// Device address of g_noalloc_partials on the current device; the first call on a
-// device looks it up (cudaGetSymbolAddress) and caches it.
+// Device address of g_noalloc_partials in the current context (the first call in a
+// context loads the module there).
 cudaError_t partials_on_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_partials_on_device[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-    if (e != cudaSuccess) return e;
-    g_partials_on_device[dev] = static_cast<double*>(p);
-  }
-  *out = g_partials_on_device[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 

@@ -24,7 +24,7 @@ FP32, FP64 = 0, 1
 POST_COLLISION, PRE_COLLISION = 0, 1
 KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_VEC, KERNEL_CLUSTER, KERNEL_TEMPORAL = 0, 1, 2, 3, 4
 
-OK, E_ARG, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE, E_NOMEM = 0, -1, -2, -3, -4, -5, -6
+OK, E_ARG, E_CUDA, E_UNSTABLE, E_STATE, E_NOMEM = 0, -1, -2, -3, -5, -6
 
 
 class LbmSwError(RuntimeError):
@@ -121,6 +121,7 @@ SIGNATURES = {
     "lbm_sw_destroy": (None, [_H]),
     "lbm_sw_set_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lbm_sw_step": (ctypes.c_int, [_H, ctypes.c_int]),
+    "lbm_sw_step_plan": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "lbm_sw_set_relaxation": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "lbm_sw_set_obstacle": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
     "lbm_sw_get_moments": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -216,6 +217,15 @@ def lbm_sw_set_state(h: int, depth: int, hu: int, hv: int | None, on_device: boo
 
 def lbm_sw_step(h: int, n: int) -> None:
     _check(load().lbm_sw_step(h, int(n)), h, "lbm_sw_step")
+
+
+def lbm_sw_step_plan(h: int, n: int) -> list[int]:
+    """Steps advanced by each kernel launch that lbm_sw_step(h, n) would make, in order."""
+    lib = load()
+    count = _check(lib.lbm_sw_step_plan(h, int(n), None, 0), h, "lbm_sw_step_plan")
+    sizes = (ctypes.c_int * max(count, 1))()
+    _check(lib.lbm_sw_step_plan(h, int(n), sizes, count), h, "lbm_sw_step_plan")
+    return list(sizes[:count])
 
 
 def lbm_sw_set_relaxation(h: int, rates=None) -> None:
@@ -472,6 +482,10 @@ class Simulation:
 
     def step(self, n: int = 1):
         lbm_sw_step(self.handle, n)
+
+    def step_plan(self, n: int) -> list[int]:
+        """Steps per kernel launch of ``step(n)``, in order (nothing is launched)."""
+        return lbm_sw_step_plan(self.handle, n)
 
     def set_relaxation(self, rates=None):
         lbm_sw_set_relaxation(self.handle, rates)

@@ -1,5 +1,5 @@
-"""Discrete adjoint (lbm_sw_tape_* / lbm_sw_adjoint) against complex-step derivatives of
-the FP64 oracle.
+"""Discrete adjoint (lbm_sw_tape_* / lbm_sw_adjoint) against complex-step derivatives and
+central finite differences of the FP64 oracle.
 
 For L = 1/2 sum (h_T - h_obs)^2 after T steps from f = f^eq(W0), the directional
 derivative dL/dW0 . delta from the GPU adjoint must equal Im L(W0 + i eps delta) / eps
@@ -79,6 +79,37 @@ def test_fp64_gradient_matches_complex_step_periodic_64():
         want = _oracle_directional((h_guess, z, z), (d, z, z), steps, p, h_obs)
         got = float((gh * d).sum())
         assert abs(got - want) <= 1e-9 * max(abs(want), 1e-3), (got, want)
+
+
+def _oracle_loss(W0, steps, p, h_obs):
+    hT = _oracle_hT(W0, steps, p)
+    return 0.5 * float(((hT - h_obs) ** 2).sum())
+
+
+def test_fp64_gradient_matches_central_differences_of_the_oracle_64():
+    """The same gradient against central finite differences of the FP64 oracle,
+    (L(W0 + eps d) - L(W0 - eps d)) / (2 eps) with eps = 1e-6, along random and single-cell
+    directions of h and random directions of hu and hv.  The difference quotient is accurate
+    to about 1e-8 here: its truncation error is of order eps^2 times the third derivative of
+    L (~ 1e-11), and the rounding of the two losses (L ~ 10, relative rounding ~ 1e-15 after
+    200 steps) contributes ~ 1e-14 / 2e-6 ~ 1e-8; the bar is 1e-6 relative."""
+    n, steps, eps = 64, 200, 1e-6
+    h_true, h_guess = _workload(n)
+    z = np.zeros((n, n))
+    p = oracle.params(n, n, a=0.05)
+    h_obs = _oracle_hT((h_true, z, z), steps, p)
+    W0 = (h_guess, z, z)
+    grads, _, _ = _gpu_gradient(W0, steps, h_obs, precision=lbm_sw.FP64)
+    cases = [(0, d) for d in _directions(n, 3, 700)]
+    cases += [(comp, inputs.uniform(710 + comp, n * n, -1, 1).reshape(n, n)) for comp in (1, 2)]
+    for comp, d in cases:
+        plus = [w.copy() for w in W0]
+        minus = [w.copy() for w in W0]
+        plus[comp] += eps * d
+        minus[comp] -= eps * d
+        want = (_oracle_loss(plus, steps, p, h_obs) - _oracle_loss(minus, steps, p, h_obs)) / (2 * eps)
+        got = float((grads[comp] * d).sum())
+        assert abs(got - want) <= 1e-6 * max(abs(want), 1e-3), (comp, got, want)
 
 
 @pytest.mark.parametrize("bc", [(W, O, I, W), (I, W, P, P), (O, O, W, W)], ids=["WOIW", "IWPP", "OOWW"])
@@ -176,6 +207,30 @@ def test_autograd_function_and_recovery():
     err0 = np.abs(h_guess - h_true).mean()
     err1 = np.abs(h_fit.cpu().numpy() - h_true).mean()
     assert err1 < 0.5 * err0
+
+
+def test_autograd_backward_twice_with_retain_graph():
+    """The tape lives as long as the autograd graph: a second backward (retain_graph=True)
+    replays the same checkpoints and doubles the accumulated gradient; the forward pass leaves
+    the caller's Simulation at step T."""
+    import torch
+
+    from paper_1401_0427_gb300 import adjoint
+
+    n, steps = 64, 40
+    h_true, h_guess = _workload(n)
+    dev = torch.device("cuda")
+    with lbm_sw.Simulation(n, n, precision=lbm_sw.FP64, stream=torch_stream()) as sim:
+        h_obs = torch.tensor(h_true, device=dev)
+        h0 = torch.tensor(h_guess, device=dev, requires_grad=True)
+        hT = adjoint.run(h0, sim, steps)
+        assert sim.info().steps_done == steps
+        assert np.array_equal(sim.moments()[0], hT.detach().cpu().numpy())
+        loss = 0.5 * ((hT - h_obs) ** 2).sum()
+        loss.backward(retain_graph=True)
+        g1 = h0.grad.clone()
+        loss.backward()
+        assert torch.equal(h0.grad, 2 * g1)
 
 
 def _gradient_with_kernel(W0, steps, h_obs, precision, bc, kernel):

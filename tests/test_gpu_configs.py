@@ -5,12 +5,13 @@
 * 2D shock reflection, 512 x 512, 2000 steps (inflow x-, wall x+, periodic in y):
   the field is y-invariant (kept bit for bit by both sides), so the oracle runs one
   row of 512 cells and every GPU row is compared with it.
-* 2D circular dam-break, 4096 x 4096, 1000 steps, FP32: too large for the oracle
-  to follow in full, so (a) the same physical case at 1024 x 1024 (250 steps,
-  same final time) is compared in full, (b) at full size, one more step from the
-  GPU state is recomputed by the oracle on sampled patches (corners, edges,
-  interior), (c) at full size the unperturbed case keeps the D4 symmetry bit for bit
-  and the FP64 totals of the FP32 state are conserved.
+* 2D circular dam-break, 4096 x 4096, 1000 steps: (a) the whole run, FP64 and FP32,
+  against the oracle run in full on every host core (marked slow: minutes of
+  oracle time), (b) the same physical case at 1024 x 1024 (250 steps, same final
+  time) compared in full, (c) at full size, one more step from the GPU state
+  recomputed by the oracle on sampled patches (corners, edges, interior), (d) at
+  full size the unperturbed case keeps the D4 symmetry bit for bit and the FP64
+  totals of the FP32 state are conserved.
 """
 
 import numpy as np
@@ -122,6 +123,32 @@ def _haloed_patch_step(sub, w, h):
     streamed = oracle.stream_2d(np.ascontiguousarray(sub), p)  # halo ring is garbage, interior exact
     interior = np.ascontiguousarray(streamed[:, 1:-1, 1:-1])
     return oracle.collide_2d(interior, oracle.params(w, h, a=0.05))
+
+
+@pytest.mark.slow
+def test_dam_break_4096_whole_run_matches_oracle():
+    """The circular dam-break workload as stated, in full: 4096 x 4096 periodic, 1000 steps
+    from the seeded initial state.  The oracle runs the whole of it on every host core
+    (1.7e10 FP64 cell updates, a few minutes, about 5 GB of host memory).  FP64 on the GPU:
+    max |gpu - oracle| / max |oracle| <= 1e-12 for h, hu and hv.  FP32 on the GPU (the
+    library's default kernel for this grid, 6 fused steps per launch): relative L1 of h
+    <= 1e-5."""
+    n, steps = 4096, 1000
+    W0 = inputs.circular_dam_break_2d(n, seed=inputs.stream_seed(3))
+    threads = oracle.set_threads(0)
+    try:
+        p = oracle.params(n, n, a=0.05)
+        F = oracle.run_2d(oracle.equilibrium_2d(*W0, p), steps, p)
+        oh, ohu, ohv = oracle.moments_2d(F, p)
+        del F
+    finally:
+        oracle.set_threads(threads)
+    gh, ghu, ghv = _run_moments(n, n, W0, steps, precision=lbm_sw.FP64, bc=(P, P, P, P), a=0.05)
+    scale = np.abs(oh).max()
+    assert rel_max(gh, oh) <= FP64_TOL
+    assert max(np.abs(ghu - ohu).max(), np.abs(ghv - ohv).max()) <= FP64_TOL * scale
+    fh, _, _ = _run_moments(n, n, W0, steps, precision=lbm_sw.FP32, bc=(P, P, P, P), a=0.05)
+    assert rel_l1(fh, oh) <= FP32_L1_TOL
 
 
 def test_dam_break_4096_sampled_step_parity():

@@ -84,15 +84,47 @@ def test_default_steps_per_launch(nx, ny, want):
         assert sim.info().steps_per_launch == want
 
 
-def test_auto_temporal_counts_launches_and_steps():
-    """AUTO on a periodic 1024^2 FP32 grid: 6 steps per launch, the remainder one per launch."""
+# Launches of lbm_sw_step(n) at K = 6: launches of 6 while more than 14 steps remain, then the
+# cheapest split of the rest into fused launches (4 + 4 in place of 6 + 2; odd sizes only on
+# periodic BGK grids, else one single step for an odd count).
+SCHEDULES_PERIODIC = {1: 1, 2: 1, 3: 1, 4: 1, 5: 1, 6: 1, 7: 2, 8: 2, 9: 2, 10: 2, 12: 2, 13: 3, 14: 3, 20: 4, 22: 4,
+                      23: 4, 1000: 167}
+SCHEDULES_WALLS = {1: 1, 2: 1, 3: 2, 5: 2, 7: 2, 8: 2, 13: 3, 20: 4, 22: 4, 23: 5}
+
+
+@pytest.mark.parametrize("steps", sorted(SCHEDULES_PERIODIC))
+def test_auto_temporal_counts_launches_and_steps(steps):
+    """AUTO on a periodic 1024^2 FP32 grid: 6 steps per launch, the tail split into fused
+    launches (20 = 6 + 6 + 4 + 4, 22 = 6 + 6 + 6 + 4, 8 = 4 + 4)."""
     W0 = inputs.circular_dam_break_2d(1024, seed=inputs.stream_seed(3))
     with lbm_sw.Simulation(1024, 1024, stream=torch_stream()) as sim:
         sim.set_state(*W0)
         before = sim.info().kernel_launches
-        sim.step(22)
+        sim.step(steps)
         info = sim.info()
-        assert info.steps_done == 22 and info.steps_per_launch == 6 and info.kernel_launches - before == 3 + 4
+        assert info.steps_done == steps and info.steps_per_launch == 6
+        assert info.kernel_launches - before == SCHEDULES_PERIODIC[steps]
+
+
+@pytest.mark.parametrize("bc", [(P, P, P, P), (W, W, W, W), (I, O, W, W)], ids=lambda b: "".join("PWOI"[k] for k in b))
+@pytest.mark.parametrize("steps", [2, 3, 5, 7, 8, 13, 20, 22, 23])
+def test_mixed_schedule_equals_single_steps(bc, steps):
+    """The split tails (fused launches of 2 .. 6 steps, a single step only for an odd count on
+    sides that are not periodic) give the bits of one step per launch."""
+    n = 1024
+    F0 = inputs.random_populations(13, 96, n, seed=7700 + steps).astype(np.float32)
+    F0 = np.ascontiguousarray(np.tile(F0, (1, n // 96 + 1, 1))[:, :n, :])
+    a = _run(F0, steps, bc, lbm_sw.KERNEL_VEC)
+    with lbm_sw.Simulation(n, n, precision=lbm_sw.FP32, bc=bc, inflow=INFLOW, stream=torch_stream()) as sim:
+        assert sim.info().kernel == lbm_sw.KERNEL_TEMPORAL and sim.info().steps_per_launch == 6
+        sim.set_populations(F0, form=lbm_sw.PRE_COLLISION)
+        before = sim.info().kernel_launches
+        sim.step(steps)
+        launches = sim.info().kernel_launches - before
+        b = sim.populations()
+    assert np.array_equal(a, b), steps
+    if bc != (P, P, P, P):
+        assert launches == SCHEDULES_WALLS[steps]
 
 
 @pytest.mark.parametrize("bc", [(P, P, P, P), (W, W, W, W), (W, O, I, W), (I, W, P, P), (O, I, W, O), (P, P, W, O)],

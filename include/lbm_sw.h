@@ -175,9 +175,9 @@ LBM_SW_API int lbm_sw_set_state(lbm_sw* h, const double* depth, const double* hu
  * kernel launches depends on the kernel in use (lbm_sw_get_info):
  *   TEMPORAL: fused launches of up to temporal_steps = K steps each (temporal blocking):
  *             launches of K while more than K + 8 steps remain, then the cheapest split of
- *             the rest into launches of at most K steps (even counts always; odd counts
- *             above one only on BGK grids with every side periodic; one step per launch
- *             only where no fused launch fits), e.g. 20 = 6 + 6 + 4 + 4 at K = 6;
+ *             the rest into launches of at most K steps (K and even counts always; other
+ *             odd counts above one only on BGK grids with every side periodic; at most one
+ *             single step), e.g. 20 = 6 + 6 + 4 + 4 at K = 6;
  *             lbm_sw_step_plan lists the launches;
  *   CLUSTER:  one launch for all n steps (1D lines up to 16384 cells);
  *   VEC, SIMPLE, obstacles: one launch per step; long runs replay a captured CUDA graph of

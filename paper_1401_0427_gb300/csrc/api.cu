@@ -10,6 +10,7 @@
 #include <string>
 
 #include "internal.h"
+#include "launch_plan.h"
 
 namespace {
 
@@ -64,53 +65,14 @@ bool temporal_active(const lbm_sw* h) {
   return lbm::temporal_mrt_supported(h->p.bc, h->p.nx, h->temporal_k) && (large || !h->auto_kernel);
 }
 
-// Relative cost of one launch of k fused steps (k = 1: one step per launch), measured as
-// ms per launch on the 4096^2 FP32 periodic dam-break: 0.257 (one step), 0.387, 0.386,
-// 0.338, 0.515, 0.437, 0.637, 0.751 (k = 2 .. 8).  Used only to split the tail of a call
-// into launches; every split gives the same bits.
-constexpr double kLaunchCost[9] = {0.0, 0.257, 0.387, 0.386, 0.338, 0.515, 0.437, 0.637, 0.751};
-
-// Steps per launch for lbm_sw_step(n) on a fused handle, into plan[] (returns the count of
-// launches, at most max_plan).  Launches of the handle's K while more than K + 8 steps
-// remain, then the cheapest split of the rest (at most K + 8 steps) into launches of at
-// most K steps: even sizes always (the two-column kernels), odd sizes above one only where
-// the one-column periodic kernel runs (BGK, every side periodic).  At K = 6 a call of 20
-// steps runs 6 + 6 + 4 + 4, one of 8 runs 4 + 4; a single step is left only where no fused
-// size fits.
+// Launch plan of a fused handle (launch_plan.h): K, and whether odd sizes above one may run
+// (the one-column periodic kernel: BGK with every side periodic).
 int plan_fused_launches(const lbm_sw* h, int n, int* plan, int max_plan) {
-  const int K = h->temporal_k;
   const bool odd_ok = !h->mrt && h->p.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC &&
                       h->p.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
-  auto allowed = [&](int k) { return k == 1 || (k <= K && (k % 2 == 0 || odd_ok)); };
-  int count = 0;
-  while (n > K + 8 && count < max_plan) {
-    plan[count++] = K;
-    n -= K;
-  }
-  // cheapest split of the remaining n <= K + 8 steps (n <= 16)
-  double best[17];
-  int first[17];
-  best[0] = 0.0;
-  first[0] = 0;
-  for (int m = 1; m <= n; ++m) {
-    best[m] = 1e300;
-    first[m] = 1;
-    for (int k = 1; k <= 8 && k <= m; ++k) {
-      if (!allowed(k)) continue;
-      const double c = kLaunchCost[k] + best[m - k];
-      if (c < best[m]) {
-        best[m] = c;
-        first[m] = k;
-      }
-    }
-  }
-  // larger launches first
-  int tail[16], nt = 0;
-  for (int m = n; m > 0; m -= first[m]) tail[nt++] = first[m];
-  std::sort(tail, tail + nt, [](int a, int b) { return a > b; });
-  for (int i = 0; i < nt && count < max_plan; ++i) plan[count++] = tail[i];
-  return count;
+  return lbm::plan_launches(h->temporal_k, odd_ok, n, plan, max_plan);
 }
+static_assert(64 > lbm::kMaxTail, "plan buffers of lbm_sw_step and lbm_sw_step_plan hold a whole tail");
 
 // One step from buffer `from` into the other buffer, on stream st (the TEMPORAL choice
 // takes single steps with the VEC kernel).

@@ -11,8 +11,9 @@ bit-identical to one step per launch).  The two 872 MB population
 buffers exceed the 129 MB L2, so every launch streams the state from HBM and back.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Prints one JSON line on rank 0.  Under torchrun each rank runs an independent
-replica on its own GPU (weak scaling); `value` is the sum over ranks.
+Prints one JSON line on rank 0.  Under torchrun (N > 1) the grid is split into N bands of
+rows, one per GPU, with ghost rows exchanged over NCCL (strong scaling; --replicas runs
+independent replicas instead); `value` is the whole grid's cell updates per second.
 """
 
 from __future__ import annotations
@@ -320,6 +321,96 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------------------- our arm
+def run_split(args, world, rank, local):
+    """N > 1: the one 4096^2 grid split into N bands of rows, one per GPU (strong scaling),
+    6 ghost rows per cut refreshed over NCCL after every fused launch of 6 steps
+    (paper_1401_0427_gb300/decomposition.py).  value = cells x steps of the whole grid over
+    the slowest rank's time."""
+    global N
+    import torch
+    import torch.distributed as dist
+
+    N = args.side
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1401_0427_gb300 import build as libbuild
+    from paper_1401_0427_gb300 import decomposition as dc
+    from paper_1401_0427_gb300 import inputs, lbm_sw
+
+    if rank == 0:
+        libbuild.build()
+    dist.barrier()
+    libbuild.build()
+    stream = torch.cuda.current_stream()
+    W0 = inputs.circular_dam_break_2d(N, seed=inputs.stream_seed(3))
+    band = dc.Band(N, N, rank, world, halo=6, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream)
+    strips = dc.DistributedStrips(band)
+    band.set_state(*W0)
+    unit = max(1, band.sim.info().steps_per_launch)
+    strips.step(max(args.warmup, 3) * unit)
+    torch.cuda.synchronize()
+    launches0 = band.sim.info().kernel_launches
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    gpu_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].strip().isdigit() else local
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    e0.record(stream)
+    strips.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.perf_counter()
+    dist.barrier()
+    time.sleep(0.2)
+    clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = band.sim.info().kernel_launches - launches0
+    value, total_ms = job_throughput(world, N * N * args.steps / world, ms)
+    diag = strips.diagnostics()
+    peak, peak_kind = measured_peaks()
+    local_cells = N * band.L.local_ny
+    achieved = BYTES_PER_LUP["f32"] * local_cells * (args.steps / unit) / (ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_kind": f"{peak_kind} (copy bandwidth)", "per": "rank (its band with ghost rows)",
+                "kernel": temporal_kernel_name(unit, local_cells), "steps_per_launch": unit}
+    # whole jobs through the public API: upload W0, JOB_STEPS steps, download h, hu, hv
+    pinned = [torch.empty((band.L.local_ny, N), dtype=torch.float64, pin_memory=True) for _ in range(3)]
+    rows = band.local_rows()
+    for t, w in zip(pinned, W0):
+        t.numpy()[...] = w[rows]
+    out = [torch.empty((band.L.local_ny, N), dtype=torch.float64, pin_memory=True) for _ in range(3)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    jobs = 2
+    for _ in range(jobs):
+        band.sim.set_state(*[p.numpy() for p in pinned])
+        strips.step(JOB_STEPS)
+        band.sim.moments_into(*[o.numpy() for o in out])
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t) * 1e3
+    e2e_value, _ = job_throughput(world, N * N * JOB_STEPS * jobs / world, e2e_ms)
+    band.sim.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": N, "ny": N, "cells": N * N, "precision": "FP32 populations",
+                       "l2": "inputs larger than L2 (each band's two population buffers exceed the 129 MB L2)",
+                       "parallelism": f"{world} bands of rows, 6 ghost rows per cut, NCCL exchange every 6 steps"},
+            "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks.summary(t_wall0, t_wall1),
+            "conservation": {"sum_h": diag[0], "min_h": diag[3]},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * N * N * 8,
+                    "d2h_bytes_per_step": 3 * N * N * 8, "step": f"one job: upload W0, {JOB_STEPS} steps, download W"},
+        }))
+    dist.destroy_process_group()
+
+
 def run_ours(args, world, rank, local):
     global N
     import torch
@@ -407,7 +498,8 @@ def run_ours(args, world, rank, local):
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-              "scaling": "weak", "vs_baseline": None, "dtype": dt_name, "data": "synthetic",
+              "scaling": "weak" if world > 1 else "strong", "vs_baseline": None, "dtype": dt_name,
+              "data": "synthetic",
               "config": {"workload": WORKLOAD if N == 4096 else WORKLOAD.replace("4096x4096", f"{N}x{N}"),
                          "nx": N, "ny": N, "cells": cells, "precision": f"{args.precision.upper()} populations",
                          "l2": "inputs larger than L2 (two 872 MB population buffers, 129 MB L2)",
@@ -799,6 +891,8 @@ def main():
                     default="step",
                     help="kernel to run for profiling (only 'step' prints the benchmark line; basin: the "
                          "dam-break with walls on every side; mrt: the dam-break with the MRT collision)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with N > 1 GPUs, run N independent replicas of the grid instead of splitting it")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
                     help="population precision of the timed loop (fp32 is the workload)")
     args = ap.parse_args()
@@ -809,6 +903,8 @@ def main():
         run_reference(args, world, rank)
     elif args.case != "step":
         profile_case(args, local)
+    elif world > 1 and not args.replicas:
+        run_split(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

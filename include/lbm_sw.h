@@ -248,6 +248,24 @@ LBM_SW_API int lbm_sw_get_populations(lbm_sw* h, void* dst, int on_device);
  * paper corresponds to loading raw populations. */
 LBM_SW_API int lbm_sw_set_populations(lbm_sw* h, const void* src, int on_device, int form);
 
+/* ---- Rows of a 2D state: domain decomposition across GPUs ----
+ * One grid split into bands of rows, one band per GPU: each band's handle holds its rows
+ * plus H ghost rows on every side that borders another band.  Streaming moves every
+ * population one cell per step (section 3, Eq. 3-stencil-d2q5), so k <= H steps change
+ * the ghost rows' influence only k rows deep: after k steps the band's own rows are exact,
+ * and copying the neighbours' outermost H rows into the ghost rows restores the state
+ * (paper_1401_0427_gb300/decomposition.py drives this over torch.distributed).
+ *
+ * lbm_sw_get_rows / lbm_sw_set_rows copy rows [y0, y0 + nrows) of every population plane
+ * of the stored state out to / in from dense planes [q][nrows][nx] of the handle's
+ * precision (on_device as elsewhere; host copies synchronise).  lbm_sw_diagnostics_rows
+ * is lbm_sw_diagnostics over rows [y0, y0 + nrows) only (the band without its ghost rows).
+ * Errors: LBM_SW_E_ARG (1D handle for the copies, rows outside [0, ny), NULL pointers),
+ * LBM_SW_E_STATE (no state set), LBM_SW_E_CUDA; LBM_SW_E_UNSTABLE as lbm_sw_diagnostics. */
+LBM_SW_API int lbm_sw_get_rows(lbm_sw* h, int y0, int nrows, void* dst, int on_device);
+LBM_SW_API int lbm_sw_set_rows(lbm_sw* h, int y0, int nrows, const void* src, int on_device);
+LBM_SW_API int lbm_sw_diagnostics_rows(lbm_sw* h, int y0, int nrows, double out[4]);
+
 /* ---- Batched instances ----
  * Many independent D2Q5Q4Q4 grids of uneven sizes (e.g. an ensemble of dam-breaks), all with
  * the same scheme parameters and boundary kinds, advanced together: one kernel launch per

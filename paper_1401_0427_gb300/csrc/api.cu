@@ -519,6 +519,74 @@ int lbm_sw_set_populations(lbm_sw* h, const void* src, int on_device, int form) 
   return LBM_SW_OK;
 }
 
+int lbm_sw_get_rows(lbm_sw* h, int y0, int nrows, void* dst, int on_device) {
+  if (!h) return LBM_SW_E_ARG;
+  if (!dst) return fail(h, LBM_SW_E_ARG, "get_rows: dst is NULL");
+  if (h->p.dim != 2) return fail(h, LBM_SW_E_ARG, "get_rows: rows are for 2D handles");
+  if (y0 < 0 || nrows < 0 || y0 > h->p.ny - nrows)
+    return fail(h, LBM_SW_E_ARG, "get_rows: rows [%d, %d) outside [0, %d)", y0, y0 + nrows, h->p.ny);
+  if (!h->has_state) return fail(h, LBM_SW_E_STATE, "get_rows: no state set");
+  if (nrows == 0) return LBM_SW_OK;
+  const size_t row = static_cast<size_t>(h->p.nx) * h->elem;
+  const size_t dplane = row * nrows;
+  const char* src = static_cast<const char*>(h->buf[h->cur]) + static_cast<size_t>(y0) * h->pitch * h->elem;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int p = 0; p < h->q; ++p)
+    LBM_CUDA(h, cudaMemcpy2DAsync(static_cast<char*>(dst) + p * dplane, row, src + p * h->plane * h->elem,
+                                  h->pitch * h->elem, row, nrows, kind, h->stream),
+             "copy rows out");
+  if (!on_device) LBM_CUDA(h, cudaStreamSynchronize(h->stream), "get_rows synchronize");
+  return LBM_SW_OK;
+}
+
+int lbm_sw_set_rows(lbm_sw* h, int y0, int nrows, const void* src, int on_device) {
+  if (!h) return LBM_SW_E_ARG;
+  if (!src) return fail(h, LBM_SW_E_ARG, "set_rows: src is NULL");
+  if (h->p.dim != 2) return fail(h, LBM_SW_E_ARG, "set_rows: rows are for 2D handles");
+  if (y0 < 0 || nrows < 0 || y0 > h->p.ny - nrows)
+    return fail(h, LBM_SW_E_ARG, "set_rows: rows [%d, %d) outside [0, %d)", y0, y0 + nrows, h->p.ny);
+  if (!h->has_state) return fail(h, LBM_SW_E_STATE, "set_rows: no state set");
+  if (nrows == 0) return LBM_SW_OK;
+  const size_t row = static_cast<size_t>(h->p.nx) * h->elem;
+  const size_t dplane = row * nrows;
+  char* dst = static_cast<char*>(h->buf[h->cur]) + static_cast<size_t>(y0) * h->pitch * h->elem;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (int p = 0; p < h->q; ++p)
+    LBM_CUDA(h, cudaMemcpy2DAsync(dst + p * h->plane * h->elem, h->pitch * h->elem,
+                                  static_cast<const char*>(src) + p * dplane, row, row, nrows, kind, h->stream),
+             "copy rows in");
+  if (!on_device) LBM_CUDA(h, cudaStreamSynchronize(h->stream), "set_rows synchronize");
+  return LBM_SW_OK;
+}
+
+int lbm_sw_diagnostics_rows(lbm_sw* h, int y0, int nrows, double out[4]) {
+  if (!h || !out) return h ? fail(h, LBM_SW_E_ARG, "diagnostics_rows: out is NULL") : LBM_SW_E_ARG;
+  if (y0 < 0 || nrows < 1 || y0 > h->p.ny - nrows)
+    return fail(h, LBM_SW_E_ARG, "diagnostics_rows: rows [%d, %d) outside [0, %d)", y0, y0 + nrows, h->p.ny);
+  if (!h->has_state) return fail(h, LBM_SW_E_STATE, "diagnostics_rows: no state set");
+  cudaError_t e;
+  if (h->p.precision == LBM_SW_FP64) {
+    auto a = args<double>(h, h->cur);
+    a.src += static_cast<long long>(y0) * h->pitch;
+    a.ny = nrows;
+    e = lbm::launch_diagnostics<double>(a, h->q, h->diag_partials, h->diag_out, h->stream);
+  } else {
+    auto a = args<float>(h, h->cur);
+    a.src += static_cast<long long>(y0) * h->pitch;
+    a.ny = nrows;
+    e = lbm::launch_diagnostics<float>(a, h->q, h->diag_partials, h->diag_out, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics kernel launch");
+  h->launches += 2;
+  LBM_CUDA(h, cudaMemcpyAsync(h->diag_host, h->diag_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+           "copy diagnostics");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "diagnostics synchronize");
+  for (int k = 0; k < 4; ++k) out[k] = h->diag_host[k];
+  if (h->diag_host[4] > 0)
+    return fail(h, LBM_SW_E_UNSTABLE, "diagnostics: %.0f cells with NaN/Inf or depth <= 0", h->diag_host[4]);
+  return LBM_SW_OK;
+}
+
 int lbm_sw_set_relaxation(lbm_sw* h, const double* rates, int count) {
   if (!h) return LBM_SW_E_ARG;
   if (!rates) {

@@ -128,6 +128,9 @@ SIGNATURES = {
     "lbm_sw_diagnostics": (ctypes.c_int, [_H, _DP]),
     "lbm_sw_get_populations": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
     "lbm_sw_set_populations": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "lbm_sw_get_rows": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+    "lbm_sw_set_rows": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+    "lbm_sw_diagnostics_rows": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, _DP]),
     "lbm_sw_synchronize": (ctypes.c_int, [_H]),
     "lbm_sw_get_info": (ctypes.c_int, [_H, ctypes.POINTER(lbm_sw_info)]),
     "lbm_sw_last_error": (ctypes.c_char_p, [_H]),
@@ -261,6 +264,23 @@ def lbm_sw_get_populations(h: int, dst: int, on_device: bool) -> None:
 
 def lbm_sw_set_populations(h: int, src: int, on_device: bool, form: int) -> None:
     _check(load().lbm_sw_set_populations(h, src, int(on_device), int(form)), h, "lbm_sw_set_populations")
+
+
+def lbm_sw_get_rows(h: int, y0: int, nrows: int, dst: int, on_device: bool) -> None:
+    _check(load().lbm_sw_get_rows(h, int(y0), int(nrows), dst, int(on_device)), h, "lbm_sw_get_rows")
+
+
+def lbm_sw_set_rows(h: int, y0: int, nrows: int, src: int, on_device: bool) -> None:
+    _check(load().lbm_sw_set_rows(h, int(y0), int(nrows), src, int(on_device)), h, "lbm_sw_set_rows")
+
+
+def lbm_sw_diagnostics_rows(h: int, y0: int, nrows: int, raise_unstable: bool = True):
+    """Returns (sum h, sum hu, sum hv, min h, status) over rows [y0, y0 + nrows)."""
+    out = (ctypes.c_double * 4)()
+    st = load().lbm_sw_diagnostics_rows(h, int(y0), int(nrows), out)
+    if st != E_UNSTABLE or raise_unstable:
+        _check(st, h, "lbm_sw_diagnostics_rows")
+    return out[0], out[1], out[2], out[3], st
 
 
 def lbm_sw_synchronize(h: int) -> None:
@@ -535,6 +555,23 @@ class Simulation:
 
     def diagnostics(self, raise_unstable: bool = True):
         return lbm_sw_diagnostics(self.handle, raise_unstable)
+
+    def diagnostics_rows(self, y0: int, nrows: int, raise_unstable: bool = True):
+        return lbm_sw_diagnostics_rows(self.handle, y0, nrows, raise_unstable)
+
+    def get_rows_into(self, y0: int, nrows: int, out):
+        """Rows [y0, y0 + nrows) of every plane into ``out`` ([q][nrows][nx], numpy or CUDA tensor)."""
+        dev = self._on_device(out)
+        lbm_sw_get_rows(self.handle, y0, nrows, _ptr(out, dev, np.dtype(self.dtype).name, self.q * nrows * self.nx,
+                                                     "rows"), dev)
+
+    def set_rows(self, y0: int, nrows: int, src):
+        """Rows [y0, y0 + nrows) of every plane from ``src`` ([q][nrows][nx])."""
+        dev = self._on_device(src)
+        if not dev:
+            src = np.ascontiguousarray(src, dtype=self.dtype)
+        lbm_sw_set_rows(self.handle, y0, nrows, _ptr(src, dev, np.dtype(self.dtype).name, self.q * nrows * self.nx,
+                                                     "rows"), dev)
 
     def synchronize(self):
         lbm_sw_synchronize(self.handle)

@@ -144,6 +144,9 @@ def test_null_arguments(lib):
     assert lib.lbm_sw_synchronize(None) == lbm_sw.E_ARG
     assert lib.lbm_sw_get_info(None, None) == lbm_sw.E_ARG
     assert lib.lbm_sw_step_plan(None, 4, None, 0) == lbm_sw.E_ARG
+    assert lib.lbm_sw_get_rows(None, 0, 1, None, 0) == lbm_sw.E_ARG
+    assert lib.lbm_sw_set_rows(None, 0, 1, None, 0) == lbm_sw.E_ARG
+    assert lib.lbm_sw_diagnostics_rows(None, 0, 1, None) == lbm_sw.E_ARG
     lib.lbm_sw_destroy(None)  # NULL-safe
     for code in (0, -1, -2, -3, -4, -5, -6, -99):
         assert lib.lbm_sw_status_string(code)

@@ -63,7 +63,18 @@ struct Consts {
   //   2D: J_x, J_y, eps, XX_rho | f_xx, f_xy, XX_u | f_yx, f_yy, XX_v   (r[0..9])
   //   1D: J_rho, eps_rho, J_q                                            (r[0..2])
   T r[10];
+  // 2D: the same rates with the exact power-of-two factors of the moment transforms folded
+  // in (collide13_mrt): J_x / 2, J_y / 2, eps, XX_rho | f_xx / 2, f_xy / 2, XX_u / 4 | f_yx / 2,
+  // f_yy / 2, XX_v / 4.  Scaling by a power of two commutes with rounding, so each product
+  // is exactly half (a quarter) of the unscaled one and the halvings that follow it vanish.
+  T m[10];
 };
+
+template <class T>
+__host__ void set_mrt_folded(Consts<T>& k) {
+  constexpr double scale[10] = {0.5, 0.5, 1.0, 1.0, 0.5, 0.5, 0.25, 0.5, 0.5, 0.25};
+  for (int i = 0; i < 10; ++i) k.m[i] = static_cast<T>(static_cast<double>(k.r[i]) * scale[i]);
+}
 
 template <class T>
 __host__ Consts<T> make_consts(double g, double lambda, double s, double a) {
@@ -75,6 +86,7 @@ __host__ Consts<T> make_consts(double g, double lambda, double s, double a) {
   k.inv4g = static_cast<T>(1.0 / (4.0 * g));
   k.nz = static_cast<T>(-0.0);
   for (int i = 0; i < 10; ++i) k.r[i] = k.s;
+  set_mrt_folded(k);
   return k;
 }
 
@@ -83,6 +95,7 @@ template <class T>
 __host__ Consts<T> make_consts_mrt(double g, double lambda, double s, double a, const double* rates, int n) {
   Consts<T> k = make_consts<T>(g, lambda, s, a);
   for (int i = 0; i < n && i < 10; ++i) k.r[i] = static_cast<T>(rates[i]);
+  set_mrt_folded(k);
   return k;
 }
 
@@ -152,15 +165,18 @@ __device__ __forceinline__ void collide13(T f[13], const Consts<T>& k) {
 //       s24 = (deps/5 - dXX)/2, df1,3 = (s13 +- dJx/lam)/2, df2,4 = (s24 +- dJy/lam)/2;
 //   gx: dfxx/lam = r4 (g1 - g3), dfxy/lam = r5 (g2 - g4), dXX_u = r6 (g1 - g2 + g3 - g4);
 //       back: dg1,3 = (dXX_u/2 +- dfxx/lam)/2, dg2,4 = (-dXX_u/2 +- dfxy/lam)/2;  gy alike (r7..r9).
+// The halvings are folded into the rates (Consts::m) and into the quarter that forms s13/2
+// and s24/2, which gives the same rounded values with 14 operations fewer per cell; the
+// last correction of each momentum family is subtracted instead of negated and added.
 template <class T>
-__device__ __forceinline__ void mrt_family4(const T d[4], T ra, T rb, T rx, T g[4]) {
-  const T a = mul(ra, sub(d[0], d[2]));
-  const T b = mul(rb, sub(d[1], d[3]));
-  const T xx = mul(mul(T(0.5), rx), sub(add(d[0], d[2]), add(d[1], d[3])));
-  g[0] = mul(T(0.5), add(xx, a));
-  g[2] = mul(T(0.5), sub(xx, a));
-  g[1] = mul(T(0.5), sub(b, xx));
-  g[3] = mul(T(0.5), sub(-xx, b));
+__device__ __forceinline__ void mrt_family4(const T d[4], T ra2, T rb2, T rx4, T& g0, T& g1, T& g2, T& g3n) {
+  const T ah = mul(ra2, sub(d[0], d[2]));  // (dfxx/lam) / 2
+  const T bh = mul(rb2, sub(d[1], d[3]));  // (dfxy/lam) / 2
+  const T xh = mul(rx4, sub(add(d[0], d[2]), add(d[1], d[3])));  // dXX_u / 4
+  g0 = add(xh, ah);
+  g2 = sub(xh, ah);
+  g1 = sub(bh, xh);
+  g3n = add(xh, bh);  // -dg4
 }
 
 template <class T>
@@ -171,24 +187,27 @@ __device__ __forceinline__ void collide13_mrt(T f[13], const Consts<T>& k, T& h,
   T d[13];
 #pragma unroll
   for (int j = 0; j < 13; ++j) d[j] = sub(e[j], f[j]);
-  const T jx = mul(k.r[0], sub(d[1], d[3]));
-  const T jy = mul(k.r[1], sub(d[2], d[4]));
-  const T e5 = mul(mul(k.r[2], sub(add(add(d[1], d[2]), add(d[3], d[4])), mul(T(4), d[0]))), T(0.2));
-  const T xx = mul(k.r[3], sub(add(d[1], d[3]), add(d[2], d[4])));
-  const T s13 = mul(T(0.5), add(e5, xx)), s24 = mul(T(0.5), sub(e5, xx));
+  const T jxh = mul(k.m[0], sub(d[1], d[3]));
+  const T jyh = mul(k.m[1], sub(d[2], d[4]));
+  const T e5 = mul(mul(k.m[2], sub(add(add(d[1], d[2]), add(d[3], d[4])), mul(T(4), d[0]))), T(0.2));
+  const T xx = mul(k.m[3], sub(add(d[1], d[3]), add(d[2], d[4])));
+  const T s13q = mul(T(0.25), add(e5, xx)), s24q = mul(T(0.25), sub(e5, xx));
   f[0] = sub(f[0], e5);
-  f[1] = add(f[1], mul(T(0.5), add(s13, jx)));
-  f[3] = add(f[3], mul(T(0.5), sub(s13, jx)));
-  f[2] = add(f[2], mul(T(0.5), add(s24, jy)));
-  f[4] = add(f[4], mul(T(0.5), sub(s24, jy)));
-  T gx[4], gy[4];
-  mrt_family4(d + 5, k.r[4], k.r[5], k.r[6], gx);
-  mrt_family4(d + 9, k.r[7], k.r[8], k.r[9], gy);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    f[5 + j] = add(f[5 + j], gx[j]);
-    f[9 + j] = add(f[9 + j], gy[j]);
-  }
+  f[1] = add(f[1], add(s13q, jxh));
+  f[3] = add(f[3], sub(s13q, jxh));
+  f[2] = add(f[2], add(s24q, jyh));
+  f[4] = add(f[4], sub(s24q, jyh));
+  T g0, g1, g2, g3n;
+  mrt_family4(d + 5, k.m[4], k.m[5], k.m[6], g0, g1, g2, g3n);
+  f[5] = add(f[5], g0);
+  f[6] = add(f[6], g1);
+  f[7] = add(f[7], g2);
+  f[8] = sub(f[8], g3n);
+  mrt_family4(d + 9, k.m[7], k.m[8], k.m[9], g0, g1, g2, g3n);
+  f[9] = add(f[9], g0);
+  f[10] = add(f[10], g1);
+  f[11] = add(f[11], g2);
+  f[12] = sub(f[12], g3n);
 }
 
 // Relaxation of either form.
@@ -316,16 +335,16 @@ __device__ __forceinline__ void collide13x2(float2 f[13], const Consts<float>& k
 }
 
 // The MRT form of collide13_mrt on (cell a, cell b) pairs, operation for operation.
-__device__ __forceinline__ void mrt_family4x2(const float2 d[4], float ra, float rb, float rx, float2 nz, float2 g[4]) {
+__device__ __forceinline__ void mrt_family4x2(const float2 d[4], float ra2, float rb2, float rx4, float2 nz,
+                                              float2& g0, float2& g1, float2& g2, float2& g3n) {
   auto mul2 = [&](float2 a, float2 b) { return fma2(a, b, nz); };
-  const float2 half = dup2(0.5f);
-  const float2 a = mul2(dup2(ra), sub2(d[0], d[2]));
-  const float2 b = mul2(dup2(rb), sub2(d[1], d[3]));
-  const float2 xx = mul2(dup2(0.5f * rx), sub2(add2(d[0], d[2]), add2(d[1], d[3])));
-  g[0] = mul2(half, add2(xx, a));
-  g[2] = mul2(half, sub2(xx, a));
-  g[1] = mul2(half, sub2(b, xx));
-  g[3] = mul2(half, sub2(make_float2(-xx.x, -xx.y), b));
+  const float2 ah = mul2(dup2(ra2), sub2(d[0], d[2]));
+  const float2 bh = mul2(dup2(rb2), sub2(d[1], d[3]));
+  const float2 xh = mul2(dup2(rx4), sub2(add2(d[0], d[2]), add2(d[1], d[3])));
+  g0 = add2(xh, ah);
+  g2 = sub2(xh, ah);
+  g1 = sub2(bh, xh);
+  g3n = add2(xh, bh);
 }
 
 __device__ __forceinline__ void collide13x2_mrt(float2 f[13], const Consts<float>& k, float2& h, float2& qx,
@@ -337,26 +356,29 @@ __device__ __forceinline__ void collide13x2_mrt(float2 f[13], const Consts<float
   float2 d[13];
 #pragma unroll
   for (int j = 0; j < 13; ++j) d[j] = sub2(e[j], f[j]);
-  const float2 half = dup2(0.5f);
-  const float2 jx = mul2(dup2(k.r[0]), sub2(d[1], d[3]));
-  const float2 jy = mul2(dup2(k.r[1]), sub2(d[2], d[4]));
+  const float2 quarter = dup2(0.25f);
+  const float2 jxh = mul2(dup2(k.m[0]), sub2(d[1], d[3]));
+  const float2 jyh = mul2(dup2(k.m[1]), sub2(d[2], d[4]));
   const float2 e5 =
-      mul2(mul2(dup2(k.r[2]), sub2(add2(add2(d[1], d[2]), add2(d[3], d[4])), mul2(dup2(4.0f), d[0]))), dup2(0.2f));
-  const float2 xx = mul2(dup2(k.r[3]), sub2(add2(d[1], d[3]), add2(d[2], d[4])));
-  const float2 s13 = mul2(half, add2(e5, xx)), s24 = mul2(half, sub2(e5, xx));
+      mul2(mul2(dup2(k.m[2]), sub2(add2(add2(d[1], d[2]), add2(d[3], d[4])), mul2(dup2(4.0f), d[0]))), dup2(0.2f));
+  const float2 xx = mul2(dup2(k.m[3]), sub2(add2(d[1], d[3]), add2(d[2], d[4])));
+  const float2 s13q = mul2(quarter, add2(e5, xx)), s24q = mul2(quarter, sub2(e5, xx));
   f[0] = sub2(f[0], e5);
-  f[1] = add2(f[1], mul2(half, add2(s13, jx)));
-  f[3] = add2(f[3], mul2(half, sub2(s13, jx)));
-  f[2] = add2(f[2], mul2(half, add2(s24, jy)));
-  f[4] = add2(f[4], mul2(half, sub2(s24, jy)));
-  float2 gx[4], gy[4];
-  mrt_family4x2(d + 5, k.r[4], k.r[5], k.r[6], nz, gx);
-  mrt_family4x2(d + 9, k.r[7], k.r[8], k.r[9], nz, gy);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    f[5 + j] = add2(f[5 + j], gx[j]);
-    f[9 + j] = add2(f[9 + j], gy[j]);
-  }
+  f[1] = add2(f[1], add2(s13q, jxh));
+  f[3] = add2(f[3], sub2(s13q, jxh));
+  f[2] = add2(f[2], add2(s24q, jyh));
+  f[4] = add2(f[4], sub2(s24q, jyh));
+  float2 g0, g1, g2, g3n;
+  mrt_family4x2(d + 5, k.m[4], k.m[5], k.m[6], nz, g0, g1, g2, g3n);
+  f[5] = add2(f[5], g0);
+  f[6] = add2(f[6], g1);
+  f[7] = add2(f[7], g2);
+  f[8] = sub2(f[8], g3n);
+  mrt_family4x2(d + 9, k.m[7], k.m[8], k.m[9], nz, g0, g1, g2, g3n);
+  f[9] = add2(f[9], g0);
+  f[10] = add2(f[10], g1);
+  f[11] = add2(f[11], g2);
+  f[12] = sub2(f[12], g3n);
 }
 
 template <bool MRT>

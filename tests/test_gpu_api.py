@@ -93,6 +93,28 @@ def test_diagnostics_are_fp64_totals(precision):
     assert d[3] == m[0].min()
 
 
+@pytest.mark.parametrize("bc", [(W, W, W, W), (lbm_sw.PERIODIC,) * 4], ids=["walls", "periodic"])
+def test_diagnostics_equal_the_oracle_totals(bc):
+    """The FP64 diagnostics of the GPU state against the oracle's own moments of its own run
+    from the same initial state (not the GPU's moments): sum h, sum hu, sum hv and min h.
+    Walls and periodic sides conserve the totals; the run keeps them within rounding of the
+    initial totals on both sides."""
+    nx, ny, steps = 97, 64, 25
+    W0 = [x.reshape(ny, nx) for x in inputs.random_states(nx * ny, seed=89, h=(0.8, 1.4), speed=0.25)]
+    with lbm_sw.Simulation(nx, ny, precision=lbm_sw.FP64, bc=bc, stream=torch_stream()) as sim:
+        sim.set_state(*W0)
+        sim.step(steps)
+        d = sim.diagnostics()
+    p = oracle.params(nx, ny, a=0.05, bc=bc)
+    oh, ohu, ohv = oracle.moments_2d(oracle.run_2d(oracle.equilibrium_2d(*W0, p), steps, p), p)
+    scale = np.abs(oh).sum()
+    assert d[4] == lbm_sw.OK
+    assert abs(d[0] - oh.sum()) <= 1e-12 * scale
+    assert abs(d[1] - ohu.sum()) <= 1e-12 * scale and abs(d[2] - ohv.sum()) <= 1e-12 * scale
+    assert abs(d[3] - oh.min()) <= 1e-12 * oh.max()
+    assert abs(d[0] - W0[0].sum()) <= 1e-12 * scale  # mass conserved by both sides
+
+
 def test_diagnostics_report_unstable_states():
     nx, ny = 64, 48
     with lbm_sw.Simulation(nx, ny, precision=lbm_sw.FP32, stream=torch_stream()) as sim:

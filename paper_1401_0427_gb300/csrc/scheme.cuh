@@ -293,7 +293,8 @@ __device__ __forceinline__ void moments_equilibrium13x2(const float2 f[13], cons
   const float2 u = mul2(qx, rh);
   const float2 v = mul2(qy, rh);
   const float2 uu = add2(mul2(u, u), mul2(v, v));
-  const float2 kap = fma2(make_float2(-uu.x, -uu.y), dup2(k.inv4g), mul2(dup2(0.5f), h));
+  // the sign on the constant instead of on uu: the same exact product, no negation per pair
+  const float2 kap = fma2(uu, dup2(-k.inv4g), mul2(dup2(0.5f), h));
   const float2 f0 = mul2(dup2(k.a), kap);
   const float2 r = mul2(sub2(h, f0), dup2(0.25f));
   const float2 p = mul2(mul2(dup2(k.half_g), h), h);

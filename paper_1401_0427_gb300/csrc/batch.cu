@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "launch_plan.h"
 #include "scheme.cuh"
 #include "step2d_vec.cuh"
 
@@ -466,17 +467,33 @@ int lbm_sw_batch_step(lbm_sw_batch* b, int n) {
   if (n < 0) return bfail(b, LBM_SW_E_ARG, "step: n must be >= 0 (got %d)", n);
   if (b->states_set != b->p.count)
     return bfail(b, LBM_SW_E_STATE, "step: %d of %d instances have no state", b->p.count - b->states_set, b->p.count);
-  if (b->temporal_k >= 2 && n >= b->temporal_k) {
-    int rc = ensure_waves(b, b->temporal_k);
-    if (rc) return rc;
+  if (b->temporal_k >= 2) {
+    // as lbm_sw_step: launches of K, the tail split into shorter fused launches (each with
+    // its own work list, built on first use), odd sizes only where every side is periodic
+    bool per = true;
+    for (int s = 0; s < 4; ++s) per = per && b->p.bc[s] == LBM_SW_BC_PERIODIC;
+    int plan[64];
+    while (n > 0) {
+      const int count = lbm::plan_launches(b->temporal_k, per, n, plan, 64);
+      for (int i = 0; i < count; ++i) {
+        const int k = plan[i];
+        cudaError_t e;
+        if (k == 1) {
+          e = launch_batch(b, b->cur, b->tile_rows, b->ctas_per_sm, b->stream);
+        } else {
+          const int rc = ensure_waves(b, k);
+          if (rc) return rc;
+          e = launch_temporal(b, b->cur, k, b->stream);
+        }
+        if (e != cudaSuccess) return bcuda(b, e, k == 1 ? "batch step launch" : "batch temporal launch");
+        b->cur ^= 1;
+        n -= k;
+      }
+    }
+    return LBM_SW_OK;
   }
   while (n > 0) {
-    if (b->temporal_k >= 2 && n >= b->temporal_k) {
-      cudaError_t e = launch_temporal(b, b->cur, b->temporal_k, b->stream);
-      if (e != cudaSuccess) return bcuda(b, e, "batch temporal launch");
-      b->cur ^= 1;
-      n -= b->temporal_k;
-    } else if (b->graph_chunk > 0 && n >= b->graph_chunk) {
+    if (b->graph_chunk > 0 && n >= b->graph_chunk) {
       if (!b->graph[b->cur]) {
         int rc = build_graph(b, b->cur);
         if (rc) return rc;

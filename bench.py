@@ -583,6 +583,7 @@ def variants(args, W0, stream, lbm_sw, torch):
     out["fp32_temporal_k"] = temporal_sweep(W0, stream, lbm_sw, torch)
     out["fp32_closed_basin"] = bounded_variant(W0, stream, lbm_sw, torch)
     out["fp32_mrt"] = mrt_variant(W0, stream, lbm_sw, torch)
+    out["fp32_obstacles"] = obstacle_variant(W0, stream, lbm_sw, torch)
     out["batched_256"] = batched_variant(stream, lbm_sw, torch)
     out["shock_reflection_512"] = shock_reflection_variant(stream, lbm_sw, torch)
     out["shock_tube_1d_1000"] = shock_tube_variant(stream, lbm_sw, torch)
@@ -651,6 +652,27 @@ def mrt_variant(W0, stream, lbm_sw, torch, steps: int = 240):
             spl = max(1, sim.info().steps_per_launch)
             t = _timed(stream, torch, lambda: sim.step(steps))
         out[kname] = {"MLUPS": N * N * steps / t / 1e6, "steps_per_launch": spl}
+    return out
+
+
+def obstacle_variant(W0, stream, lbm_sw, torch, steps: int = 120):
+    """The same periodic dam-break with 64 square obstacles (32 x 32 cells each, 0.39 % of the
+    grid): the vectorised obstacle kernel (the library's choice) against one thread per cell
+    (SIMPLE), one step per launch both."""
+    solid = np.zeros((N, N), dtype=np.uint8)
+    for i in range(8):
+        for j in range(8):
+            y, x = 256 + 512 * i - 16, 256 + 512 * j - 16
+            solid[y:y + 32, x:x + 32] = 1
+    out = {"solid_fraction": float(solid.mean())}
+    for kname, kernel in (("auto", lbm_sw.KERNEL_AUTO), ("one_thread_per_cell", lbm_sw.KERNEL_SIMPLE)):
+        with lbm_sw.Simulation(N, N, precision=lbm_sw.FP32, lam=LAM, s=S_RATE, a=A_REST, stream=stream.cuda_stream,
+                               kernel=kernel) as sim:
+            sim.set_obstacle(solid)
+            sim.set_state(*W0)
+            sim.step(4)
+            t = _timed(stream, torch, lambda: sim.step(steps))
+        out[kname] = {"MLUPS": N * N * steps / t / 1e6}
     return out
 
 
@@ -760,7 +782,7 @@ def shock_tube_variant(stream, lbm_sw, torch, steps: int = 500):
     return {"MLUPS": n * steps / t / 1e6, "ms_per_run": t * 1e3, "steps": steps}
 
 
-def end_to_end(W0, stream, lbm_sw, torch, jobs: int = 3):
+def end_to_end(W0, stream, lbm_sw, torch, jobs: int = 4):
     """Whole jobs through the public API with pinned host buffers: upload W0
     (lbm_sw_set_state from host), 1000 steps, download (h, hu, hv) (lbm_sw_get_moments
     to host).  One e2e step = one job."""
@@ -776,10 +798,13 @@ def end_to_end(W0, stream, lbm_sw, torch, jobs: int = 3):
     sim.moments_into(*dst)
     torch.cuda.synchronize()
     t = time.perf_counter()
+    per_job = []
     for _ in range(jobs):
+        tj = time.perf_counter()
         sim.set_state(*src)
         sim.step(JOB_STEPS)
-        sim.moments_into(*dst)
+        sim.moments_into(*dst)  # host arrays: returns once the moments are in host memory
+        per_job.append((time.perf_counter() - tj) * 1e3)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t
     # one more job, untimed above, with a synchronize after each phase: where a job's time goes
@@ -794,7 +819,8 @@ def end_to_end(W0, stream, lbm_sw, torch, jobs: int = 3):
     nbytes = 3 * N * N * 8
     return {"value": N * N * JOB_STEPS * jobs / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
             "d2h_bytes_per_step": nbytes, "step": f"one job: upload W0, {JOB_STEPS} steps, download W",
-            "lb_steps_per_step": JOB_STEPS, "jobs": jobs, "seconds": dt, "phases_of_one_more_job": phases}
+            "lb_steps_per_step": JOB_STEPS, "jobs": jobs, "seconds": dt, "per_job_ms": per_job,
+            "phases_of_one_more_job": phases}
 
 
 def profile_case(args, local):

@@ -215,8 +215,10 @@ LBM_SW_API int lbm_sw_set_relaxation(lbm_sw* h, const double* rates, int count);
  * population, the momentum family normal to the face negated.  Solid cells hold no fluid:
  * they are not collided or streamed and keep the populations they hold (also through
  * lbm_sw_set_populations(PRE_COLLISION)); their moments still count in the diagnostics.
- * With obstacles every step runs the one-thread-per-cell obstacle kernel, whatever the
- * params' kernel.  solid == NULL removes the obstacles.  The adjoint does not support them.
+ * With obstacles every step runs an obstacle kernel, one step per launch: the vectorised row
+ * kernel (warps with no solid cell near them take the plain path), or one thread per cell
+ * when the params' kernel is SIMPLE; both give the same bits.  solid == NULL removes the
+ * obstacles.  The adjoint does not support them.
  * Errors: LBM_SW_E_ARG (1D handle), LBM_SW_E_NOMEM, LBM_SW_E_CUDA. */
 LBM_SW_API int lbm_sw_set_obstacle(lbm_sw* h, const unsigned char* solid, int on_device);
 

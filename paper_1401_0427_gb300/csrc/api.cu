@@ -79,8 +79,9 @@ static_assert(64 > lbm::kMaxTail, "plan buffers of lbm_sw_step and lbm_sw_step_p
 cudaError_t launch_one_step(lbm_sw* h, int from, cudaStream_t st) {
   const int variant = h->kernel == LBM_SW_KERNEL_TEMPORAL ? LBM_SW_KERNEL_VEC : h->kernel;
   if (h->has_obstacles)
-    return h->p.precision == LBM_SW_FP64 ? lbm::launch_step2d_obstacle<double>(args<double>(h, from), consts(h), h->solid, st)
-                                         : lbm::launch_step2d_obstacle<float>(args<float>(h, from), consts(h), h->solid, st);
+    return h->p.precision == LBM_SW_FP64
+               ? lbm::launch_step2d_obstacle<double>(args<double>(h, from), consts(h), h->solid, variant, st)
+               : lbm::launch_step2d_obstacle<float>(args<float>(h, from), consts(h), h->solid, variant, st);
   if (h->p.precision == LBM_SW_FP64) {
     auto a = args<double>(h, from);
     return h->p.dim == 1 ? lbm::launch_step1d<double>(a, consts(h), st)

@@ -40,9 +40,10 @@ cudaError_t launch_init2d(const StepArgs<T>& a, const ConstsD& k, const double* 
 template <class T>
 cudaError_t launch_collide2d_dense(const StepArgs<T>& a, const ConstsD& k, const T* dense,
                                   const unsigned char* solid, cudaStream_t st);
-// one step with obstacles (solid: [ny][nx] device mask, nonzero = solid)
+// one step with obstacles (solid: [ny][nx] device mask, nonzero = solid); variant SIMPLE:
+// one thread per cell, otherwise the vectorised row kernel
 template <class T>
-cudaError_t launch_step2d_obstacle(const StepArgs<T>& a, const ConstsD& k, const unsigned char* solid,
+cudaError_t launch_step2d_obstacle(const StepArgs<T>& a, const ConstsD& k, const unsigned char* solid, int variant,
                                    cudaStream_t st);
 template <class T>
 cudaError_t launch_moments2d(const StepArgs<T>& a, double* h, double* hu, double* hv, cudaStream_t st);

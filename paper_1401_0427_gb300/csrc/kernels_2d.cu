@@ -157,6 +157,17 @@ __global__ void __launch_bounds__(32 * BY) step2d_vec(const StepArgs<T> A, const
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// The same step with solid cells inside the domain (mirror walls on their faces; OBST in
+// vec_row), launched like step2d_vec.
+template <class T, int BY, bool MRT>
+__global__ void __launch_bounds__(32 * BY)
+    step2d_vec_obstacle(const StepArgs<T> A, const Consts<T> K, const unsigned char* __restrict__ solid) {
+  constexpr int V = V16<T>::n;
+  const int x0 = (blockIdx.x * 32 + threadIdx.x) * V;
+  for (int y = blockIdx.y * BY + threadIdx.y; y < A.ny; y += gridDim.y * BY)  // warp-uniform
+    vec_row<T, false, MRT, true>(A, K, y, x0, threadIdx.x, nullptr, solid);
+}
+
 // The same step, also writing the moments (h, hu, hv) of the new state to three planes
 // (used by the replay of the discrete adjoint).
 template <class T, int BY>
@@ -308,14 +319,25 @@ cudaError_t launch_step2d(const StepArgs<T>& a, const ConstsD& kd, int variant, 
 }
 
 template <class T>
-cudaError_t launch_step2d_obstacle(const StepArgs<T>& a, const ConstsD& kd, const unsigned char* solid,
+cudaError_t launch_step2d_obstacle(const StepArgs<T>& a, const ConstsD& kd, const unsigned char* solid, int variant,
                                    cudaStream_t st) {
   const Consts<T> K = to_consts<T>(kd);
-  const dim3 block(32, 8);
+  if (variant == LBM_SW_KERNEL_SIMPLE) {  // one thread per cell
+    const dim3 block(32, 8);
+    if (kd.mrt)
+      step2d_obstacle<T, true><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, K, solid);
+    else
+      step2d_obstacle<T, false><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, K, solid);
+    return cudaGetLastError();
+  }
+  constexpr int BY = 4;
+  constexpr int V = V16<T>::n;
+  const dim3 block(32, BY);
+  const dim3 grid((a.nx + 32 * V - 1) / (32 * V), static_cast<unsigned>(std::min<long long>((a.ny + BY - 1) / BY, 65535)));
   if (kd.mrt)
-    step2d_obstacle<T, true><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, K, solid);
+    step2d_vec_obstacle<T, BY, true><<<grid, block, 0, st>>>(a, K, solid);
   else
-    step2d_obstacle<T, false><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, K, solid);
+    step2d_vec_obstacle<T, BY, false><<<grid, block, 0, st>>>(a, K, solid);
   return cudaGetLastError();
 }
 
@@ -394,7 +416,7 @@ cudaError_t launch_inflow_feq2d(T* out, const int bc[4], const double inflow[4][
                                         const double*, cudaStream_t);                                      \
   template cudaError_t launch_collide2d_dense<T>(const StepArgs<T>&, const ConstsD&, const T*,              \
                                                 const unsigned char*, cudaStream_t);                        \
-  template cudaError_t launch_step2d_obstacle<T>(const StepArgs<T>&, const ConstsD&, const unsigned char*, \
+  template cudaError_t launch_step2d_obstacle<T>(const StepArgs<T>&, const ConstsD&, const unsigned char*, int, \
                                                  cudaStream_t);                                             \
   template cudaError_t launch_moments2d<T>(const StepArgs<T>&, double*, double*, double*, cudaStream_t);   \
   template cudaError_t launch_inflow_feq2d<T>(T*, const int[4], const double[4][3], const ConstsD&, cudaStream_t); \

@@ -61,9 +61,18 @@ __device__ __forceinline__ T pick(const T (&a)[V], int i) {
 // One row segment: cells x0 .. x0 + V - 1 of row y (x0 >= nx: the lane only takes part
 // in the shuffles).  With STORE_W the moments (h, hu, hv) of the new state are also
 // written to w_out (three planes with the population pitch).
-template <class T, bool STORE_W, bool MRT = false>
+//
+// OBST: solid cells (solid[ny][nx], nonzero = solid) inside the domain.  A population that
+// would be pulled from a solid cell takes the value of the fluid cell's own reflected
+// population, the family normal to the face negated (the WALL rule on the face); solid
+// cells keep their populations and are not collided.  A warp whose cells and their four
+// neighbours are all fluid runs the plain path; the others also load their own +y and -y
+// movers (the values the mirror rule and the solid cells need).  The same operations on
+// the same values as the one-thread-per-cell obstacle kernel, so the same bits.
+template <class T, bool STORE_W, bool MRT = false, bool OBST = false>
 __device__ __forceinline__ void vec_row(const StepArgs<T>& A, const Consts<T>& K, int y, int x0, int lane,
-                                        T* __restrict__ w_out) {
+                                        T* __restrict__ w_out, const unsigned char* __restrict__ solid = nullptr) {
+  static_assert(!(STORE_W && OBST), "obstacles are not stored with moments");
   using VV = V16<T>;
   constexpr int V = VV::n;
   const int nx = A.nx, ny = A.ny;
@@ -203,6 +212,75 @@ __device__ __forceinline__ void vec_row(const StepArgs<T>& A, const Consts<T>& K
         for (int c = 0; c < 3; ++c) R[c][k] = rv[c];
   }
 
+  // OBST: solid flags (bit k for cell x0 + k) of this segment and of rows y -+ 1, and of the
+  // cells left of x0 and right of x0 + V - 1 (periodic sides wrap; beyond other sides the
+  // domain rule already applies)
+  unsigned ms = 0, mu = 0, md = 0, lb = 0, rb = 0, rlast = 0;
+  bool obst = false;
+  T o2[3][V], o4[3][V];  // own +y and -y movers (OBST warps that meet a solid cell)
+  if constexpr (OBST) {
+    const long long mrow = static_cast<long long>(y) * nx;
+    auto bits = [&](long long r) {
+      unsigned b = 0;
+#pragma unroll
+      for (int k = 0; k < V; ++k)
+        if (x0 + k < nx && solid[r + x0 + k]) b |= 1u << k;
+      return b;
+    };
+    const bool has_up = y > 0 || A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
+    const bool has_dn = y < ny - 1 || A.bc[LBM_SW_SIDE_YP] == LBM_SW_BC_PERIODIC;
+    if (active) {
+      ms = bits(mrow);
+      if (has_up) mu = bits(static_cast<long long>(y > 0 ? y - 1 : ny - 1) * nx);
+      if (has_dn) md = bits(static_cast<long long>(y < ny - 1 ? y + 1 : 0) * nx);
+    }
+    lb = __shfl_up_sync(kFullMask, (ms >> (V - 1)) & 1u, 1);  // cell x0 - 1
+    rb = __shfl_down_sync(kFullMask, ms & 1u, 1);             // cell x0 + V
+    if (lane == 0) lb = (active && x0 > 0) ? (solid[mrow + x0 - 1] != 0) : 0u;
+    if (lane == 31) rb = (x0 + V < nx) ? (solid[mrow + x0 + V] != 0) : 0u;
+    if (x0 == 0) lb = A.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC ? (solid[mrow + nx - 1] != 0) : 0u;
+    if (kk >= 0 && kk < V) rlast = A.bc[LBM_SW_SIDE_XP] == LBM_SW_BC_PERIODIC ? (solid[mrow] != 0) : 0u;
+    obst = __any_sync(kFullMask, (ms | mu | md | lb | rb | rlast) != 0u);
+    if (obst) {
+#pragma unroll
+      for (int k = 0; k < V; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o2[c][k] = o4[c][k] = T(0);
+      if (active)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          VV::load(S + (2 + 4 * c) * P + row + x0, o2[c]);
+          VV::load(S + (4 + 4 * c) * P + row + x0, o4[c]);
+        }
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        if ((ms >> k) & 1u) continue;  // a solid cell keeps its populations (below)
+        const unsigned sl = k == 0 ? lb : (ms >> (k - 1)) & 1u;
+        const unsigned sr = k == kk ? rlast : (k == V - 1 ? rb : (ms >> (k + 1)) & 1u);
+        if (sl) {  // +x movers from a solid cell: own -x movers, hu family negated
+          L[0][k] = xm[0][k];
+          L[1][k] = -xm[1][k];
+          L[2][k] = xm[2][k];
+        }
+        if (sr) {  // -x movers: own +x movers
+          R[0][k] = xp[0][k];
+          R[1][k] = -xp[1][k];
+          R[2][k] = xp[2][k];
+        }
+        if ((mu >> k) & 1u) {  // +y movers: own -y movers, hv family negated
+          yp[0][k] = o4[0][k];
+          yp[1][k] = o4[1][k];
+          yp[2][k] = -o4[2][k];
+        }
+        if ((md >> k) & 1u) {  // -y movers: own +y movers
+          ym[0][k] = o2[0][k];
+          ym[1][k] = o2[1][k];
+          ym[2][k] = -o2[2][k];
+        }
+      }
+    }
+  }
+
   T out[13][V];
   T wo[3][V];
 #pragma unroll
@@ -210,7 +288,14 @@ __device__ __forceinline__ void vec_row(const StepArgs<T>& A, const Consts<T>& K
     T f[13] = {c0[k],    L[0][k], yp[0][k], R[0][k], ym[0][k], L[1][k], yp[1][k],
                R[1][k], ym[1][k], L[2][k], yp[2][k], R[2][k], ym[2][k]};
     T wh, wx, wy;
-    collide13_any<T, MRT>(f, K, wh, wx, wy);
+    if (OBST && obst && ((ms >> k) & 1u)) {
+      const T own[13] = {c0[k],    xp[0][k], o2[0][k], xm[0][k], o4[0][k], xp[1][k], o2[1][k],
+                         xm[1][k], o4[1][k], xp[2][k], o2[2][k], xm[2][k], o4[2][k]};
+#pragma unroll
+      for (int p = 0; p < 13; ++p) f[p] = own[p];
+    } else {
+      collide13_any<T, MRT>(f, K, wh, wx, wy);
+    }
     const bool valid = x0 + k < nx;  // padding cells are stored as zero
 #pragma unroll
     for (int p = 0; p < 13; ++p) out[p][k] = valid ? f[p] : T(0);

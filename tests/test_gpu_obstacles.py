@@ -41,6 +41,24 @@ def test_obstacles_match_oracle(nx, ny, bc, precision):
         assert np.array_equal(got[:, solid != 0], F0[:, solid != 0])  # solid cells keep their populations
 
 
+@pytest.mark.parametrize("mrt", [False, True], ids=["bgk", "mrt"])
+@pytest.mark.parametrize("precision", [lbm_sw.FP64, lbm_sw.FP32])
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: "".join("PWOI"[k] for k in b))
+@pytest.mark.parametrize("nx,ny,fraction", [(1, 1, 0.5), (3, 2, 0.3), (7, 5, 0.3), (33, 17, 0.05), (130, 12, 0.25),
+                                            (257, 33, 0.02), (513, 20, 0.3), (129, 64, 0.0)])
+def test_vectorised_obstacle_kernel_equals_one_thread_per_cell(nx, ny, fraction, bc, precision, mrt):
+    """The row kernel (16-byte vectors, warp shuffles, a warp with no solid cell near it on the
+    plain path) against the one-thread-per-cell obstacle kernel: the same operations on the
+    same values, so the same bits, over several steps."""
+    solid = inputs.random_obstacles(ny, nx, seed=930 + nx + ny, fraction=fraction)
+    F0 = inputs.random_populations(13, ny, nx, seed=940 + nx + ny)
+    rates = [0.0, 1.1, 1.2, 1.3, 1.4, 0.0, 1.5, 1.6, 1.7, 0.0, 1.75, 1.65, 0.9] if mrt else None
+    kw = dict(dim=2, precision=precision, bc=bc, inflow=INFLOW_STATES, a=0.05, solid=solid, mrt_rates=rates)
+    a = gpu_post(F0, 7, kernel=lbm_sw.KERNEL_SIMPLE, **kw)
+    b = gpu_post(F0, 7, kernel=lbm_sw.KERNEL_VEC, **kw)
+    assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("precision", [lbm_sw.FP64, lbm_sw.FP32])
 def test_empty_mask_equals_simple_kernel(precision):
     F0 = inputs.random_populations(13, 19, 70, seed=920)

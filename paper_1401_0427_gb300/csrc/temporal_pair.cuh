@@ -199,10 +199,14 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
                                     : dup2(A.inflow_feq[LBM_SW_SIDE_YP * 13 + 4 + 4 * fam]);
   };
 
+  // rows land in order, one per call of issue_row (j = 0, 1, 2, ...): with periodic y sides
+  // the wrapped row advances by one per call instead of being reduced modulo ny every row
+  int next_gr = py ? ((ys - K) % ny + ny) % ny : 0;
   auto issue_row = [&](int j) {
     const int r = ys - K + j;
+    const int gr = py ? next_gr : r;
+    if (py) next_gr = next_gr + 1 == ny ? 0 : next_gr + 1;
     if (j < iters && col_live && (py || (r >= 0 && r < ny))) {
-      const int gr = py ? ((r % ny) + ny) % ny : r;
       const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
       float* sa = l0a + (j % S::A0) * 3 * RS + col + 2;
       float* sb = l0b + (j % S::B0) * S::BP * RS + col + 2;

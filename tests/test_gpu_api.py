@@ -16,16 +16,43 @@ P, W, O, I = lbm_sw.PERIODIC, lbm_sw.WALL, lbm_sw.OUTFLOW, lbm_sw.INFLOW
 
 @pytest.mark.parametrize("precision", [lbm_sw.FP64, lbm_sw.FP32])
 @pytest.mark.parametrize("bc", [(P, P, P, P), (W, W, W, W), (O, O, O, O), (W, O, P, P)], ids=str)
-@pytest.mark.parametrize("h0", [1.0, 2.0, 0.5])
-def test_lake_at_rest_stays_exactly_at_rest(precision, bc, h0):
+@pytest.mark.parametrize("h0", [1.0, 2.0, 0.5, 1.37, 0.73, 2.9])
+def test_lake_at_rest_stays_at_rest(precision, bc, h0):
+    """A lake at rest keeps exactly zero velocities and a uniform depth (every cell rounds
+    alike and the x / y mirror pairs cancel exactly).  The BGK step evaluates
+    (1 - s) f + s f^eq, which maps the initial equilibrium onto a rounding neighbour: the
+    populations settle within about one unit in the last place of it in the first steps and
+    stay there (the same bound after 200 and 2000 steps, no drift)."""
     nx, ny = 133, 70
+    tol = 1e-14 if precision == lbm_sw.FP64 else 1e-6
     with lbm_sw.Simulation(nx, ny, precision=precision, bc=bc, stream=torch_stream()) as sim:
         sim.set_state(np.full((ny, nx), h0), np.zeros((ny, nx)), np.zeros((ny, nx)))
+        F0 = sim.populations().astype(np.float64)
+        for n in (200, 1800):
+            sim.step(n)
+            F = sim.populations().astype(np.float64)
+            assert np.abs(F - F0).max() <= tol * np.abs(F0).max()
+            h, hu, hv = sim.moments()
+            assert np.all(hu == 0) and np.all(hv == 0)
+            assert np.all(h == h.flat[0]) and abs(h.flat[0] - h0) <= tol * h0
+
+
+@pytest.mark.parametrize("precision", [lbm_sw.FP64, lbm_sw.FP32])
+@pytest.mark.parametrize("bc", [(P, P, P, P), (W, O, P, P)], ids=str)
+@pytest.mark.parametrize("h0", [1.37, 0.73])
+def test_lake_at_rest_is_a_fixed_point_of_the_mrt_collision(precision, bc, h0):
+    """The MRT form relaxes f^eq - f, which is exactly zero at rest: with any rates (here all
+    equal to s, the BGK operator) the equilibrium maps to itself bit for bit."""
+    nx, ny = 133, 70
+    with lbm_sw.Simulation(nx, ny, precision=precision, bc=bc, stream=torch_stream()) as sim:
+        sim.set_relaxation([0.0] + [1.8] * 4 + [0.0] + [1.8] * 3 + [0.0] + [1.8] * 3)
+        sim.set_state(np.full((ny, nx), h0), np.zeros((ny, nx)), np.zeros((ny, nx)))
         F0 = sim.populations()
+        W0 = sim.moments()  # the depth of the stored equilibrium (its FP32 sum may round off h0)
         sim.step(200)
         assert np.array_equal(sim.populations(), F0)
         h, hu, hv = sim.moments()
-    assert np.all(h == h0) and np.all(hu == 0) and np.all(hv == 0)
+    assert np.array_equal(h, W0[0]) and np.all(h == h.flat[0]) and np.all(hu == 0) and np.all(hv == 0)
 
 
 @pytest.mark.parametrize("precision", [lbm_sw.FP64, lbm_sw.FP32])

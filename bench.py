@@ -740,7 +740,10 @@ def shock_reflection_variant(stream, lbm_sw, torch, steps: int = 2000):
 def adjoint_variant(stream, lbm_sw, torch, steps: int = 200):
     """Inverse-problem workload: 1024 x 1024 periodic, 8 Gaussian bumps on depth 1, T = 200,
     FP32 states with FP64 checkpoints every ceil(sqrt(T)) steps.  One gradient = recorded
-    forward run + adjoint (segment replays + adjoint steps), against 2T plain steps."""
+    forward run + adjoint (segment replays + adjoint steps), against 2T plain steps.  Also
+    timed: the other end of the tape's memory / time trade-off, one checkpoint interval of
+    T steps, where the recorded forward run keeps the moments of every step (T + K slots of
+    3 planes) and the backward pass replays nothing."""
     from paper_1401_0427_gb300 import inputs
 
     n = 1024
@@ -752,22 +755,30 @@ def adjoint_variant(stream, lbm_sw, torch, steps: int = 200):
         t_plain = _timed(stream, torch, lambda: sim.step(2 * steps))
         g = torch.zeros((n, n), dtype=torch.float64, device="cuda")
         g += 1e-3
-        times = []
-        for _ in range(2):
-            sim.set_state(h0, z, z)
-            tape = lbm_sw.Tape(sim, steps)
+        res = {}
+        for interval in (0, steps):
+            times = []
+            for _ in range(2):
+                sim.set_state(h0, z, z)
+                tape = lbm_sw.Tape(sim, steps, interval)
 
-            def gradient():
-                tape.record()
-                tape.adjoint(g)
+                def gradient():
+                    tape.record()
+                    tape.adjoint(g)
 
-            times.append(_timed(stream, torch, gradient))
-            info = tape.info()
-            tape.close()
-    t_grad = min(times)
+                times.append(_timed(stream, torch, gradient))
+                info = tape.info()
+                tape.close()
+            res[interval] = (min(times), info)
+    t_grad, info = res[0]
+    t_all, info_all = res[steps]
     return {"cells": n * n, "steps": steps, "interval": info.interval, "checkpoints": info.checkpoints,
-            "checkpoint_bytes": info.checkpoint_bytes, "ms_per_gradient": t_grad * 1e3,
-            "ms_2T_plain_steps": t_plain * 1e3, "gradient_over_2T_plain": t_grad / t_plain}
+            "checkpoint_bytes": info.checkpoint_bytes, "moment_bytes": info.replay_bytes,
+            "ms_per_gradient": t_grad * 1e3, "ms_2T_plain_steps": t_plain * 1e3,
+            "gradient_over_2T_plain": t_grad / t_plain,
+            "interval_T": {"interval": info_all.interval, "checkpoints": info_all.checkpoints,
+                           "checkpoint_bytes": info_all.checkpoint_bytes, "moment_bytes": info_all.replay_bytes,
+                           "ms_per_gradient": t_all * 1e3, "gradient_over_2T_plain": t_all / t_plain}}
 
 
 def shock_tube_variant(stream, lbm_sw, torch, steps: int = 500):

@@ -353,8 +353,8 @@ __global__ void __launch_bounds__(COLS / 2, 2)
   extern __shared__ __align__(16) float smem[];
   pdl_wait();
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
-    pair_wave<K, COLS, PF, STORE_W, L0R, true, false, STORE_W, !STORE_W && K <= 6>(A, Kc, smem, strip * P.w, P.w, ys,
-                                                                                   ye, wout, wslot);
+    pair_wave<K, COLS, PF, STORE_W, L0R, true, false, STORE_W, !STORE_W && K <= 6,
+              !STORE_W && K == 6 && COLS == 256>(A, Kc, smem, strip * P.w, P.w, ys, ye, wout, wslot);
   });
   pdl_done();
 }

@@ -74,8 +74,15 @@ __host__ __device__ constexpr int reg_index(int p) {
 // columns and rows outside the domain are neither loaded nor computed, except the second lane
 // of the pair that holds the last column of an odd nx (loaded from the row's padding,
 // computed, never stored, never pulled).
+//
+// STEADY (periodic, U3): the iterations in which every level's row lies in its range run a
+// body without the per-level row and column tests: every lane of a warp with a live column
+// computes every level, lanes outside a level's columns produce values that no valid cell
+// pulls, and the stores keep their tests.  One branch-free block per iteration lets the
+// code generator overlap a level's loads with the previous level's collision (+1 % at K = 6
+// with 256 columns; slower at K = 4 and with 128 columns, which keep the tests).
 template <int K, int COLS, int PF, bool STORE_W, bool L0R, bool PER = true, bool MRT = false, bool ODD = true,
-          bool U3 = false>
+          bool U3 = false, bool STEADY = false>
 __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts<float>& Kc, float* smem, int x0, int w,
                                           int ys, int ye, float* __restrict__ wout, long long wslot) {
   using S = PairShape<K, COLS, PF, L0R>;
@@ -109,6 +116,7 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
   const bool at_xp = !px && gx_raw + 1 == nx - 1;  // lane .y is its last (even nx)
   const bool at_xp_x = !px && gx_raw == nx - 1;    // lane .x is its last (odd nx)
   const int iters = (ye - ys) + 2 * K;
+  const bool warp_live = __any_sync(0xffffffffu, col_live);  // STEADY: a warp with no live column skips
 
   // Level t's values as the input of level t + 1: the -y movers of the row computed now
   // (a_now), and f0 (f0r) and the +y movers (cr) of the rows of the last three iterations,
@@ -232,7 +240,8 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
 
 #pragma unroll
   for (int q = 0; q < PF; ++q) issue_row(q);
-  auto iter = [&](int j, auto phc) {
+  auto iter = [&](int j, auto phc, auto fullc) {
+    constexpr bool FULL = decltype(fullc)::value;  // every level's row valid, every lane computes
     // slots of the rows of iterations j, j - 1, j - 2
     constexpr int PH = decltype(phc)::value, P1 = U3 ? (PH + 2) % 3 : 1, P2 = U3 ? (PH + 1) % 3 : 2;
     __pipeline_wait_prior(PF - 1);  // row j has landed (this thread's copies)
@@ -280,7 +289,7 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
       const int R = ys - K + j - t;
       const bool row_ok = R >= ys - K + t && R < ye + K - t;
       const bool row_live = py || (R >= 0 && R < ny);
-      if (row_ok && row_live && col_live && col + 1 >= t && col < w + 2 * K - t) {
+      if (FULL ? warp_live : (row_ok && row_live && col_live && col + 1 >= t && col < w + 2 * K - t)) {
         float2 f[13];
         if (t == 1 && L0R) {
           const float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;                 // row R + 1
@@ -382,13 +391,28 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
   if constexpr (U3) {
     // extra iterations past iters compute and load nothing (their rows are out of range)
     const int iters3 = (iters + 2) / 3 * 3;
-    for (int j = 0; j < iters3; j += 3) {
-      iter(j, std::integral_constant<int, 0>{});
-      iter(j + 1, std::integral_constant<int, 1>{});
-      iter(j + 2, std::integral_constant<int, 2>{});
+    using F0 = std::integral_constant<bool, false>;
+    using F1 = std::integral_constant<bool, true>;
+    int j = 0;
+    if constexpr (STEADY && PER) {
+      for (; j < 2 * K; j += 3) {  // fill: a level whose first row is not reached yet
+        iter(j, std::integral_constant<int, 0>{}, F0{});
+        iter(j + 1, std::integral_constant<int, 1>{}, F0{});
+        iter(j + 2, std::integral_constant<int, 2>{}, F0{});
+      }
+      for (; j + 2 < iters; j += 3) {  // steady state: j in [2K, iters)
+        iter(j, std::integral_constant<int, 0>{}, F1{});
+        iter(j + 1, std::integral_constant<int, 1>{}, F1{});
+        iter(j + 2, std::integral_constant<int, 2>{}, F1{});
+      }
+    }
+    for (; j < iters3; j += 3) {
+      iter(j, std::integral_constant<int, 0>{}, F0{});
+      iter(j + 1, std::integral_constant<int, 1>{}, F0{});
+      iter(j + 2, std::integral_constant<int, 2>{}, F0{});
     }
   } else {
-    for (int j = 0; j < iters; ++j) iter(j, std::integral_constant<int, 0>{});
+    for (int j = 0; j < iters; ++j) iter(j, std::integral_constant<int, 0>{}, std::integral_constant<bool, false>{});
   }
   __pipeline_wait_prior(0);
 }

@@ -181,6 +181,12 @@ def test_inverse_problem_workload_1024():
     d = inputs.uniform(77, n * n, -1, 1).reshape(n, n)
     want = _oracle_directional((h_guess, z, z), (d, z, z), steps, p, h_obs)
     assert abs(float((g64 * d).sum()) - want) <= 1e-9 * abs(want)
+    # one interval of T steps: the recorded run keeps the moments of every step and the
+    # backward pass replays nothing; the adjoint launches split the steps differently, so the
+    # gradient agrees to FP32 rounding
+    (gT, _, _), _, infoT = _gpu_gradient((h_guess, z, z), steps, h_obs, precision=lbm_sw.FP32, interval=steps)
+    assert infoT.interval == steps and infoT.checkpoints == 1
+    assert np.abs(gT - g32).max() <= 1e-5 * np.abs(g32).max()
 
 
 def test_autograd_function_and_recovery():

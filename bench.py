@@ -62,10 +62,10 @@ def temporal_kernel_name(k: int, cells: int = 4096 * 4096) -> str:
 # kernel sources it was taken on.
 NCU_TRAFFIC = {
     "step2d_temporal_periodic_x2<6, 256, 1, 0, 1>": {
-        "src_sha256": "244da910e174589b394c95c467d50601613cb25aa6683dc5c59a3a210ac81f32",
-        "sources": ("temporal.cu", "temporal.cuh", "temporal_pair.cuh", "scheme.cuh"), "bytes_per_launch": 1744.57e6,
+        "src_sha256": "18bc2ede92591ad85d61e2880a9a077f0f1898820ff90040b9faf6c900debbe5",
+        "sources": ("temporal.cu", "temporal.cuh", "temporal_pair.cuh", "scheme.cuh"), "bytes_per_launch": 1744.88e6,
         "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of the 5 launches of "
-                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 920.92 MB read + 823.65 MB "
+                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.09 MB read + 823.79 MB "
                 "written per launch (mean)"},
 }
 

@@ -210,32 +210,66 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
   // rows land in order, one per call of issue_row (j = 0, 1, 2, ...): with periodic y sides
   // the wrapped row advances by one per call instead of being reduced modulo ny every row
   int next_gr = py ? ((ys - K) % ny + ny) % ny : 0;
+  // BGK: two commit groups per row: first the planes read in the iteration the row lands (the
+  // -y movers, and f0 and the +y movers of the C group), then the B group, first read one
+  // iteration later; an iteration waits for its row's first group and the previous row's
+  // B group, so the B copies have two iterations to land in the same ring slots (+0.4 %
+  // periodic, +1.5 % with walls at K = 6).  MRT keeps one group per row (the split measured
+  // 2-3 % slower there).
+  constexpr bool SPLIT = !MRT;
   auto issue_row = [&](int j) {
     const int r = ys - K + j;
     const int gr = py ? next_gr : r;
     if (py) next_gr = next_gr + 1 == ny ? 0 : next_gr + 1;
-    if (j < iters && col_live && (py || (r >= 0 && r < ny))) {
+    if constexpr (SPLIT) {
+      const bool live = j < iters && col_live && (py || (r >= 0 && r < ny));
       const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
+      const float* g2 = A.src + static_cast<long long>(gr) * A.pitch + gx2;
       float* sa = l0a + (j % S::A0) * 3 * RS + col + 2;
       float* sb = l0b + (j % S::B0) * S::BP * RS + col + 2;
       float* sc = l0c + (j % S::C0) * S::CP * RS + col + 2;
-      if (!split) {
+      auto copies = [&](bool b_group) {
+        if (!live) return;
 #pragma unroll
         for (int p = 0; p < 13; ++p) {
+          if ((grp(p) == 1) != b_group) continue;
           float* d = grp(p) == 0 ? sa : (grp(p) == 1 ? sb : sc);
-          __pipeline_memcpy_async(d + idx(p) * RS, g + p * A.plane, 2 * sizeof(float));
+          if (!split) {
+            __pipeline_memcpy_async(d + idx(p) * RS, g + p * A.plane, 2 * sizeof(float));
+          } else {
+            __pipeline_memcpy_async(d + idx(p) * RS, g + p * A.plane, sizeof(float));
+            __pipeline_memcpy_async(d + idx(p) * RS + 1, g2 + p * A.plane, sizeof(float));
+          }
         }
-      } else {
-        const float* g2 = A.src + static_cast<long long>(gr) * A.pitch + gx2;
+      };
+      copies(false);
+      __pipeline_commit();
+      copies(true);
+      __pipeline_commit();
+    } else {
+      if (j < iters && col_live && (py || (r >= 0 && r < ny))) {
+        const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
+        float* sa = l0a + (j % S::A0) * 3 * RS + col + 2;
+        float* sb = l0b + (j % S::B0) * S::BP * RS + col + 2;
+        float* sc = l0c + (j % S::C0) * S::CP * RS + col + 2;
+        if (!split) {
 #pragma unroll
-        for (int p = 0; p < 13; ++p) {
-          float* d = grp(p) == 0 ? sa : (grp(p) == 1 ? sb : sc);
-          __pipeline_memcpy_async(d + idx(p) * RS, g + p * A.plane, sizeof(float));
-          __pipeline_memcpy_async(d + idx(p) * RS + 1, g2 + p * A.plane, sizeof(float));
+          for (int p = 0; p < 13; ++p) {
+            float* d = grp(p) == 0 ? sa : (grp(p) == 1 ? sb : sc);
+            __pipeline_memcpy_async(d + idx(p) * RS, g + p * A.plane, 2 * sizeof(float));
+          }
+        } else {
+          const float* g2 = A.src + static_cast<long long>(gr) * A.pitch + gx2;
+#pragma unroll
+          for (int p = 0; p < 13; ++p) {
+            float* d = grp(p) == 0 ? sa : (grp(p) == 1 ? sb : sc);
+            __pipeline_memcpy_async(d + idx(p) * RS, g + p * A.plane, sizeof(float));
+            __pipeline_memcpy_async(d + idx(p) * RS + 1, g2 + p * A.plane, sizeof(float));
+          }
         }
       }
+      __pipeline_commit();
     }
-    __pipeline_commit();
   };
 
 #pragma unroll
@@ -244,7 +278,8 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
     constexpr bool FULL = decltype(fullc)::value;  // every level's row valid, every lane computes
     // slots of the rows of iterations j, j - 1, j - 2
     constexpr int PH = decltype(phc)::value, P1 = U3 ? (PH + 2) % 3 : 1, P2 = U3 ? (PH + 1) % 3 : 2;
-    __pipeline_wait_prior(PF - 1);  // row j has landed (this thread's copies)
+    // row j's first group and row j - 1's B group (SPLIT), or all of row j, have landed
+    __pipeline_wait_prior(SPLIT ? 2 * PF - 1 : PF - 1);
     __syncthreads();                // ... and every thread's; iteration j - 1 is over everywhere
     if (L0R) {
       // f0 and the +y movers of the row just landed, into registers (read by level 1 one

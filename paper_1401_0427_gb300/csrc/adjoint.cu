@@ -428,10 +428,9 @@ int run_adjoint(lbm_sw* h, lbm_sw_tape* t, const double* gh, const double* gu, c
     if (seg == t->checkpoints - 1 && t->last_w) {
       t->last_w = false;
     } else {
-    TAPE_CUDA(t, (lbm::launch_convert<double, T>(t->ckpt + static_cast<size_t>(seg) * t->state_elems,
-                                                 static_cast<T*>(t->rep[0]), static_cast<long long>(t->state_elems), st)),
-              "checkpoint restore");
-    TAPE_CUDA(t, lbm::launch_moments2d_planes<T>(replay_args<T>(h, t, 0), W, st), "replay moments");
+    TAPE_CUDA(t, lbm::launch_restore_moments2d<T>(t->ckpt + static_cast<size_t>(seg) * t->state_elems,
+                                                   replay_args<T>(h, t, 1), W, st),
+              "checkpoint restore");  // into rep[0] (the dst of replay_args(.., 1)), with W^{k0}
     int from = 0, j = 1;
     if constexpr (sizeof(T) == 4) {
       // FP32: K steps per launch where the fused kernel can store every level's moments

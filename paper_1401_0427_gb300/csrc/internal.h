@@ -57,6 +57,10 @@ template <class T>
 cudaError_t launch_step2d_store_w(const StepArgs<T>& a, const ConstsD& k, T* w_out, cudaStream_t st);
 template <class T>
 cudaError_t launch_moments2d_planes(const StepArgs<T>& a, T* w_out, cudaStream_t st);
+// An FP64 checkpoint (pitched planes of a.dst's layout) restored into a.dst, with its moments
+// in the three planes at w_out (as launch_moments2d_planes of the restored state).
+template <class T>
+cudaError_t launch_restore_moments2d(const double* ck, const StepArgs<T>& a, T* w_out, cudaStream_t st);
 template <class Tin, class Tout>
 cudaError_t launch_convert(const Tin* in, Tout* out, long long n, cudaStream_t st);
 

@@ -252,6 +252,29 @@ __global__ void moments2d_planes(const StepArgs<T> A, T* __restrict__ w) {
   }
 }
 
+// An FP64 checkpoint back into the storage precision (A.dst, pitched planes) with the moments
+// of the restored populations (summed as moments2d_planes does) in the three planes at w:
+// the restore and the first moment slot of a segment replay in one pass.
+template <class T>
+__global__ void restore_moments2d(const double* __restrict__ ck, const StepArgs<T> A, T* __restrict__ w) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < A.ny; y += gridDim.y * blockDim.y) {
+    if (x >= A.nx) continue;
+    const long long c = static_cast<long long>(y) * A.pitch + x;
+    T f[13];
+#pragma unroll
+    for (int p = 0; p < 13; ++p) {
+      f[p] = static_cast<T>(ck[p * A.plane + c]);
+      A.dst[p * A.plane + c] = f[p];
+    }
+    T d, qx, qy;
+    moments13(f, d, qx, qy);
+    w[c] = d;
+    w[A.plane + c] = qx;
+    w[2 * A.plane + c] = qy;
+  }
+}
+
 template <class Tin, class Tout>
 __global__ void convert_kernel(const Tin* __restrict__ in, Tout* __restrict__ out, long long n) {
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
@@ -354,6 +377,13 @@ cudaError_t launch_step2d_store_w(const StepArgs<T>& a, const ConstsD& kd, T* w_
 }
 
 template <class T>
+cudaError_t launch_restore_moments2d(const double* ck, const StepArgs<T>& a, T* w_out, cudaStream_t st) {
+  const dim3 block(128, 2);
+  restore_moments2d<T><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(ck, a, w_out);
+  return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t launch_moments2d_planes(const StepArgs<T>& a, T* w_out, cudaStream_t st) {
   const dim3 block(128, 2);
   moments2d_planes<T><<<cell_grid(a.nx, a.ny, block), block, 0, st>>>(a, w_out);
@@ -421,7 +451,8 @@ cudaError_t launch_inflow_feq2d(T* out, const int bc[4], const double inflow[4][
   template cudaError_t launch_moments2d<T>(const StepArgs<T>&, double*, double*, double*, cudaStream_t);   \
   template cudaError_t launch_inflow_feq2d<T>(T*, const int[4], const double[4][3], const ConstsD&, cudaStream_t); \
   template cudaError_t launch_step2d_store_w<T>(const StepArgs<T>&, const ConstsD&, T*, cudaStream_t);       \
-  template cudaError_t launch_moments2d_planes<T>(const StepArgs<T>&, T*, cudaStream_t);
+  template cudaError_t launch_moments2d_planes<T>(const StepArgs<T>&, T*, cudaStream_t);                          \
+  template cudaError_t launch_restore_moments2d<T>(const double*, const StepArgs<T>&, T*, cudaStream_t);
 
 LBM_INSTANTIATE_2D(float)
 LBM_INSTANTIATE_2D(double)

@@ -144,16 +144,16 @@ def test_paired_kernel_equals_single_steps(nx, ny, k, bc):
         assert np.array_equal(a, b), (steps, nx, ny)
 
 
-@pytest.mark.parametrize("steps", [6, 13, 20])
-def test_large_periodic_kernel_equals_single_steps(steps):
+@pytest.mark.parametrize("nx,ny,steps", [(2900, 2900, 6), (2900, 2900, 13), (2900, 2900, 20), (3002, 2795, 20)])
+def test_large_periodic_kernel_equals_single_steps(nx, ny, steps):
     """Periodic grids of 2^23 cells or more with an even width run K = 6 in 256-column
-    strips (the headline kernel): bit for bit equal to one step per launch on non-equilibrium
-    populations (a seeded random 96-row tile repeated over 2900 x 2900 cells)."""
-    n = 2900
-    tile = inputs.random_populations(13, 96, n, seed=7900 + steps).astype(np.float32)
-    F0 = np.ascontiguousarray(np.tile(tile, (1, n // 96 + 1, 1))[:, :n, :])
+    strips (the headline kernel, with its branch-free steady state): bit for bit equal to one
+    step per launch on non-equilibrium populations (a seeded random 96-row tile repeated over
+    the grid; 3002 x 2795 has a narrow last strip and an odd height)."""
+    tile = inputs.random_populations(13, 96, nx, seed=7900 + steps + nx).astype(np.float32)
+    F0 = np.ascontiguousarray(np.tile(tile, (1, ny // 96 + 1, 1))[:, :ny, :])
     a = _run(F0, steps, (P, P, P, P), lbm_sw.KERNEL_VEC)
-    with lbm_sw.Simulation(n, n, precision=lbm_sw.FP32, stream=torch_stream()) as sim:
+    with lbm_sw.Simulation(nx, ny, precision=lbm_sw.FP32, stream=torch_stream()) as sim:
         assert sim.info().kernel == lbm_sw.KERNEL_TEMPORAL and sim.info().steps_per_launch == 6
         sim.set_populations(F0, form=lbm_sw.PRE_COLLISION)
         sim.step(steps)

@@ -184,7 +184,7 @@ __device__ __forceinline__ void equilibrium_vjp_x2(float2 h, float2 qx, float2 q
                                                    const Consts<float>& K, float2& zh, float2& zx, float2& zy) {
   const float2 nz = dup2(K.nz);
   auto mul = [&](float2 a, float2 b) { return fma2(a, b, nz); };
-  const float2 rh = make_float2(1.0f / h.x, 1.0f / h.y);
+  const float2 rh = make_float2(recip(h.x), recip(h.y));
   const float2 u = mul(qx, rh), v = mul(qy, rh);
   const float2 gh = mul(dup2(2.0f * K.half_g), h);
   const float2 inv2gh = mul(dup2(2.0f * K.inv4g), rh);

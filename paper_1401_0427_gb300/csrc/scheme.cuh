@@ -278,7 +278,7 @@ __device__ __forceinline__ void collide13_any(T f[13], const Consts<T>& k, T& h,
 template <class T>
 __device__ __forceinline__ void equilibrium_vjp(T h, T qx, T qy, const T psi[13], const Consts<T>& K, T& zh,
                                                 T& zx, T& zy) {
-  const T rh = T(1) / h;
+  const T rh = recip(h);
   const T u = qx * rh, v = qy * rh;
   const T gh = T(2) * K.half_g * h;
   const T inv2gh = T(2) * K.inv4g * rh;

@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(COLS / 2, 2)
   extern __shared__ __align__(16) float smem[];
   pdl_wait();
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
-    pair_wave<K, COLS, PF, false, L0R, PER, true, true>(A, Kc, smem, strip * P.w, P.w, ys, ye, nullptr, 0);
+    pair_wave<K, COLS, PF, false, L0R, PER, true, true, false, PER>(A, Kc, smem, strip * P.w, P.w, ys, ye, nullptr, 0);
   });
   pdl_done();
 }

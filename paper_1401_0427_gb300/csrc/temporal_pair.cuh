@@ -75,12 +75,13 @@ __host__ __device__ constexpr int reg_index(int p) {
 // of the pair that holds the last column of an odd nx (loaded from the row's padding,
 // computed, never stored, never pulled).
 //
-// STEADY (periodic, U3): the iterations in which every level's row lies in its range run a
+// STEADY (periodic): the iterations in which every level's row lies in its range run a
 // body without the per-level row and column tests: every lane of a warp with a live column
 // computes every level, lanes outside a level's columns produce values that no valid cell
 // pulls, and the stores keep their tests.  One branch-free block per iteration lets the
-// code generator overlap a level's loads with the previous level's collision (+1 % at K = 6
-// with 256 columns; slower at K = 4 and with 128 columns, which keep the tests).
+// code generator overlap a level's loads with the previous level's collision (BGK at K = 6
+// with 256 columns +1 %, MRT +1.4 %; BGK at K = 4 and with 128 columns measured slower and
+// keeps the tests).
 template <int K, int COLS, int PF, bool STORE_W, bool L0R, bool PER = true, bool MRT = false, bool ODD = true,
           bool U3 = false, bool STEADY = false>
 __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts<float>& Kc, float* smem, int x0, int w,
@@ -447,7 +448,12 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
       iter(j + 2, std::integral_constant<int, 2>{}, F0{});
     }
   } else {
-    for (int j = 0; j < iters; ++j) iter(j, std::integral_constant<int, 0>{}, std::integral_constant<bool, false>{});
+    int j = 0;
+    if constexpr (STEADY && PER) {
+      for (; j < 2 * K; ++j) iter(j, std::integral_constant<int, 0>{}, std::integral_constant<bool, false>{});
+      for (; j < iters; ++j) iter(j, std::integral_constant<int, 0>{}, std::integral_constant<bool, true>{});
+    }
+    for (; j < iters; ++j) iter(j, std::integral_constant<int, 0>{}, std::integral_constant<bool, false>{});
   }
   __pipeline_wait_prior(0);
 }

@@ -116,6 +116,20 @@ def test_mrt_temporal_equals_single_steps(nx, ny, bc, k):
         assert np.array_equal(a, b), (steps, nx, ny)
 
 
+@pytest.mark.parametrize("bc", [(P, P, P, P), (W, O, P, P)], ids=lambda b: "".join("PWOI"[k] for k in b))
+def test_mrt_large_grid_temporal_equals_single_steps(bc):
+    """Grids of 2^23 cells or more run the MRT wavefront in 256-column strips (periodic: with
+    its branch-free steady state): bit for bit equal to one MRT step per launch, 13 steps
+    (6 + 6 + 1) on a seeded random 96-row tile repeated over 2900 x 2900 cells."""
+    n = 2900
+    tile = inputs.random_populations(13, 96, n, seed=6900).astype(np.float32)
+    F0 = np.ascontiguousarray(np.tile(tile, (1, n // 96 + 1, 1))[:, :n, :])
+    a, _ = _run_mrt(F0, 13, bc, lbm_sw.KERNEL_VEC)
+    b, spl = _run_mrt(F0, 13, bc, lbm_sw.KERNEL_AUTO)
+    assert spl == 6
+    assert np.array_equal(a, b)
+
+
 def test_mrt_temporal_choice():
     """AUTO on 1024^2 FP32 grids keeps temporal blocking with MRT (the two-column kernel, any
     width and sides)."""

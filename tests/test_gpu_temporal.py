@@ -144,10 +144,12 @@ def test_paired_kernel_equals_single_steps(nx, ny, k, bc):
         assert np.array_equal(a, b), (steps, nx, ny)
 
 
-@pytest.mark.parametrize("nx,ny,steps", [(2900, 2900, 6), (2900, 2900, 13), (2900, 2900, 20), (3002, 2795, 20)])
+@pytest.mark.parametrize("nx,ny,steps", [(2900, 2900, 2), (2900, 2900, 6), (2900, 2900, 13), (2900, 2900, 20),
+                                         (3002, 2795, 20), (2901, 2901, 20)])
 def test_large_periodic_kernel_equals_single_steps(nx, ny, steps):
     """Periodic grids of 2^23 cells or more with an even width run K = 6 in 256-column
-    strips (the headline kernel, with its branch-free steady state): bit for bit equal to one
+    strips (the headline kernel, with its branch-free steady state), and their tails K = 4
+    and K = 2 (20 = 6 + 6 + 4 + 4; 2), and the odd-width form (2901): bit for bit equal to one
     step per launch on non-equilibrium populations (a seeded random 96-row tile repeated over
     the grid; 3002 x 2795 has a narrow last strip and an odd height)."""
     tile = inputs.random_populations(13, 96, nx, seed=7900 + steps + nx).astype(np.float32)

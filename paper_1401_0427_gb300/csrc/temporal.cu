@@ -516,11 +516,11 @@ template <int K>
 cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t st, int sm_count) {
   const bool per = a.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC && a.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
   // even K: the paired kernel, the measured best at each K: 256 columns and two rows of
-  // prefetch up to K = 4 (periodic: with the input row's f0 and +y movers in registers,
-  // +1.6 % at K = 4 and +30 % at K = 2); at K = 6, 256 columns, one row of prefetch and the
-  // input row's f0 and +y movers in registers (two CTAs per SM); at K = 8, 192 columns and
-  // one row of prefetch.  Sides that are not periodic take the same shapes (without the
-  // registers at K <= 4) with their boundary rules.
+  // prefetch up to K = 4, with the input row's f0 and +y movers in registers (periodic
+  // +1.6 % at K = 4 and +30 % at K = 2, walls +0.7 % and +31 %); at K = 6, 256 columns, one
+  // row of prefetch and the same registers (two CTAs per SM); at K = 8, 192 columns and one
+  // row of prefetch.  Sides that are not periodic take the same shapes with their boundary
+  // rules.
   if constexpr (K % 2 == 0) {
     // 128-column strips (four CTAs per SM) on small grids, whose row segments are longer for
     // the same number of CTAs, so less of the work is the wavefront's fill: K = 6 below 2^23
@@ -529,8 +529,8 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
     const long long cells = static_cast<long long>(a.nx) * a.ny;
     const bool small = cells < (1LL << 23);
     if constexpr (K == 4)
-      if (cells < (1LL << 21))
-        return per ? launch_k_pairs<K, 128, 2>(a, kd, st, sm_count)
+      if (cells < (1LL << 21))  // (periodic: f0 and +y movers in registers, +1.8 % at 1024^2; walls: -13 %)
+        return per ? launch_k_pairs<K, 128, 2, true>(a, kd, st, sm_count)
                    : launch_k_pairs<K, 128, 2, false, false>(a, kd, st, sm_count);
     if (per) {
       if constexpr (K <= 4)
@@ -542,7 +542,7 @@ cudaError_t launch_k(const StepArgs<float>& a, const ConstsD& kd, cudaStream_t s
         return launch_k_pairs<K, 192, 1>(a, kd, st, sm_count);
     }
     if constexpr (K <= 4)
-      return launch_k_pairs<K, 256, 2, false, false>(a, kd, st, sm_count);
+      return launch_k_pairs<K, 256, 2, true, false>(a, kd, st, sm_count);
     else if constexpr (K == 6)
       return small ? launch_k_pairs<K, 128, 1, true, false>(a, kd, st, sm_count)
                    : launch_k_pairs<K, 256, 1, true, false>(a, kd, st, sm_count);

@@ -144,6 +144,24 @@ def test_paired_kernel_equals_single_steps(nx, ny, k, bc):
         assert np.array_equal(a, b), (steps, nx, ny)
 
 
+@pytest.mark.parametrize("bc", [(W, W, W, W), (I, O, W, W)], ids=lambda b: "".join("PWOI"[k] for k in b))
+@pytest.mark.parametrize("steps", [2, 20])
+def test_large_bounded_kernel_equals_single_steps(bc, steps):
+    """Grids of 2^21 cells or more with walls, inflow and outflow run the two-column
+    wavefront in 256-column strips (K = 6, and K = 4 and 2 for the tails, with the input
+    row's f0 and +y movers in registers): bit for bit equal to one step per launch."""
+    nx, ny = 2900, 2900
+    tile = inputs.random_populations(13, 96, nx, seed=8100 + steps).astype(np.float32)
+    F0 = np.ascontiguousarray(np.tile(tile, (1, ny // 96 + 1, 1))[:, :ny, :])
+    a = _run(F0, steps, bc, lbm_sw.KERNEL_VEC)
+    with lbm_sw.Simulation(nx, ny, precision=lbm_sw.FP32, bc=bc, inflow=INFLOW, stream=torch_stream()) as sim:
+        assert sim.info().kernel == lbm_sw.KERNEL_TEMPORAL and sim.info().steps_per_launch == 6
+        sim.set_populations(F0, form=lbm_sw.PRE_COLLISION)
+        sim.step(steps)
+        b = sim.populations()
+    assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("nx,ny,steps", [(2900, 2900, 2), (2900, 2900, 6), (2900, 2900, 13), (2900, 2900, 20),
                                          (3002, 2795, 20), (2901, 2901, 20)])
 def test_large_periodic_kernel_equals_single_steps(nx, ny, steps):

@@ -345,7 +345,9 @@ __global__ void __launch_bounds__(COLS / 2, 2)
 }
 
 // Every side periodic.  The plain kernel runs even widths; the one that also stores the
-// moments of every level (the adjoint's replays) and the _odd kernels any width.
+// moments of every level (the adjoint's replays) and the _odd kernels any width.  The
+// branch-free steady state: the 6-step 256-column plain kernel and every replay kernel
+// (-1 % per gradient at 1024^2).
 template <int K, int COLS, int PF, bool STORE_W = false, bool L0R = false>
 __global__ void __launch_bounds__(COLS / 2, 2)
     step2d_temporal_periodic_x2(const StepArgs<float> A, const Consts<float> Kc, const Partition P,
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(COLS / 2, 2)
   pdl_wait();
   run_segment(P, A.ny, [&](int strip, int ys, int ye) {
     pair_wave<K, COLS, PF, STORE_W, L0R, true, false, STORE_W, !STORE_W && K <= 6,
-              !STORE_W && K == 6 && COLS == 256>(A, Kc, smem, strip * P.w, P.w, ys, ye, wout, wslot);
+              STORE_W || (K == 6 && COLS == 256)>(A, Kc, smem, strip * P.w, P.w, ys, ye, wout, wslot);
   });
   pdl_done();
 }

@@ -1,6 +1,7 @@
 // K reverse steps of the discrete adjoint per launch (temporal blocking of the adjoint
 // recurrence of adjoint.cu), FP32: all-periodic domains, and any sides with an even nx.
 #include <cuda_pipeline.h>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -322,10 +323,14 @@ __device__ __forceinline__ void adjoint_pair_wave(const StepArgs<float>& A, cons
   const bool out_ym = !py && A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_OUTFLOW;
   const bool out_yp = !py && A.bc[LBM_SW_SIDE_YP] == LBM_SW_BC_OUTFLOW;
 
+  // rows land in order, one per call of issue_row: with periodic y sides the wrapped row
+  // advances by one per call, and the rows of the moments read by each level follow it
+  int next_gr = py ? ((ys - K) % ny + ny) % ny : 0;
   auto issue_row = [&](int j) {
     const int r = ys - K + j;
+    const int gr = py ? next_gr : r;
+    if (py) next_gr = next_gr + 1 == ny ? 0 : next_gr + 1;
     if (j < iters && col_live && (py || (r >= 0 && r < ny))) {
-      const int gr = py ? ((r % ny) + ny) % ny : r;
       const float* g = A.src + static_cast<long long>(gr) * A.pitch + gx;
       float* sa = l0a + (j % S::A0) * 3 * RS + col + 2;
       float* sb = l0b + (j % S::B0) * 7 * RS + col + 2;
@@ -342,7 +347,7 @@ __device__ __forceinline__ void adjoint_pair_wave(const StepArgs<float>& A, cons
       for (int t = 1; t <= K; ++t) {
         const int rt0 = r - t;
         if (py || (rt0 >= 0 && rt0 < ny)) {
-          const int rt = py ? (rt0 % ny + ny) % ny : rt0;
+          const int rt = !py ? rt0 : (ny > K ? (gr >= t ? gr - t : gr - t + ny) : (rt0 % ny + ny) % ny);
           const float* gw = w0 - (t - 1) * wslot + static_cast<long long>(rt) * A.pitch + gx;
           float* d = wr(t, j % S::W0) + col + 2;
 #pragma unroll
@@ -355,7 +360,9 @@ __device__ __forceinline__ void adjoint_pair_wave(const StepArgs<float>& A, cons
 
 #pragma unroll
   for (int q = 0; q < PF; ++q) issue_row(q);
-  for (int j = 0; j < iters; ++j) {
+  const bool warp_live = __any_sync(0xffffffffu, col_live);
+  auto iter = [&](int j, auto fullc) {
+    constexpr bool FULL = decltype(fullc)::value;  // every level's row valid, every lane computes
     __pipeline_wait_prior(PF - 1);
     __syncthreads();
     if constexpr (!PER) {
@@ -383,7 +390,7 @@ __device__ __forceinline__ void adjoint_pair_wave(const StepArgs<float>& A, cons
       const int R = ys - K + j - t;
       const bool row_ok = R >= ys - K + t && R < ye + K - t;
       const bool row_live = py || (R >= 0 && R < ny);
-      if (row_ok && row_live && col_live && col + 1 >= t && col < w + 2 * K - t) {
+      if (FULL ? warp_live : (row_ok && row_live && col_live && col + 1 >= t && col < w + 2 * K - t)) {
         const float* wp = wr(t, j % S::W0) + col + 2;
         const float2 wh = ld2(wp), wx = ld2(wp + RS), wy = ld2(wp + 2 * RS);
         float2 psi[13];
@@ -455,7 +462,15 @@ __device__ __forceinline__ void adjoint_pair_wave(const StepArgs<float>& A, cons
         }
       }
     }
+  };
+  int j = 0;
+  if constexpr (PER) {
+    // the iterations in which every level's row lies in its range run without the per-level
+    // tests (lanes outside a level's columns compute values nothing pulls; stores keep theirs)
+    for (; j < 2 * K; ++j) iter(j, std::integral_constant<bool, false>{});
+    for (; j < iters; ++j) iter(j, std::integral_constant<bool, true>{});
   }
+  for (; j < iters; ++j) iter(j, std::integral_constant<bool, false>{});
   __pipeline_wait_prior(0);
 }
 

@@ -62,10 +62,10 @@ def temporal_kernel_name(k: int, cells: int = 4096 * 4096) -> str:
 # kernel sources it was taken on.
 NCU_TRAFFIC = {
     "step2d_temporal_periodic_x2<6, 256, 1, 0, 1>": {
-        "src_sha256": "f92830855d26bae6eaa5257350d5bbcf54f09eb316b9ee80b2f43465cdf2f456",
-        "sources": ("temporal.cu", "temporal.cuh", "temporal_pair.cuh", "scheme.cuh"), "bytes_per_launch": 1744.10e6,
+        "src_sha256": "81eaf0fb6b42dbd2f15894cb44012f9a7ca81ae41962bf024f024c1636b2918d",
+        "sources": ("temporal.cu", "temporal.cuh", "temporal_pair.cuh", "scheme.cuh"), "bytes_per_launch": 1745.18e6,
         "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of the 5 launches of "
-                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 920.48 MB read + 823.62 MB "
+                "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.25 MB read + 823.93 MB "
                 "written per launch (mean)"},
 }
 

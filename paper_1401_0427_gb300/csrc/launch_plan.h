@@ -7,10 +7,10 @@
 namespace lbm {
 
 // Relative cost of one launch of k fused steps (k = 1: one step per launch), measured as
-// ms per launch on the 4096^2 FP32 periodic dam-break: 0.253 (one step), 0.291, 0.377,
-// 0.309, 0.488, 0.372, 0.577, 0.628 (k = 2 .. 8).  Used only to split the tail of a call
+// ms per launch on the 4096^2 FP32 periodic dam-break: 0.253 (one step), 0.291, 0.300,
+// 0.309, 0.355, 0.372, 0.577, 0.628 (k = 2 .. 8).  Used only to split the tail of a call
 // into launches; every split gives the same bits.
-constexpr double kLaunchCost[9] = {0.0, 0.253, 0.291, 0.377, 0.309, 0.488, 0.372, 0.577, 0.628};
+constexpr double kLaunchCost[9] = {0.0, 0.253, 0.291, 0.300, 0.309, 0.355, 0.372, 0.577, 0.628};
 
 constexpr int kMaxTail = 16;  // K + 8 with K <= 8
 

@@ -101,10 +101,13 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
   auto grp = [](int p) { return L0R ? reg_group(p) : plane_group(p); };
   auto idx = [](int p) { return L0R ? reg_index(p) : plane_index(p); };
 
-  const int gx_raw = x0 - K + col;
+  // left halo KL = K rounded up to even, so that tile columns keep the parity of the global
+  // columns (8-byte aligned pairs) at odd K too; the tile spans w + K + KL columns
+  constexpr int KL = K + (K & 1);
+  const int gx_raw = x0 - KL + col;
   const bool px = PER || A.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC;
   const bool py = PER || A.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;
-  const bool col_live = col < w + 2 * K && (px || (gx_raw >= 0 && gx_raw < nx));
+  const bool col_live = col < w + K + KL && (px || (gx_raw >= 0 && gx_raw < nx));
   const int gx = px ? ((gx_raw % nx) + nx) % nx : gx_raw;
   // An odd nx puts, with periodic x sides, the pairs of the halo that wraps around at odd
   // columns and one pair across the periodic seam: those land by two 4-byte copies; with
@@ -325,7 +328,7 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
       const int R = ys - K + j - t;
       const bool row_ok = R >= ys - K + t && R < ye + K - t;
       const bool row_live = py || (R >= 0 && R < ny);
-      if (FULL ? warp_live : (row_ok && row_live && col_live && col + 1 >= t && col < w + 2 * K - t)) {
+      if (FULL ? warp_live : (row_ok && row_live && col_live && col + 1 >= t && col < w + K + KL - t)) {
         float2 f[13];
         if (t == 1 && L0R) {
           const float* ra = l0a + (j % S::A0) * 3 * RS + col + 2;                 // row R + 1
@@ -366,7 +369,7 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
         }
         float2 wh, wx, wy;
         collide13x2_any<MRT>(f, Kc, wh, wx, wy);
-        if (STORE_W && R >= ys && R < ye && col >= K && col < K + w && gx_raw < nx) {
+        if (STORE_W && R >= ys && R < ye && col >= KL && col < KL + w && gx_raw < nx) {
           float* wp = wout + (t - 1) * wslot + static_cast<long long>(R) * A.pitch + gx_raw;
           if (!lane_y_out) {
             st2(wp, wh);
@@ -395,7 +398,7 @@ __device__ __forceinline__ void pair_wave(const StepArgs<float>& A, const Consts
               for (int fam = 0; fam < 3; ++fam) cr[t][P1][fam] = ym_ghost(fam, f[4 + 4 * fam], f[2 + 4 * fam]);
             }
           }
-        } else if (col >= K && col < K + w && gx_raw < nx) {
+        } else if (col >= KL && col < KL + w && gx_raw < nx) {
           float* g = A.dst + static_cast<long long>(R) * A.pitch + gx_raw;
           if (!lane_y_out) {
 #pragma unroll

@@ -162,13 +162,14 @@ def test_large_bounded_kernel_equals_single_steps(bc, steps):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("nx,ny,steps", [(2900, 2900, 2), (2900, 2900, 6), (2900, 2900, 13), (2900, 2900, 20),
-                                         (3002, 2795, 20), (2901, 2901, 20)])
+@pytest.mark.parametrize("nx,ny,steps", [(2900, 2900, 2), (2900, 2900, 3), (2900, 2900, 5), (2900, 2900, 6),
+                                         (2900, 2900, 11), (2900, 2900, 13), (2900, 2900, 20), (3002, 2795, 20),
+                                         (2901, 2901, 5), (2901, 2901, 20)])
 def test_large_periodic_kernel_equals_single_steps(nx, ny, steps):
     """Periodic grids of 2^23 cells or more with an even width run K = 6 in 256-column
-    strips (the headline kernel, with its branch-free steady state), and their tails K = 4
-    and K = 2 (20 = 6 + 6 + 4 + 4; 2), and the odd-width form (2901): bit for bit equal to one
-    step per launch on non-equilibrium populations (a seeded random 96-row tile repeated over
+    strips (the headline kernel, with its branch-free steady state), and their tails K = 4,
+    2, and the odd K = 5 and 3 (paired with an even left halo: 20 = 6 + 6 + 4 + 4, 11 = 6 + 5,
+    2, 3, 5), and the odd-width form (2901): bit for bit equal to one step per launch on non-equilibrium populations (a seeded random 96-row tile repeated over
     the grid; 3002 x 2795 has a narrow last strip and an odd height)."""
     tile = inputs.random_populations(13, 96, nx, seed=7900 + steps + nx).astype(np.float32)
     F0 = np.ascontiguousarray(np.tile(tile, (1, ny // 96 + 1, 1))[:, :ny, :])

@@ -66,7 +66,8 @@ bool temporal_active(const lbm_sw* h) {
 }
 
 // Launch plan of a fused handle (launch_plan.h): K, and whether odd sizes above one may run
-// (the one-column periodic kernel: BGK with every side periodic).
+// (BGK with every side periodic: the paired kernel with an even left halo at K = 3 and 5 on
+// large grids, else the one-column kernel).
 int plan_fused_launches(const lbm_sw* h, int n, int* plan, int max_plan) {
   const bool odd_ok = !h->mrt && h->p.bc[LBM_SW_SIDE_XM] == LBM_SW_BC_PERIODIC &&
                       h->p.bc[LBM_SW_SIDE_YM] == LBM_SW_BC_PERIODIC;

@@ -18,8 +18,9 @@ constexpr int kMaxTail = 16;  // K + 8 with K <= 8
 // (returns the number of launches written, at most max_plan, max_plan > kMaxTail).
 // Launches of K while more than K + 8 steps remain, then the cheapest split of the rest
 // (at most K + 8 steps) into launches of at most K steps: K itself and even sizes always
-// (the two-column kernels), other odd sizes above one only when odd_ok (the one-column
-// periodic kernel), at most one single step.  At K = 6 a call of 20
+// (the two-column kernels), other odd sizes above one only when odd_ok (every side periodic:
+// the paired kernel with an even left halo, or the one-column kernel), at most one single
+// step.  At K = 6 a call of 20
 // steps runs 6 + 6 + 4 + 4, one of 8 runs 4 + 4.  When max_plan runs out first, the
 // launches written cover part of n and the caller plans the rest in another call.
 inline int plan_launches(int K, bool odd_ok, int n, int* plan, int max_plan) {

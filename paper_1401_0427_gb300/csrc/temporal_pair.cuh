@@ -26,9 +26,10 @@ __host__ __device__ constexpr int plane_index(int p) {
 // Rows of the shared-memory planes have COLS + 4 floats, tile column i at i + 2, so a
 // pair is 8-byte aligned and a read one column beyond either end of the tile stays inside
 // the row (the cells that read it lie outside the level's valid range and are never used).
-// Input pairs land by 8-byte cp.async; with even K and even strip widths every strip
-// starts at an even column, so with an even nx no pair straddles the periodic seam (with
-// an odd nx the few that do land in two 4-byte copies).
+// Input pairs land by 8-byte cp.async; with the left halo rounded up to even (K + 1 columns
+// at odd K) and even strip widths every tile starts at an even column, so with an even nx no
+// pair straddles the periodic seam (with an odd nx the few that do land in two 4-byte
+// copies).
 template <int K, int COLS, int PF, bool L0R = false>
 struct PairShape {
   static constexpr int RS = COLS + 4;  // floats per plane row

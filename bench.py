@@ -62,7 +62,7 @@ def temporal_kernel_name(k: int, cells: int = 4096 * 4096) -> str:
 # kernel sources it was taken on.
 NCU_TRAFFIC = {
     "step2d_temporal_periodic_x2<6, 256, 1, 0, 1>": {
-        "src_sha256": "5b1d76084bb881438b01965d1ae813eab1caf6552addbb791f1a90055d29a84d",
+        "src_sha256": "80e7ae7f74be93879b84e2497f4374045768ef0edce63502b5c6969ca2b8cb60",
         "sources": ("temporal.cu", "temporal.cuh", "temporal_pair.cuh", "scheme.cuh"), "bytes_per_launch": 1745.18e6,
         "case": "ncu dram__bytes_read.sum + dram__bytes_write.sum (1 pass) of the 5 launches of "
                 "bench.py --quick --skip-cpu --steps 12 --warmup 3 (4096x4096): 921.25 MB read + 823.93 MB "

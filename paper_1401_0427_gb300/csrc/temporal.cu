@@ -464,11 +464,7 @@ cudaError_t launch_k_pairs(const StepArgs<float>& a, const ConstsD& kd, cudaStre
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int resident = cached_resident(fn, COLS / 2, smem);
-  // strips of at most COLS - K - KL columns (KL: the left halo, K rounded up to even)
-  Partition P = partition(a.nx, a.ny, (COLS - 2 * K - (K & 1)) & ~1, K, resident * std::max(sm_count, 1), 1);
-  P.w += P.w & 1;  // even strip width (<= COLS - K - KL since that is even)
-  P.strips = (a.nx + P.w - 1) / P.w;
-  const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
+  const Partition Q = pair_partition(a.nx, a.ny, K, COLS, resident * std::max(sm_count, 1));
   const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
   const dim3 grid(Q.strips * Q.segments), block(COLS / 2);
   float* const no_w = nullptr;
@@ -491,10 +487,7 @@ cudaError_t launch_k_pairs_w(const StepArgs<float>& a, const ConstsD& kd, float*
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int resident = cached_resident(fn, COLS / 2, smem);
-  Partition P = partition(a.nx, a.ny, COLS - 2 * K, K, resident * std::max(sm_count, 1), 1);
-  P.w += P.w & 1;
-  P.strips = (a.nx + P.w - 1) / P.w;
-  const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
+  const Partition Q = pair_partition(a.nx, a.ny, K, COLS, resident * std::max(sm_count, 1));
   const Consts<float> K_ = make_consts<float>(kd.g, kd.lambda, kd.s, kd.a);
   const dim3 grid(Q.strips * Q.segments), block(COLS / 2);
   if constexpr (PER)

@@ -110,5 +110,16 @@ inline Partition partition(int nx, int ny, int wmax, int K, int slots, int waves
   return partition_rows(P, ny, K, slots, waves);
 }
 
+// Strips and row segments of the paired wavefront (COLS tile columns, K steps): strips of an
+// even width of at most COLS - K - KL columns, KL = K rounded up to even being the left halo
+// (K + 1 columns at odd K), so that every tile starts at an even column and its K + w + KL
+// columns fit the COLS of the CTA; row segments for one wave of `slots` CTAs.
+inline Partition pair_partition(int nx, int ny, int K, int COLS, int slots) {
+  Partition P = partition(nx, ny, (COLS - 2 * K - (K & 1)) & ~1, K, slots, 1);
+  P.w += P.w & 1;  // even strip width (the bound above is even)
+  P.strips = (nx + P.w - 1) / P.w;
+  return partition_rows(P, ny, K, slots, 1);
+}
+
 }  // namespace
 }  // namespace lbm

@@ -32,10 +32,7 @@ cudaError_t launch_pairs_mrt(const StepArgs<float>& a, const ConstsD& kd, cudaSt
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int resident = cached_resident(fn, COLS / 2, smem);
-  Partition P = partition(a.nx, a.ny, COLS - 2 * K, K, resident * std::max(sm_count, 1), 1);
-  P.w += P.w & 1;  // even strip width (<= COLS - 2K since that is even)
-  P.strips = (a.nx + P.w - 1) / P.w;
-  const Partition Q = partition_rows(P, a.ny, K, resident * std::max(sm_count, 1), 1);
+  const Partition Q = pair_partition(a.nx, a.ny, K, COLS, resident * std::max(sm_count, 1));
   const Consts<float> K_ = make_consts_mrt<float>(kd.g, kd.lambda, kd.s, kd.a, kd.rates, 10);
   return launch_pdl(step2d_temporal_x2_mrt<K, COLS, PF, L0R, PER>, dim3(Q.strips * Q.segments), dim3(COLS / 2), smem,
                     st, a, K_, Q);

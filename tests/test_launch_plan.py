@@ -4,7 +4,7 @@ and run for every K, both kinds of sides and every step count up to 3000, in the
 lbm_sw_step calls it (plan buffers of 64 launches, called again until n is covered).
 
 Every plan must cover exactly n steps, use only sizes the kernels provide (at most K: K itself,
-even sizes, other odd sizes above one only where the one-column periodic kernel runs), run the bulk
+even sizes, other odd sizes above one only with every side periodic), run the bulk
 as launches of K, and use at most one single step (with even fused sizes only, only for an
 odd step count)."""
 
